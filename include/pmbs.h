@@ -1,0 +1,246 @@
+/*
+ * pmbs.h - C ABI of the B300 batched push-rollout engine for PMBS (parallel Monte
+ * Carlo tree search with batched simulation, arXiv 2207.06649).
+ *
+ * The engine executes the paper's batch expansion and batch simulation (Sec. IV-C):
+ * many environments, each loaded with a selected state (Sec. IV-C "Batch Expansion":
+ * environments are loaded with the selected states, then the transition is carried
+ * out in parallel), execute a first push action and then further random pushes drawn
+ * by the contour action sampler (Sec. IV-B "Speeding up Action Sampling"), with a
+ * terminal test after every push (Sec. IV-C "Batch Simulation").  A scene is a set of
+ * rigid boxes on a table plane with a designated target (Sec. III-A, state space); an
+ * action is a straight push a^p = (x_s, y_s, x_e, y_e) of a kinematic vertical capsule
+ * (Sec. III-A, action space); the transition is rigid-body simulation with friction and
+ * collisions (Sec. III-A, transition function); the terminal test is a geometric
+ * grasp-clearance check in place of the learned grasp classifier (Sec. IV-B "Grasp
+ * Evaluation"); the cost-to-go of an environment is the number of pushes until the
+ * target is graspable and its reward gamma^(cost-1) (Sec. III-A reward, Sec. V-A gamma).
+ *
+ * Conventions.  SI units (m, kg, s, rad); z up; the table plane is z = 0; quaternions
+ * are (w, x, y, z).  A box state row has 13 floats: x y z qw qx qy qz vx vy vz wx wy wz.
+ * All arithmetic is IEEE binary32 on CUDA cores of one GPU (sm_103a).
+ *
+ * Errors.  Every call returns a pmbs_status; nothing aborts, exits or traps the GPU.
+ * CUDA errors map to PMBS_E_CUDA and invalid arguments to PMBS_E_INVALID, with a
+ * message in pmbs_last_error().  Device-side waits are bounded.
+ *
+ * Ownership.  The context owns all device memory it allocates (or the arena handed to
+ * pmbs_create_with_arena, which the caller keeps alive until pmbs_destroy).  Host input
+ * arrays are copied before a call returns; host output arrays belong to the caller.
+ * Pointers documented as "device" must be device-accessible pointers on the context's
+ * device; every other pointer is a host pointer.
+ *
+ * Threads.  pmbs_create / pmbs_destroy are not thread-safe.  Every other call takes the
+ * context's lock, so calls from several threads are serialised and safe.
+ */
+#ifndef PMBS_H
+#define PMBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmbs_ctx pmbs_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    PMBS_OK = 0,
+    PMBS_E_INVALID = 1,   /* bad argument or scene (non-finite, non-unit quaternion, ...) */
+    PMBS_E_OOM = 2,       /* device arena cannot hold the request (memory admission) */
+    PMBS_E_CUDA = 3,      /* a CUDA runtime call failed; see pmbs_last_error */
+    PMBS_E_NOT_READY = 4, /* the batch still has substeps to run */
+    PMBS_E_TIMEOUT = 5,   /* a bounded device wait gave up */
+    PMBS_E_BUSY = 6       /* the resource is in use (e.g. releasing a running batch) */
+} pmbs_status;
+
+/* Per-environment result flags (out_flags). */
+enum {
+    PMBS_FLAG_GRASP_AFTER_PUSH1 = 1, /* target graspable after the first push */
+    PMBS_FLAG_INVALID_START = 2,     /* first push starts inside a box: not simulated */
+    PMBS_FLAG_OUT_OF_WORKSPACE = 4,  /* a box centre left the table (Sec. V-A boundary) */
+    PMBS_FLAG_CONTACT_OVERFLOW = 8,  /* a pair/manifold/point/colour cap dropped contacts */
+    PMBS_FLAG_NOOP_PUSH = 16         /* a sampled push found no free start: no-op push */
+};
+
+/* Event counters per environment (pmbs_query_events), in this order. */
+#define PMBS_NUM_EVENTS 16
+
+typedef struct {
+    int device;                 /* CUDA device ordinal */
+    int max_envs;               /* largest batch accepted by one pmbs_rollout_pushes */
+    int max_boxes_per_env;      /* <= 64 */
+    size_t mem_budget_bytes;    /* device arena size (scenes + batches + solver scratch) */
+    float dt;                   /* substep length, 1/240 s */
+    int substeps_per_push;      /* 240 */
+    int pgs_iters;              /* 10 projected Gauss-Seidel iterations per substep */
+    float gravity[3];           /* 0, 0, -9.81 */
+    float table_half[2];        /* workspace half sizes, 0.2 x 0.2 m */
+    float table_mu, pusher_mu;  /* 0.5, 0.5 (pair friction = sqrt(mu_a mu_b)) */
+    float pusher_radius;        /* 0.01 m */
+    float pusher_z0, pusher_z1; /* capsule segment z range, 0.01 .. 0.20 m */
+    float pusher_speed;         /* 0.1 m/s */
+    float push_length;          /* 0.1 m, length of device-sampled pushes */
+    float gamma;                /* 0.8 (Sec. V-A) */
+    float grasp_opening;        /* 0.085 m (two-finger gripper, fixed opening, Sec. III-A) */
+    float grasp_clearance;      /* 0.002 m */
+    float finger_depth;         /* 0.01 m */
+    float finger_width;         /* 0.022 m */
+    int grasp_angles;           /* 16 jaw angles k*pi/16, <= 32 */
+    float margin;               /* 1e-3 m contact margin */
+    float slop;                 /* 5e-4 m allowed penetration */
+    float baumgarte;            /* 0.2 */
+    float sample_clearance;     /* 0.005 m: sampled pushes start this far beyond radius */
+    int sample_attempts;        /* 8 tries per sampled push, <= 32 */
+    int contour_points;         /* 16 contour points per object (N_a, Sec. IV-B) */
+    int contact_cap;            /* 512 contact points per environment */
+    int manifold_cap;           /* 256 manifolds per environment (<= 1024) */
+    int pair_cap;               /* 1024 box-box broadphase pairs per environment */
+    int warps_per_block;        /* launch shape; 0 = autotune */
+    int smem_points;            /* contact points kept in shared memory per env; -1 = autotune */
+    int smem_manifolds;         /* manifolds kept in shared memory per env; -1 = autotune */
+} pmbs_config;
+
+/* Fill *cfg with the defaults listed above.  Never fails. */
+void pmbs_default_config(pmbs_config* cfg);
+
+/* Create a context on cfg->device that enqueues all work on cuda_stream (a cudaStream_t;
+ * NULL = the legacy default stream).  Allocates a device arena of cfg->mem_budget_bytes.
+ * Returns PMBS_E_INVALID for out-of-range fields, PMBS_E_OOM / PMBS_E_CUDA on failure. */
+pmbs_status pmbs_create(const pmbs_config* cfg, void* cuda_stream, pmbs_ctx** out);
+
+/* As pmbs_create, but uses the caller's device allocation (e.g. a PyTorch tensor) of
+ * arena_bytes bytes at device pointer d_arena (256-byte aligned) instead of allocating. */
+pmbs_status pmbs_create_with_arena(const pmbs_config* cfg, void* cuda_stream, void* d_arena,
+                                   size_t arena_bytes, pmbs_ctx** out);
+
+/* Synchronise the stream and free everything the context owns.  NULL is a no-op. */
+void pmbs_destroy(pmbs_ctx* ctx);
+
+/* Message of the last error on this context (empty string if none).  Valid until the
+ * next call on the context. */
+const char* pmbs_last_error(const pmbs_ctx* ctx);
+
+/* Load scenes into the device-resident scene store (Sec. IV-C batch expansion loads
+ * selected states into environments; a scene here is such a state).  CSR over boxes:
+ * scene s owns rows box_offset[s] .. box_offset[s+1]-1 of pose [B][7] (x y z qw qx qy
+ * qz), vel [B][6] (linear, angular; NULL = at rest), half_ext [B][3], mass [B], mu [B];
+ * target[s] is the local index of its target box.  Writes one id per scene to
+ * out_scene_ids.  Validation: finite values, | |q| - 1 | <= 1e-3, 1 <= n <= max boxes,
+ * positive half extents and mass, target in range -> else PMBS_E_INVALID; no room in the
+ * arena -> PMBS_E_OOM.  Copies synchronously. */
+pmbs_status pmbs_load_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offset,
+                             const float* pose, const float* vel, const float* half_ext,
+                             const float* mass, const float* mu, const int32_t* target,
+                             int32_t* out_scene_ids);
+
+/* Release scenes.  Unknown or already-freed ids -> PMBS_E_INVALID; a scene used by a batch
+ * that has not been released -> PMBS_E_BUSY. */
+pmbs_status pmbs_free_scenes(pmbs_ctx* ctx, int n, const int32_t* scene_ids);
+
+/* Enqueue a rollout batch (Sec. IV-C batch expansion + batch simulation, Alg. 1
+ * Expansion and Simulation): environment e starts from scene scene_ids[e] and executes
+ * first_push[e] = (x_s, y_s, x_e, y_e), then depth-1 pushes drawn on the device by the
+ * contour sampler keyed by seeds[e].  Several environments may share one scene (leaf
+ * parallelisation, Sec. IV-C).  Copies the inputs and returns a batch handle; no
+ * substep runs until pmbs_step.  depth in 1..64; n_envs in 0..max_envs. */
+pmbs_status pmbs_rollout_pushes(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids,
+                                const float* first_push, int depth, const uint64_t* seeds,
+                                int64_t* out_batch);
+
+/* As pmbs_rollout_pushes with device pointers for scene_ids, first_push and seeds (read
+ * on the stream before the first pmbs_step of the batch returns control). */
+pmbs_status pmbs_rollout_pushes_device(pmbs_ctx* ctx, int n_envs, const int32_t* d_scene_ids,
+                                       const float* d_first_push, int depth,
+                                       const uint64_t* d_seeds, int64_t* out_batch);
+
+/* Advance every unfinished environment of the batch by up to max_substeps substeps
+ * (<= 0: to completion) in one persistent launch on the context's stream.  Returns
+ * PMBS_OK when the batch is finished, PMBS_E_NOT_READY when substeps remain.  The call
+ * synchronises the stream only when max_substeps > 0 (to report readiness); with
+ * max_substeps <= 0 it returns PMBS_OK immediately after enqueueing. */
+pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps);
+
+/* Results of a finished batch, copied to host arrays of n_envs entries: cost (pushes
+ * until graspable, depth+1 if never), reward (gamma^(cost-1) or 0), flags (PMBS_FLAG_*).
+ * out_child_states (NULL to skip): [sum of boxes][13] state after push 1, the new tree
+ * node of the expansion (Sec. IV-C); out_child_scene_ids (NULL to skip): registers each
+ * child state as a new scene and writes its id.  Synchronises the stream.  Any output
+ * pointer may be NULL. */
+pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, float* out_reward,
+                            uint8_t* out_flags, float* out_child_states,
+                            int32_t* out_child_scene_ids);
+
+/* As pmbs_query_cost but copies into device buffers asynchronously on the stream. */
+pmbs_status pmbs_query_cost_device(pmbs_ctx* ctx, int64_t batch, int32_t* d_cost,
+                                   float* d_reward, uint8_t* d_flags);
+
+/* Current state of every environment ([sum of boxes][13], rows in env order) and the
+ * number of substeps each environment has simulated so far.  Either may be NULL.
+ * Synchronises the stream. */
+pmbs_status pmbs_query_states(pmbs_ctx* ctx, int64_t batch, float* out_states,
+                              int32_t* out_env_steps);
+
+/* Event counters [n_envs][PMBS_NUM_EVENTS] (substeps, box-steps, pair tests, SAT tests,
+ * face contacts, edge contacts, plane candidates, pusher candidates, contact points,
+ * manifolds, PGS manifold visits, PGS point visits, push evaluations, sampler attempts,
+ * clipped vertices, colours) used to count the algorithmic flops of a launch. */
+pmbs_status pmbs_query_events(pmbs_ctx* ctx, int64_t batch, uint64_t* out_events);
+
+/* Number of environments and boxes in the batch. */
+pmbs_status pmbs_batch_info(pmbs_ctx* ctx, int64_t batch, int32_t* out_n_envs,
+                            int32_t* out_n_boxes);
+
+/* Free a batch's device memory (synchronises the stream). */
+pmbs_status pmbs_release_batch(pmbs_ctx* ctx, int64_t batch);
+
+/* Snapshot evaluation of the bit-exact binary32 predicates, running the same device
+ * functions as the rollout kernel, one environment per warp.  Environments are CSR over
+ * state rows ([B][13]) and half extents ([B][3]).
+ *  pmbs_eval_pairs: broadphase at the given states (Sec. III-A collisions; AABB per box,
+ *    box-box pairs in lexicographic order, plane and pusher candidates).  pusher_xy
+ *    [n_envs][2] or NULL (no pusher).  Outputs: out_pairs [n_envs][pair_cap][2],
+ *    out_n_pairs [n_envs] (capped), out_plane / out_pusher [B] (per env, in CSR rows, the
+ *    first out_n_plane[e] / out_n_pusher[e] entries are box indices).
+ *  pmbs_eval_grasp: grasp-clearance decision of target[e] (Sec. IV-B grasp evaluation).
+ *  pmbs_eval_sample: device-sampled push number k (>= 2) keyed by seeds[e] (Sec. IV-B
+ *    contour sampling); out_attempt[e] = accepted attempt or -1 for a no-op push.
+ *  pmbs_eval_start_blocked: 1 when a push starting at starts[e] (x, y) would start inside
+ *    a box (Sec. IV-B start-pose collision check). */
+pmbs_status pmbs_eval_pairs(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset,
+                            const float* states, const float* half_ext, const float* pusher_xy,
+                            int32_t* out_pairs, int32_t* out_n_pairs, int32_t* out_plane,
+                            int32_t* out_n_plane, int32_t* out_pusher, int32_t* out_n_pusher);
+pmbs_status pmbs_eval_grasp(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset,
+                            const float* states, const float* half_ext, const int32_t* target,
+                            uint8_t* out_graspable);
+pmbs_status pmbs_eval_sample(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset,
+                             const float* states, const float* half_ext, const uint64_t* seeds,
+                             int k, float* out_push, int32_t* out_attempt);
+pmbs_status pmbs_eval_start_blocked(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset,
+                                    const float* states, const float* half_ext,
+                                    const float* starts, uint8_t* out_blocked);
+
+/* Launch shape the context uses for a batch whose largest scene has max_boxes boxes:
+ * warps per block, contact points and manifolds kept in shared memory per environment,
+ * and shared bytes per block.  Chosen by the autotuner unless fixed in the config. */
+pmbs_status pmbs_launch_shape(pmbs_ctx* ctx, int max_boxes, int32_t* out_warps_per_block,
+                              int32_t* out_smem_points, int32_t* out_smem_manifolds,
+                              int32_t* out_smem_bytes);
+
+/* Override the launch shape for subsequent batches (warps_per_block in {1,2,4,8}; smem
+ * points/manifolds >= 0).  Changes scheduling only: results are bit-identical. */
+pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int warps_per_block, int smem_points,
+                                  int smem_manifolds);
+
+/* Measured FP32 FMA throughput of the device (TFLOP/s) from a microbenchmark of
+ * independent FMA chains at full occupancy; the paper has no counterpart (roofline
+ * denominator for the contact solve). */
+pmbs_status pmbs_fp32_peak(pmbs_ctx* ctx, double* out_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMBS_H */

@@ -443,17 +443,19 @@ bool box_plane(const Body& b, int bi, const oracle_params& P, Manifold& M) {
 }
 
 // Sutherland-Hodgman clip of a polygon against the half space dot(p - o, a) - h <= 0.
+// At most eight vertices are kept (the bound for a convex quad clipped four times).
 std::vector<V3> clip_side(const std::vector<V3>& poly, V3 o, V3 a, double h) {
     std::vector<V3> out;
     const size_t N = poly.size();
+    auto add = [&](V3 p) { if (out.size() < 8) out.push_back(p); };
     for (size_t i = 0; i < N; i++) {
         const V3 cur = poly[i], prev = poly[(i + N - 1) % N];
         const double dc = dot(cur - o, a) - h, dp = dot(prev - o, a) - h;
         if (dc <= 0) {
-            if (dp > 0) out.push_back(prev + (cur - prev) * (dp / (dp - dc)));
-            out.push_back(cur);
+            if (dp > 0) add(prev + (cur - prev) * (dp / (dp - dc)));
+            add(cur);
         } else if (dp <= 0) {
-            out.push_back(prev + (cur - prev) * (dp / (dp - dc)));
+            add(prev + (cur - prev) * (dp / (dp - dc)));
         }
     }
     return out;

@@ -1,0 +1,371 @@
+// Narrowphase of the rollout engine (FP32, one lane per candidate pair).
+//
+// The paper specifies the transition only as rigid-body motion with friction and
+// collisions (Sec. III-A, transition function); the contact model below is this
+// library's reading: box-plane vertex contacts, box-box separating-axis test over 15 axes
+// with reference-face clipping (at most four points) or one edge-edge point, and a
+// capsule pusher against a box by closest points at the ends of the overlapping height
+// range.  Separation d < 0 means penetration; contacts are kept while d < margin.
+#pragma once
+#include <cstdint>
+
+namespace pmbs {
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float norm3(float3 a) { return sqrtf(dot3(a, a)); }
+
+// A box for collision: centre, row-major rotation (columns = axes), half extents.
+struct CBox {
+    float3 c;
+    float R[9];
+    float h[3];
+    __device__ __forceinline__ float3 ax(int k) const { return f3(R[k], R[3 + k], R[6 + k]); }
+    __device__ __forceinline__ float3 rot(float3 l) const {
+        return f3(R[0] * l.x + R[1] * l.y + R[2] * l.z, R[3] * l.x + R[4] * l.y + R[5] * l.z,
+                  R[6] * l.x + R[7] * l.y + R[8] * l.z);
+    }
+};
+
+// Contact points produced for one candidate: point p (world), separation d; all points
+// share one normal n, from body A to body B.
+struct CManifold {
+    int np;
+    float3 n;
+    float3 p[4];
+    float d[4];
+};
+
+// Box against plane z = 0 (A = plane, B = box): vertices below the margin, deepest
+// first with ties by vertex index, at most four.  Contact offsets from the box centre
+// are returned in p (the world point is c + p).
+__device__ __forceinline__ void collide_box_plane(const CBox& b, float margin, CManifold& M) {
+    M.np = 0;
+    M.n = f3(0.f, 0.f, 1.f);
+    for (int v = 0; v < 8; v++) {
+        const float3 l = f3((v & 1) ? b.h[0] : -b.h[0], (v & 2) ? b.h[1] : -b.h[1], (v & 4) ? b.h[2] : -b.h[2]);
+        const float3 r = b.rot(l);
+        const float d = b.c.z + r.z;
+        if (!(d < margin)) continue;
+        // insertion into the depth-sorted list (stable: equal depths keep vertex order)
+        int pos = M.np < 4 ? M.np : 4;
+        while (pos > 0 && d < M.d[pos - 1]) pos--;
+        if (pos >= 4) continue;
+        const int last = M.np < 4 ? M.np : 3;
+        for (int k = last; k > pos; k--) {
+            M.d[k] = M.d[k - 1];
+            M.p[k] = M.p[k - 1];
+        }
+        M.d[pos] = d;
+        M.p[pos] = r;
+        if (M.np < 4) M.np++;
+    }
+}
+
+// Sutherland-Hodgman clip of poly (n points) against dot(p - o, a) - h <= 0.  A convex
+// quad clipped four times has at most eight vertices; rounding on degenerate faces could
+// produce more, and vertices beyond the eighth are dropped.
+__device__ __forceinline__ int clip_side(const float3* in, int n, float3* out, float3 o, float3 a, float h) {
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        const float3 cur = in[i];
+        const float3 prev = in[(i + n - 1) % n];
+        const float dc = dot3(cur - o, a) - h, dp = dot3(prev - o, a) - h;
+        if (dc <= 0.f) {
+            if (dp > 0.f && m < 8) out[m++] = prev + (cur - prev) * (dp / (dp - dc));
+            if (m < 8) out[m++] = cur;
+        } else if (dp <= 0.f) {
+            if (m < 8) out[m++] = prev + (cur - prev) * (dp / (dp - dc));
+        }
+    }
+    return m;
+}
+
+// Clip the incident face of `inc` against the side planes of face k (outward normal
+// nref) of `ref`; keep points within the margin; reduce to four points.  Returns the
+// number of points in M (p = world point, d = separation from the reference face).
+__device__ __forceinline__ int face_contact(const CBox& ref, int k, float3 nref, const CBox& inc, float margin,
+                                            CManifold& M, int& clip_verts) {
+    const float3 fc = ref.c + nref * ref.h[k];
+    const int k1 = (k == 0) ? 1 : 0, k2 = (k == 2) ? 1 : 2;
+    const float3 u = ref.ax(k1), v = ref.ax(k2);
+    const float hu = ref.h[k1], hv = ref.h[k2];
+    int best_f = 0;
+    float best = 0.f;
+    for (int m = 0; m < 3; m++) {
+        const float dm = dot3(inc.ax(m), nref);
+        if (m == 0 || dm < best) {
+            best = dm;
+            best_f = 2 * m;
+        }
+        if (-dm < best) {
+            best = -dm;
+            best_f = 2 * m + 1;
+        }
+    }
+    const int mi = best_f >> 1;
+    const float si = (best_f & 1) ? -1.f : 1.f;
+    const int m1 = (mi == 0) ? 1 : 0, m2 = (mi == 2) ? 1 : 2;
+    const float3 fi = inc.c + inc.ax(mi) * (si * inc.h[mi]);
+    const float3 e1 = inc.ax(m1) * inc.h[m1], e2 = inc.ax(m2) * inc.h[m2];
+    float3 A[8], B[8];
+    A[0] = fi + e1 + e2;
+    A[1] = fi - e1 + e2;
+    A[2] = fi - e1 - e2;
+    A[3] = fi + e1 - e2;
+    int n = 4;
+    n = clip_side(A, n, B, fc, u, hu);
+    n = clip_side(B, n, A, fc, -u, hu);
+    n = clip_side(A, n, B, fc, v, hv);
+    n = clip_side(B, n, A, fc, -v, hv);
+    clip_verts += n;
+    float kd[8];
+    int nk = 0;
+    for (int i = 0; i < n; i++) {
+        const float d = dot3(A[i] - fc, nref);
+        if (d < margin) {
+            B[nk] = A[i];
+            kd[nk] = d;
+            nk++;
+        }
+    }
+    if (nk <= 4) {
+        for (int i = 0; i < nk; i++) {
+            M.p[i] = B[i];
+            M.d[i] = kd[i];
+        }
+        return nk;
+    }
+    // deepest; farthest from it; largest triangle; largest area added outside an edge
+    unsigned used = 0;
+    int i1 = 0;
+    for (int i = 1; i < nk; i++)
+        if (kd[i] < kd[i1]) i1 = i;
+    used |= 1u << i1;
+    int i2 = -1;
+    float b2 = -1.f;
+    for (int i = 0; i < nk; i++) {
+        if (used >> i & 1u) continue;
+        const float3 e = B[i] - B[i1];
+        const float l = dot3(e, e);
+        if (i2 < 0 || l > b2) {
+            b2 = l;
+            i2 = i;
+        }
+    }
+    used |= 1u << i2;
+    int i3 = -1;
+    float b3 = -1.f;
+    for (int i = 0; i < nk; i++) {
+        if (used >> i & 1u) continue;
+        const float a = fabsf(dot3(cross3(B[i2] - B[i1], B[i] - B[i1]), nref));
+        if (i3 < 0 || a > b3) {
+            b3 = a;
+            i3 = i;
+        }
+    }
+    used |= 1u << i3;
+    const float sgn = dot3(cross3(B[i2] - B[i1], B[i3] - B[i1]), nref) < 0.f ? -1.f : 1.f;
+    int i4 = -1;
+    float b4 = 0.f;
+    for (int i = 0; i < nk; i++) {
+        if (used >> i & 1u) continue;
+        float a = -sgn * dot3(cross3(B[i2] - B[i1], B[i] - B[i1]), nref);
+        a = fmaxf(a, -sgn * dot3(cross3(B[i3] - B[i2], B[i] - B[i2]), nref));
+        a = fmaxf(a, -sgn * dot3(cross3(B[i1] - B[i3], B[i] - B[i3]), nref));
+        if (i4 < 0 || a > b4) {
+            b4 = a;
+            i4 = i;
+        }
+    }
+    const int sel[4] = {i1, i2, i3, i4};
+    for (int i = 0; i < 4; i++) {
+        M.p[i] = B[sel[i]];
+        M.d[i] = kd[sel[i]];
+    }
+    return 4;
+}
+
+// Box-box contact (A = lower index).  Separating axes: 3 faces of A, 3 of B, 9 edge
+// crosses (skipped when |cross|^2 < 1e-12).  Any separation >= margin: no contact.  A
+// face of B replaces A's best face only when its separation is larger by > 1e-5 m; an
+// edge axis replaces the face only when larger by > 1e-4 m + 5% |face separation|;
+// earliest axis wins exact ties.  Normal from A to B.  kind: 0 none, 1 face, 2 edge.
+__device__ __forceinline__ int collide_box_box(const CBox& A, const CBox& B, float margin, CManifold& M,
+                                               int& clip_verts) {
+    M.np = 0;
+    const float3 D = B.c - A.c;
+    float3 a[3] = {A.ax(0), A.ax(1), A.ax(2)};
+    float3 b[3] = {B.ax(0), B.ax(1), B.ax(2)};
+    float aC[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int m = 0; m < 3; m++) aC[k][m] = fabsf(dot3(a[k], b[m]));
+    int fa = -1;
+    float sa = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float s = fabsf(dot3(D, a[k])) - (A.h[k] + (B.h[0] * aC[k][0] + B.h[1] * aC[k][1] + B.h[2] * aC[k][2]));
+        if (s >= margin) return 0;
+        if (fa < 0 || s > sa) {
+            fa = k;
+            sa = s;
+        }
+    }
+    int fb = -1;
+    float sb = 0.f;
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        const float s = fabsf(dot3(D, b[m])) - ((A.h[0] * aC[0][m] + A.h[1] * aC[1][m] + A.h[2] * aC[2][m]) + B.h[m]);
+        if (s >= margin) return 0;
+        if (fb < 0 || s > sb) {
+            fb = m;
+            sb = s;
+        }
+    }
+    int fe = -1;
+    float se = 0.f;
+    float3 le = f3(0.f, 0.f, 0.f);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            const float3 L = cross3(a[i], b[j]);
+            const float l2 = dot3(L, L);
+            if (l2 < 1e-12f) continue;
+            const float len = sqrtf(l2);
+            const float rA = (A.h[0] * fabsf(dot3(a[0], L)) + A.h[1] * fabsf(dot3(a[1], L))) + A.h[2] * fabsf(dot3(a[2], L));
+            const float rB = (B.h[0] * fabsf(dot3(b[0], L)) + B.h[1] * fabsf(dot3(b[1], L))) + B.h[2] * fabsf(dot3(b[2], L));
+            const float s = (fabsf(dot3(D, L)) - (rA + rB)) / len;
+            if (s >= margin) return 0;
+            if (fe < 0 || s > se) {
+                fe = 6 + 3 * i + j;
+                se = s;
+                le = L * (1.f / len);
+            }
+        }
+    int axis = fa;
+    float s = sa;
+    float3 L = a[fa];
+    if (sb > sa + 1e-5f) {
+        axis = 3 + fb;
+        s = sb;
+        L = b[fb];
+    }
+    if (fe >= 0 && se > s + 1e-4f + 0.05f * fabsf(s)) {
+        axis = fe;
+        s = se;
+        L = le;
+    }
+    if (dot3(L, D) < 0.f) L = -L;
+    M.n = L;
+    if (axis < 3) {
+        M.np = face_contact(A, axis, L, B, margin, M, clip_verts);
+        return M.np ? 1 : 0;
+    }
+    if (axis < 6) {
+        M.np = face_contact(B, axis - 3, -L, A, margin, M, clip_verts);
+        return M.np ? 1 : 0;
+    }
+    const int ea = (axis - 6) / 3, eb = (axis - 6) % 3;
+    float3 pA = A.c, pB = B.c;
+    for (int k = 0; k < 3; k++) {
+        if (k == ea) continue;
+        const float sg = dot3(a[k], L) < 0.f ? -1.f : 1.f;
+        pA = pA + a[k] * (sg * A.h[k]);
+    }
+    for (int m = 0; m < 3; m++) {
+        if (m == eb) continue;
+        const float sg = dot3(b[m], L) > 0.f ? -1.f : 1.f;
+        pB = pB + b[m] * (sg * B.h[m]);
+    }
+    const float3 dA = a[ea], dB = b[eb];
+    const float3 r = pA - pB;
+    const float bb = dot3(dA, dB), c = dot3(dA, r), f = dot3(dB, r);
+    const float den = 1.f - bb * bb;
+    float ta = 0.f, tb;
+    if (den > 1e-12f) {
+        ta = (bb * f - c) / den;
+        tb = f + ta * bb;
+    } else {
+        tb = f;
+    }
+    ta = fminf(fmaxf(ta, -A.h[ea]), A.h[ea]);
+    tb = fminf(fmaxf(tb, -B.h[eb]), B.h[eb]);
+    const float3 qa = pA + dA * ta, qb = pB + dB * tb;
+    M.p[0] = (qa + qb) * 0.5f;
+    M.d[0] = s;
+    M.np = 1;
+    return 2;
+}
+
+// Vertical capsule (axis through (px, py), z in [z0, z1], radius r) against a box (A =
+// box, B = pusher).  The segment is clipped to the box's vertical extent; each end of
+// the clipped range (its middle when shorter than 1 mm; the nearer segment end when the
+// ranges do not meet) yields the closest box point.  Normal (box to pusher) of the
+// nearest candidate.  p = point on the box (world).
+__device__ __forceinline__ void collide_capsule_box(const CBox& b, float px, float py, float z0, float z1, float r,
+                                                    float margin, CManifold& M) {
+    M.np = 0;
+    const float ez = (fabsf(b.R[6]) * b.h[0] + fabsf(b.R[7]) * b.h[1]) + fabsf(b.R[8]) * b.h[2];
+    const float zlo = b.c.z - ez, zhi = b.c.z + ez;
+    const float za = fmaxf(z0, zlo), zb = fminf(z1, zhi);
+    float zc[2];
+    int nc;
+    if (za > zb) {
+        zc[0] = (zhi < z0) ? z0 : z1;
+        nc = 1;
+    } else if (zb - za < 1e-3f) {
+        zc[0] = (za + zb) * 0.5f;
+        nc = 1;
+    } else {
+        zc[0] = za;
+        zc[1] = zb;
+        nc = 2;
+    }
+    float best_d = 0.f;
+    float3 best_n = f3(1.f, 0.f, 0.f);
+    for (int i = 0; i < nc; i++) {
+        const float3 S = f3(px, py, zc[i]);
+        const float3 rel = S - b.c;
+        float loc[3], ql[3];
+        for (int k = 0; k < 3; k++) {
+            loc[k] = dot3(b.ax(k), rel);
+            ql[k] = fminf(fmaxf(loc[k], -b.h[k]), b.h[k]);
+        }
+        const float3 Q = b.c + b.ax(0) * ql[0] + b.ax(1) * ql[1] + b.ax(2) * ql[2];
+        const float3 diff = S - Q;
+        const float dist = norm3(diff);
+        float3 nrm;
+        float d;
+        if (dist > 1e-6f) {
+            nrm = diff * (1.f / dist);
+            d = dist - r;
+        } else {
+            float pen = b.h[0] - fabsf(loc[0]);
+            pen = fminf(pen, b.h[1] - fabsf(loc[1]));
+            pen = fminf(pen, b.h[2] - fabsf(loc[2]));
+            d = -pen - r;
+            const float3 w = f3(S.x - b.c.x, S.y - b.c.y, 0.f);
+            const float lw = norm3(w);
+            nrm = lw > 1e-9f ? w * (1.f / lw) : f3(1.f, 0.f, 0.f);
+        }
+        if (!(d < margin)) continue;
+        M.p[M.np] = Q;
+        M.d[M.np] = d;
+        if (M.np == 0 || d < best_d) {
+            best_d = d;
+            best_n = nrm;
+        }
+        M.np++;
+    }
+    M.n = best_n;
+}
+
+}  // namespace pmbs

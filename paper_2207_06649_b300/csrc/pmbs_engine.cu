@@ -1,0 +1,1434 @@
+// Batched push-rollout engine for PMBS on one B300 (sm_103a): kernels and the C ABI.
+//
+// One warp runs one environment (a scene copy, Sec. IV-C: "the number of parallel
+// environments in the simulator is fixed to some number N_e"); a persistent grid pulls
+// environments from a device work queue ordered by box count, largest first, so that
+// scenes of uneven size share one launch and a warp that finishes an environment early
+// (target graspable, Sec. IV-C: early-terminated environments are re-purposed) takes the
+// next one.  See pmbs.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pmbs.h"
+#include "pmbs_warp.cuh"
+
+using namespace pmbs;
+
+namespace {
+
+constexpr int kRecFloats = 18;  // scene record per box: state13, half[3], mass, mu
+constexpr int kSceneTableCap = 1 << 18;
+constexpr int kMaxWarpsPerSM = 32;
+
+struct SceneDesc {
+    const float* rec;
+    int n;
+    int target;
+};
+
+struct EnvIn {
+    const float* rec;
+    int n;
+    int target;
+    int box_off;
+    int scene;
+};
+
+struct EnvProg {
+    int k, s, push_ready, done;
+    int flags, cost, steps, noop;
+    float reward;
+    float push[4];
+    int pad[3];
+};
+
+struct RolloutArgs {
+    SimConst C;
+    Layout L;
+    int n_envs, depth, max_substeps, child_on;
+    const EnvIn* env;
+    const int* order;
+    int* queue_head;
+    int* done_count;
+    const float4* first_push;
+    const uint64_t* seeds;
+    EnvProg* prog;
+    float* state;
+    float* child;
+    int32_t* cost;
+    float* reward;
+    uint8_t* flags;
+    int32_t* steps;
+    unsigned long long* events;
+    float4* gscratch;
+    int scratch_f4_per_warp;
+};
+
+// ------------------------------------------------------------------ device: one env
+__device__ void load_env(const RolloutArgs& a, const WarpMem& W, const EnvIn& ei, bool from_scene, int lane) {
+    const int NB = W.NB;
+    for (int i = lane; i < ei.n; i += 32) {
+        const float* r = ei.rec + kRecFloats * i;
+        const float* s = from_scene ? r : a.state + (size_t)(ei.box_off + i) * 13;
+        W.x[i] = s[0];
+        W.x[NB + i] = s[1];
+        W.x[2 * NB + i] = s[2];
+        W.q[i] = s[3];
+        W.q[NB + i] = s[4];
+        W.q[2 * NB + i] = s[5];
+        W.q[3 * NB + i] = s[6];
+        const float h0 = r[13], h1 = r[14], h2 = r[15], m = r[16], mu = r[17];
+        W.h[i] = h0;
+        W.h[NB + i] = h1;
+        W.h[2 * NB + i] = h2;
+        W.bv[i] = make_float4(s[7], s[8], s[9], 1.f / m);
+        W.bw[i] = make_float4(s[10], s[11], s[12], mu);
+        const float hx2 = h0 * h0, hy2 = h1 * h1, hz2 = h2 * h2;
+        W.ib[i] = 1.f / (m / 3.f * (hy2 + hz2));
+        W.ib[NB + i] = 1.f / (m / 3.f * (hx2 + hz2));
+        W.ib[2 * NB + i] = 1.f / (m / 3.f * (hx2 + hy2));
+    }
+    __syncwarp();
+}
+
+__device__ void store_state(const WarpMem& W, int n, float* dst, int lane) {
+    const int NB = W.NB;
+    for (int i = lane; i < n; i += 32) {
+        float* s = dst + (size_t)i * 13;
+        const float4 v = W.bv[i], w = W.bw[i];
+        s[0] = W.x[i];
+        s[1] = W.x[NB + i];
+        s[2] = W.x[2 * NB + i];
+        s[3] = W.q[i];
+        s[4] = W.q[NB + i];
+        s[5] = W.q[2 * NB + i];
+        s[6] = W.q[3 * NB + i];
+        s[7] = v.x;
+        s[8] = v.y;
+        s[9] = v.z;
+        s[10] = w.x;
+        s[11] = w.y;
+        s[12] = w.z;
+    }
+}
+
+struct Counters {
+    unsigned long long ev[kNumEvents];
+};
+
+// One substep of one environment (all lanes).  Returns true on a cap overflow.
+__device__ bool substep(const RolloutArgs& a, const WarpMem& W, int n, const Pusher& pu, int s, int lane,
+                        Counters& cnt) {
+    const SimConst& C = a.C;
+    const int done = s < pu.moving ? s : pu.moving;
+    const float travel = (C.pspeed * C.dt) * (float)done;
+    const float Px = pu.sx + pu.dx * travel, Py = pu.sy + pu.dy * travel;
+    const float3 V = (pu.active && s < pu.moving) ? f3(pu.dx * C.pspeed, pu.dy * C.pspeed, 0.f) : f3(0.f, 0.f, 0.f);
+    for (int i = lane; i < n; i += 32) {
+        float4 v = W.bv[i];
+        v.x += C.gx * C.dt;
+        v.y += C.gy * C.dt;
+        v.z += C.gz * C.dt;
+        W.bv[i] = v;
+    }
+    frames_and_aabb(W, n, lane, C.margin);
+    __syncwarp();
+    bool ovf = broadphase(W, n, lane, C.pair_cap, pu.active, Px, Py, C);
+    NarrowStats st{0, 0, 0, 0, 0, 0};
+    ovf |= narrowphase(W, lane, C, Px, Py, st);
+    prepare(W, lane, C);
+    ovf |= colour_manifolds(W, n, lane);
+    const int visits = pgs(W, lane, C.iters, V);
+    integrate(W, n, lane, C.dt);
+    cnt.ev[EV_SUBSTEPS] += 1;
+    cnt.ev[EV_BOX_STEPS] += n;
+    cnt.ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
+    cnt.ev[EV_SAT] += st.sat;
+    cnt.ev[EV_FACE] += st.face;
+    cnt.ev[EV_EDGE] += st.edge;
+    cnt.ev[EV_PLANE] += st.plane;
+    cnt.ev[EV_PUSHER] += st.pusher;
+    cnt.ev[EV_POINTS] += W.scal[4];
+    cnt.ev[EV_MANIFOLDS] += W.scal[3];
+    cnt.ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal[6];
+    cnt.ev[EV_PGS_PTS] += __reduce_add_sync(0xffffffffu, visits);
+    cnt.ev[EV_CLIP_VERTS] += st.clip_verts;
+    cnt.ev[EV_COLOURS] += W.scal[5];
+    __syncwarp();
+    return ovf;
+}
+
+__device__ void run_env(const RolloutArgs& a, const WarpMem& W, int e, int lane) {
+    const SimConst& C = a.C;
+    const EnvIn ei = a.env[e];
+    EnvProg pg = a.prog[e];
+    if (pg.done) return;
+    const int n = ei.n;
+    load_env(a, W, ei, pg.k == 0, lane);
+    if (pg.k == 0) {
+        pg.k = 1;
+        pg.s = 0;
+        pg.push_ready = 0;
+    }
+    Counters cnt;
+    for (int k = 0; k < kNumEvents; k++) cnt.ev[k] = 0;
+    bool ovf = false;
+    int budget = a.max_substeps > 0 ? a.max_substeps : INT_MAX;
+    while (!pg.done && budget > 0) {
+        if (!pg.push_ready) {
+            compute_footprints(W, n, lane);
+            float push[4];
+            if (pg.k == 1) {
+                const float4 fp = a.first_push[e];
+                push[0] = fp.x; push[1] = fp.y; push[2] = fp.z; push[3] = fp.w;
+                if (start_blocked(W, n, lane, fp.x, fp.y, C.pr)) {
+                    pg.flags |= FLAG_INVALID_START;
+                    pg.done = 1;
+                    pg.cost = a.depth + 1;
+                    pg.reward = 0.f;
+                    break;
+                }
+                pg.noop = 0;
+            } else {
+                const int at = sample_push(W, n, lane, a.seeds[e], pg.k, C, push);
+                cnt.ev[EV_SAMPLE_ATTEMPTS] += at < 0 ? C.attempts : at + 1;
+                if (at < 0) {
+                    pg.noop = 1;
+                    pg.flags |= FLAG_NOOP;
+                    push[0] = push[1] = push[2] = push[3] = 0.f;
+                } else {
+                    pg.noop = 0;
+                }
+            }
+            for (int i = 0; i < 4; i++) pg.push[i] = push[i];
+            pg.push_ready = 1;
+        }
+        const Pusher pu = make_pusher(C, pg.push, pg.noop != 0);
+        while (pg.s < C.substeps && budget > 0) {
+            ovf |= substep(a, W, n, pu, pg.s, lane, cnt);
+            pg.s++;
+            pg.steps++;
+            budget--;
+        }
+        if (pg.s == C.substeps) {
+            cnt.ev[EV_PUSH_EVALS] += 1;
+            if (pg.k == 1 && a.child_on) store_state(W, n, a.child + (size_t)ei.box_off * 13, lane);
+            bool out = false;
+            for (int i = lane; i < n; i += 32)
+                out = out || fabsf(W.x[i]) > C.table_hx || fabsf(W.x[W.NB + i]) > C.table_hy;
+            out = __any_sync(0xffffffffu, out);
+            if (out) {
+                pg.flags |= FLAG_OUT_OF_WS;
+                pg.done = 1;
+                pg.cost = a.depth + 1;
+                pg.reward = 0.f;
+            } else {
+                compute_footprints(W, n, lane);
+                if (grasp_check(W, n, ei.target, lane, C)) {
+                    pg.done = 1;
+                    pg.cost = pg.k;
+                    pg.reward = powf(C.gamma, (float)(pg.k - 1));
+                    if (pg.k == 1) pg.flags |= FLAG_GRASP1;
+                } else if (pg.k >= a.depth) {
+                    pg.done = 1;
+                    pg.cost = a.depth + 1;
+                    pg.reward = 0.f;
+                } else {
+                    pg.k++;
+                    pg.s = 0;
+                    pg.push_ready = 0;
+                }
+            }
+        }
+    }
+    if (ovf) pg.flags |= FLAG_OVERFLOW;
+    store_state(W, n, a.state + (size_t)ei.box_off * 13, lane);
+    if (lane == 0) {
+        a.prog[e] = pg;
+        unsigned long long* ev = a.events + (size_t)e * kNumEvents;
+        for (int k = 0; k < kNumEvents; k++) ev[k] += cnt.ev[k];
+        a.steps[e] = pg.steps;
+        if (pg.done) {
+            a.cost[e] = pg.cost;
+            a.reward[e] = pg.reward;
+            a.flags[e] = (uint8_t)pg.flags;
+            atomicAdd(a.done_count, 1);
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) rollout_kernel(const __grid_constant__ RolloutArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    const WarpMem W = bind_mem(a.L, smem + (size_t)wib * a.L.bytes,
+                               a.gscratch + (size_t)gw * a.scratch_f4_per_warp);
+    for (;;) {
+        int slot = 0;
+        if (lane == 0) slot = atomicAdd(a.queue_head, 1);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= a.n_envs) break;
+        run_env(a, W, a.order[slot], lane);
+    }
+}
+
+// Batch set-up: per-env scene descriptor and box offset (block-wide scan), processing
+// order by descending box count (bucket sort), totals.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) prepare_batch_kernel(int n_envs, const int32_t* scene_ids,
+                                                             const SceneDesc* table, int table_cap, EnvIn* env,
+                                                             int* order, int* counters) {
+    __shared__ int hist[kMaxBoxes + 2];
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    const int t = threadIdx.x;
+    if (t < kMaxBoxes + 2) hist[t] = 0;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_envs; base += 1024) {
+        const int e = base + t;
+        int n = 0;
+        SceneDesc d{nullptr, 0, 0};
+        int sid = -1;
+        if (e < n_envs) {
+            sid = scene_ids[e];
+            if (sid >= 0 && sid < table_cap) d = table[sid];
+            if (d.n <= 0 || d.rec == nullptr) atomicOr(counters + 1, 1);
+            n = d.n > 0 ? d.n : 0;
+        }
+        // block exclusive scan of n
+        int v = n;
+        const int lane = t & 31, w = t >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) warp_sums[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            int s = warp_sums[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += u;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int excl = carry + (w ? warp_sums[w - 1] : 0) + v - n;
+        if (e < n_envs) {
+            env[e] = EnvIn{d.rec, n, d.target, excl, sid};
+            atomicAdd(&hist[kMaxBoxes - min(n, kMaxBoxes)], 1);
+        }
+        __syncthreads();
+        if (t == 0) carry += warp_sums[31];
+        __syncthreads();
+    }
+    if (t == 0) {
+        counters[0] = carry;
+        int acc = 0;
+        for (int b = 0; b <= kMaxBoxes; b++) {
+            const int c = hist[b];
+            hist[b] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < n_envs; e += 1024) {
+        const int b = kMaxBoxes - min(env[e].n, kMaxBoxes);
+        const int pos = atomicAdd(&hist[b], 1);
+        order[pos] = e;
+    }
+}
+
+// ------------------------------------------------------------------ snapshot evaluation
+struct EvalArgs {
+    SimConst C;
+    Layout L;
+    int n_envs, mode, k;
+    const int32_t* box_offset;
+    const float* states;
+    const float* half;
+    const float* pusher_xy;
+    const int32_t* target;
+    const uint64_t* seeds;
+    const float* starts;
+    int32_t* out_pairs;
+    int32_t* out_n_pairs;
+    int32_t* out_plane;
+    int32_t* out_n_plane;
+    int32_t* out_pusher;
+    int32_t* out_n_pusher;
+    uint8_t* out_u8;
+    float* out_push;
+    int32_t* out_attempt;
+};
+
+__global__ void __launch_bounds__(128) eval_kernel(const __grid_constant__ EvalArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const WarpMem W = bind_mem(a.L, smem + (size_t)wib * a.L.bytes, nullptr);
+    const int NB = W.NB;
+    for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < a.n_envs; e += nw) {
+        const int b0 = a.box_offset[e], n = a.box_offset[e + 1] - b0;
+        for (int i = lane; i < n; i += 32) {
+            const float* s = a.states + (size_t)(b0 + i) * 13;
+            const float* h = a.half + (size_t)(b0 + i) * 3;
+            W.x[i] = s[0]; W.x[NB + i] = s[1]; W.x[2 * NB + i] = s[2];
+            W.q[i] = s[3]; W.q[NB + i] = s[4]; W.q[2 * NB + i] = s[5]; W.q[3 * NB + i] = s[6];
+            W.h[i] = h[0]; W.h[NB + i] = h[1]; W.h[2 * NB + i] = h[2];
+            W.ib[i] = 1.f; W.ib[NB + i] = 1.f; W.ib[2 * NB + i] = 1.f;
+        }
+        __syncwarp();
+        if (a.mode == 0) {
+            frames_and_aabb(W, n, lane, a.C.margin);
+            __syncwarp();
+            const bool on = a.pusher_xy != nullptr;
+            const float px = on ? a.pusher_xy[2 * e] : 0.f, py = on ? a.pusher_xy[2 * e + 1] : 0.f;
+            broadphase(W, n, lane, a.C.pair_cap, on, px, py, a.C);
+            const int np = W.scal[0], npl = W.scal[1], npu = W.scal[2];
+            for (int k = lane; k < np; k += 32) {
+                a.out_pairs[((size_t)e * a.C.pair_cap + k) * 2] = W.pairs[k] & 255;
+                a.out_pairs[((size_t)e * a.C.pair_cap + k) * 2 + 1] = W.pairs[k] >> 8;
+            }
+            for (int k = lane; k < npl; k += 32) a.out_plane[b0 + k] = W.plane[k];
+            for (int k = lane; k < npu; k += 32) a.out_pusher[b0 + k] = W.pusher[k];
+            if (lane == 0) {
+                a.out_n_pairs[e] = np;
+                a.out_n_plane[e] = npl;
+                a.out_n_pusher[e] = npu;
+            }
+        } else {
+            compute_footprints(W, n, lane);
+            if (a.mode == 1) {
+                const bool g = grasp_check(W, n, a.target[e], lane, a.C);
+                if (lane == 0) a.out_u8[e] = g ? 1 : 0;
+            } else if (a.mode == 2) {
+                float push[4] = {0.f, 0.f, 0.f, 0.f};
+                const int at = sample_push(W, n, lane, a.seeds[e], a.k, a.C, push);
+                if (lane == 0) {
+                    a.out_attempt[e] = at;
+                    for (int i = 0; i < 4; i++) a.out_push[4 * e + i] = at < 0 ? 0.f : push[i];
+                }
+            } else {
+                const bool b = start_blocked(W, n, lane, a.starts[2 * e], a.starts[2 * e + 1], a.C.pr);
+                if (lane == 0) a.out_u8[e] = b ? 1 : 0;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ FP32 peak probe
+__global__ void __launch_bounds__(256) fma_peak_kernel(float* out, int iters, float seed) {
+    float a0 = seed + threadIdx.x, a1 = a0 + 1.f, a2 = a0 + 2.f, a3 = a0 + 3.f;
+    float a4 = a0 + 4.f, a5 = a0 + 5.f, a6 = a0 + 6.f, a7 = a0 + 7.f;
+    const float m = 0.999999f, c = 1e-7f;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+            a0 = fmaf(a0, m, c); a1 = fmaf(a1, m, c); a2 = fmaf(a2, m, c); a3 = fmaf(a3, m, c);
+            a4 = fmaf(a4, m, c); a5 = fmaf(a5, m, c); a6 = fmaf(a6, m, c); a7 = fmaf(a7, m, c);
+        }
+    }
+    const float s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (s == 12345.678f) out[blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------------ host side
+struct Arena {
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> bytes
+    size_t used = 0;
+    void init(char* b, size_t s) {
+        base = b;
+        size = s;
+        free_.clear();
+        free_[0] = s;
+        used = 0;
+    }
+    // first fit, 256-byte aligned; returns SIZE_MAX if full
+    size_t alloc(size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const size_t off = it->first, rem = it->second - bytes;
+                free_.erase(it);
+                if (rem) free_[off + bytes] = rem;
+                used += bytes;
+                return off;
+            }
+        }
+        return SIZE_MAX;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        used -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct SceneRec {
+    bool live = false;
+    size_t off = 0, bytes = 0;
+    int n = 0, target = 0;
+    int uses = 0;                 // batches referencing it (host-submitted ids only)
+    std::vector<float> host;      // records, kRecFloats per box
+};
+
+struct Batch {
+    int n_envs = 0, depth = 0, nb = 0;
+    size_t state_boxes = 0;
+    bool host_ids = false;
+    std::vector<int> scene_ids;   // for use counts (host submissions)
+    size_t off = 0, bytes = 0;
+    EnvIn* env = nullptr;
+    int* order = nullptr;
+    int* counters = nullptr;      // [0] total boxes, [1] bad id, [2] queue head, [3] done count
+    float4* first_push = nullptr;
+    uint64_t* seeds = nullptr;
+    int32_t* ids = nullptr;
+    EnvProg* prog = nullptr;
+    float* state = nullptr;
+    float* child = nullptr;
+    int32_t* cost = nullptr;
+    float* reward = nullptr;
+    uint8_t* flags = nullptr;
+    int32_t* steps = nullptr;
+    unsigned long long* events = nullptr;
+    bool finished = false;
+    int wpb = 4, Ms = 0, Ps = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+}  // namespace
+
+struct pmbs_ctx {
+    pmbs_config cfg;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    bool own_arena = false;
+    Arena arena;
+    std::vector<SceneRec> scenes;
+    std::vector<int> free_ids;
+    SceneDesc* d_table = nullptr;
+    size_t table_off = 0;
+    std::map<int64_t, Batch> batches;
+    int64_t next_batch = 1;
+    std::string err;
+    std::mutex mu;
+    float4* gscratch = nullptr;
+    size_t gscratch_off = 0, gscratch_bytes = 0;
+    int fixed_wpb = 0, fixed_Ps = -1, fixed_Ms = -1;
+    SimConst C;
+};
+
+namespace {
+
+pmbs_status fail(pmbs_ctx* c, pmbs_status s, const std::string& m) {
+    c->err = m;
+    return s;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, PMBS_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void fill_const(const pmbs_config& c, SimConst& C) {
+    C.dt = c.dt;
+    C.gx = c.gravity[0];
+    C.gy = c.gravity[1];
+    C.gz = c.gravity[2];
+    C.table_hx = c.table_half[0];
+    C.table_hy = c.table_half[1];
+    C.table_mu = c.table_mu;
+    C.pusher_mu = c.pusher_mu;
+    C.pr = c.pusher_radius;
+    C.pz0 = c.pusher_z0;
+    C.pz1 = c.pusher_z1;
+    C.pspeed = c.pusher_speed;
+    C.plen = c.push_length;
+    C.gamma = c.gamma;
+    C.grasp_W = c.grasp_opening;
+    C.grasp_c = c.grasp_clearance;
+    C.grasp_f = c.finger_depth;
+    C.grasp_fw = c.finger_width;
+    C.margin = c.margin;
+    C.slop = c.slop;
+    C.baumgarte = c.baumgarte;
+    C.sample_clear = c.sample_clearance;
+    C.substeps = c.substeps_per_push;
+    C.iters = c.pgs_iters;
+    C.grasp_K = c.grasp_angles;
+    C.attempts = c.sample_attempts;
+    C.npts = c.contour_points;
+    C.Pcap = c.contact_cap;
+    C.Mcap = c.manifold_cap;
+    C.pair_cap = c.pair_cap;
+    for (int k = 0; k < 32; k++) {
+        const double th = k < c.grasp_angles ? k * M_PI / c.grasp_angles : 0.0;
+        C.gcos[k] = (float)std::cos(th);
+        C.gsin[k] = (float)std::sin(th);
+    }
+}
+
+bool finite(float x) { return std::isfinite(x); }
+
+void* arena_ptr(pmbs_ctx* ctx, size_t off) { return ctx->arena.base + off; }
+
+// Launch shape for environments of up to nb boxes: warps per block and shared-memory
+// contact capacities.  Heuristic default: about 18 KB of shared memory per warp.
+void choose_shape(pmbs_ctx* ctx, int nb, int& wpb, int& Ms, int& Ps) {
+    const pmbs_config& c = ctx->cfg;
+    const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
+    wpb = ctx->fixed_wpb > 0 ? ctx->fixed_wpb : (c.warps_per_block > 0 ? c.warps_per_block : 4);
+    const int base = make_layout(nb, pairS, 0, 0, c.manifold_cap).bytes;
+    int target = 18 * 1024;
+    int rem = std::max(0, target - base);
+    int ms = rem / (48 + 3 * 64);
+    int ps = 3 * ms;
+    if (c.smem_points >= 0) ps = c.smem_points;
+    if (c.smem_manifolds >= 0) ms = c.smem_manifolds;
+    if (ctx->fixed_Ps >= 0) ps = ctx->fixed_Ps;
+    if (ctx->fixed_Ms >= 0) ms = ctx->fixed_Ms;
+    Ps = std::min(ps, c.contact_cap);
+    Ms = std::min(ms, c.manifold_cap);
+    // keep one block within the 227 KB opt-in limit
+    while (wpb > 1 && (size_t)wpb * make_layout(nb, pairS, Ms, Ps, c.manifold_cap).bytes > 227 * 1024) wpb >>= 1;
+    while ((size_t)make_layout(nb, pairS, Ms, Ps, c.manifold_cap).bytes > 227 * 1024 && (Ps > 0 || Ms > 0)) {
+        Ps /= 2;
+        Ms /= 2;
+    }
+}
+
+pmbs_status ensure_scratch(pmbs_ctx* ctx, size_t warps) {
+    const size_t per = (size_t)(3 * ctx->cfg.manifold_cap + 4 * ctx->cfg.contact_cap) * sizeof(float4);
+    const size_t need = warps * per;
+    if (need <= ctx->gscratch_bytes) return PMBS_OK;
+    if (ctx->gscratch) ctx->arena.release(ctx->gscratch_off, ctx->gscratch_bytes);
+    ctx->gscratch = nullptr;
+    ctx->gscratch_bytes = 0;
+    const size_t off = ctx->arena.alloc(need);
+    if (off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "solver scratch does not fit in the arena");
+    ctx->gscratch_off = off;
+    ctx->gscratch_bytes = need;
+    ctx->gscratch = (float4*)arena_ptr(ctx, off);
+    return PMBS_OK;
+}
+
+pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, size_t arena_bytes, pmbs_ctx** out) {
+    if (!cfg || !out) return PMBS_E_INVALID;
+    *out = nullptr;
+    const pmbs_config& c = *cfg;
+    if (c.max_boxes_per_env < 1 || c.max_boxes_per_env > kMaxBoxes || c.max_envs < 0 || c.substeps_per_push < 1 ||
+        c.pgs_iters < 0 || !(c.dt > 0) || c.grasp_angles < 1 || c.grasp_angles > 32 || c.sample_attempts < 1 ||
+        c.sample_attempts > 32 || c.contour_points < 1 || c.contact_cap < 4 || c.manifold_cap < 1 ||
+        c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096 || !(c.pusher_speed > 0) ||
+        !(c.pusher_radius > 0))
+        return PMBS_E_INVALID;
+    pmbs_ctx* ctx = new pmbs_ctx();
+    ctx->cfg = c;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->device = c.device;
+    fill_const(c, ctx->C);
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return PMBS_E_CUDA;
+    }
+    char* base = (char*)d_arena;
+    size_t bytes = arena_bytes;
+    if (!base) {
+        bytes = c.mem_budget_bytes;
+        if (bytes < (size_t)64 << 20) bytes = (size_t)64 << 20;
+        e = cudaMalloc((void**)&base, bytes);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return PMBS_E_OOM;
+        }
+        ctx->own_arena = true;
+    } else if (((uintptr_t)base & 255) != 0) {
+        delete ctx;
+        return PMBS_E_INVALID;
+    }
+    ctx->arena.init(base, bytes);
+    ctx->table_off = ctx->arena.alloc(sizeof(SceneDesc) * kSceneTableCap);
+    if (ctx->table_off == SIZE_MAX) {
+        if (ctx->own_arena) cudaFree(base);
+        delete ctx;
+        return PMBS_E_OOM;
+    }
+    ctx->d_table = (SceneDesc*)(base + ctx->table_off);
+    e = cudaMemsetAsync(ctx->d_table, 0, sizeof(SceneDesc) * kSceneTableCap, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) {
+        if (ctx->own_arena) cudaFree(base);
+        delete ctx;
+        return PMBS_E_CUDA;
+    }
+    *out = ctx;
+    return PMBS_OK;
+}
+
+void release_batch_mem(pmbs_ctx* ctx, Batch& b) {
+    if (b.graph) cudaGraphExecDestroy(b.graph);
+    b.graph = nullptr;
+    if (b.bytes) ctx->arena.release(b.off, b.bytes);
+    b.bytes = 0;
+    for (int s : b.scene_ids)
+        if (s >= 0 && s < (int)ctx->scenes.size()) ctx->scenes[s].uses--;
+    b.scene_ids.clear();
+}
+
+pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push, int depth,
+                           const uint64_t* seeds, bool device_ptrs, int64_t* out_batch) {
+    const pmbs_config& c = ctx->cfg;
+    if (!out_batch || n_envs < 0 || n_envs > c.max_envs || depth < 1 || depth > 64)
+        return fail(ctx, PMBS_E_INVALID, "bad batch size or depth");
+    if (n_envs > 0 && (!scene_ids || !first_push || (!seeds && depth > 1)))
+        return fail(ctx, PMBS_E_INVALID, "missing input array");
+    Batch b;
+    b.n_envs = n_envs;
+    b.depth = depth;
+    b.host_ids = !device_ptrs;
+    size_t boxes = 0;
+    int nb = 1;
+    if (!device_ptrs) {
+        for (int e = 0; e < n_envs; e++) {
+            const int s = scene_ids[e];
+            if (s < 0 || s >= (int)ctx->scenes.size() || !ctx->scenes[s].live)
+                return fail(ctx, PMBS_E_INVALID, "unknown scene id " + std::to_string(s));
+            boxes += ctx->scenes[s].n;
+            nb = std::max(nb, ctx->scenes[s].n);
+            const float* p = first_push + 4 * e;
+            if (!finite(p[0]) || !finite(p[1]) || !finite(p[2]) || !finite(p[3]))
+                return fail(ctx, PMBS_E_INVALID, "non-finite push");
+        }
+    } else {
+        for (const SceneRec& r : ctx->scenes)
+            if (r.live) nb = std::max(nb, r.n);
+        boxes = (size_t)n_envs * nb;
+    }
+    b.nb = nb;
+    b.state_boxes = boxes;
+    const size_t ne = (size_t)std::max(n_envs, 1);
+    size_t sz = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = sz;
+        sz += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_env = take(sizeof(EnvIn) * ne), o_order = take(sizeof(int) * ne), o_cnt = take(sizeof(int) * 8),
+                 o_fp = take(sizeof(float4) * ne), o_seed = take(sizeof(uint64_t) * ne),
+                 o_ids = take(sizeof(int32_t) * ne), o_prog = take(sizeof(EnvProg) * ne),
+                 o_state = take(sizeof(float) * 13 * std::max(boxes, (size_t)1)),
+                 o_child = take(sizeof(float) * 13 * std::max(boxes, (size_t)1)), o_cost = take(sizeof(int32_t) * ne),
+                 o_rew = take(sizeof(float) * ne), o_flags = take(ne), o_steps = take(sizeof(int32_t) * ne),
+                 o_ev = take(sizeof(unsigned long long) * kNumEvents * ne);
+    b.off = ctx->arena.alloc(sz);
+    if (b.off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "batch does not fit in the device arena");
+    b.bytes = sz;
+    char* base = (char*)arena_ptr(ctx, b.off);
+    b.env = (EnvIn*)(base + o_env);
+    b.order = (int*)(base + o_order);
+    b.counters = (int*)(base + o_cnt);
+    b.first_push = (float4*)(base + o_fp);
+    b.seeds = (uint64_t*)(base + o_seed);
+    b.ids = (int32_t*)(base + o_ids);
+    b.prog = (EnvProg*)(base + o_prog);
+    b.state = (float*)(base + o_state);
+    b.child = (float*)(base + o_child);
+    b.cost = (int32_t*)(base + o_cost);
+    b.reward = (float*)(base + o_rew);
+    b.flags = (uint8_t*)(base + o_flags);
+    b.steps = (int32_t*)(base + o_steps);
+    b.events = (unsigned long long*)(base + o_ev);
+    auto bail = [&](const char* what, cudaError_t e) {
+        ctx->arena.release(b.off, b.bytes);
+        return fail(ctx, PMBS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaMemsetAsync(base + o_cnt, 0, sizeof(int) * 8, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.prog, 0, sizeof(EnvProg) * ne, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.events, 0, sizeof(unsigned long long) * kNumEvents * ne, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.steps, 0, sizeof(int32_t) * ne, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.seeds, 0, sizeof(uint64_t) * ne, ctx->stream);
+    if (n_envs > 0 && e == cudaSuccess) {
+        const cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        e = cudaMemcpyAsync(b.ids, scene_ids, sizeof(int32_t) * n_envs, k, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b.first_push, first_push, sizeof(float4) * n_envs, k, ctx->stream);
+        if (e == cudaSuccess && seeds) e = cudaMemcpyAsync(b.seeds, seeds, sizeof(uint64_t) * n_envs, k, ctx->stream);
+        if (e == cudaSuccess) {
+            prepare_batch_kernel<<<1, 1024, 0, ctx->stream>>>(n_envs, b.ids, ctx->d_table, kSceneTableCap, b.env,
+                                                              b.order, b.counters);
+            e = cudaGetLastError();
+        }
+        // host-submitted ids: the copies read pageable memory, so wait for them here
+        if (e == cudaSuccess && !device_ptrs) e = cudaStreamSynchronize(ctx->stream);
+    }
+    if (e != cudaSuccess) return bail("batch set-up", e);
+    if (!device_ptrs) {
+        b.scene_ids.assign(scene_ids, scene_ids + n_envs);
+        for (int s : b.scene_ids) ctx->scenes[s].uses++;
+    }
+    b.finished = n_envs == 0;
+    choose_shape(ctx, nb, b.wpb, b.Ms, b.Ps);
+    const int64_t id = ctx->next_batch++;
+    ctx->batches[id] = b;
+    *out_batch = id;
+    return PMBS_OK;
+}
+
+pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps) {
+    const pmbs_config& c = ctx->cfg;
+    const int nb = b.nb;
+    const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
+    const Layout L = make_layout(nb, pairS, b.Ms, b.Ps, c.manifold_cap);
+    const int threads = 32 * b.wpb;
+    const size_t smem = (size_t)L.bytes * b.wpb;
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel, threads, smem));
+    if (per_sm < 1) return fail(ctx, PMBS_E_INVALID, "launch shape does not fit on an SM");
+    per_sm = std::min(per_sm, kMaxWarpsPerSM / b.wpb);
+    const int blocks = std::max(1, std::min((b.n_envs + b.wpb - 1) / b.wpb, per_sm * ctx->num_sms));
+    const pmbs_status st = ensure_scratch(ctx, (size_t)blocks * b.wpb);
+    if (st != PMBS_OK) return st;
+    RolloutArgs a;
+    a.C = ctx->C;
+    a.L = L;
+    a.n_envs = b.n_envs;
+    a.depth = b.depth;
+    a.max_substeps = max_substeps;
+    a.child_on = 1;
+    a.env = b.env;
+    a.order = b.order;
+    a.queue_head = b.counters + 2;
+    a.done_count = b.counters + 3;
+    a.first_push = b.first_push;
+    a.seeds = b.seeds;
+    a.prog = b.prog;
+    a.state = b.state;
+    a.child = b.child;
+    a.cost = b.cost;
+    a.reward = b.reward;
+    a.flags = b.flags;
+    a.steps = b.steps;
+    a.events = b.events;
+    a.gscratch = ctx->gscratch;
+    a.scratch_f4_per_warp = 3 * c.manifold_cap + 4 * c.contact_cap;
+    CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), ctx->stream));
+    rollout_kernel<<<blocks, threads, smem, ctx->stream>>>(a);
+    CU(cudaGetLastError());
+    return PMBS_OK;
+}
+
+Batch* find_batch(pmbs_ctx* ctx, int64_t id) {
+    auto it = ctx->batches.find(id);
+    return it == ctx->batches.end() ? nullptr : &it->second;
+}
+
+pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offset, const float* rec_host,
+                            const int32_t* target, int32_t* out_ids) {
+    const int total = box_offset[n_scenes] - box_offset[0];
+    const size_t bytes = sizeof(float) * kRecFloats * std::max(total, 1);
+    // one arena block per scene keeps freeing simple
+    std::vector<int> ids(n_scenes);
+    for (int s = 0; s < n_scenes; s++) {
+        int id;
+        if (!ctx->free_ids.empty()) {
+            id = ctx->free_ids.back();
+            ctx->free_ids.pop_back();
+        } else {
+            id = (int)ctx->scenes.size();
+            if (id >= kSceneTableCap) return fail(ctx, PMBS_E_OOM, "scene table full");
+            ctx->scenes.emplace_back();
+        }
+        ids[s] = id;
+        SceneRec& r = ctx->scenes[id];
+        r.n = box_offset[s + 1] - box_offset[s];
+        r.target = target[s];
+        r.bytes = sizeof(float) * kRecFloats * r.n;
+        r.off = ctx->arena.alloc(r.bytes);
+        if (r.off == SIZE_MAX) {
+            ctx->free_ids.push_back(id);
+            for (int t = 0; t < s; t++) {
+                SceneRec& q = ctx->scenes[ids[t]];
+                ctx->arena.release(q.off, q.bytes);
+                q.live = false;
+                ctx->free_ids.push_back(ids[t]);
+            }
+            return fail(ctx, PMBS_E_OOM, "scene store is full");
+        }
+        r.host.assign(rec_host + (size_t)kRecFloats * (box_offset[s] - box_offset[0]),
+                      rec_host + (size_t)kRecFloats * (box_offset[s + 1] - box_offset[0]));
+        r.live = true;
+        r.uses = 0;
+    }
+    (void)bytes;
+    std::vector<SceneDesc> desc(n_scenes);
+    for (int s = 0; s < n_scenes; s++) {
+        SceneRec& r = ctx->scenes[ids[s]];
+        float* dptr = (float*)arena_ptr(ctx, r.off);
+        CU(cudaMemcpyAsync(dptr, r.host.data(), r.bytes, cudaMemcpyHostToDevice, ctx->stream));
+        desc[s] = SceneDesc{dptr, r.n, r.target};
+    }
+    for (int s = 0; s < n_scenes; s++)
+        CU(cudaMemcpyAsync(ctx->d_table + ids[s], &desc[s], sizeof(SceneDesc), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int s = 0; s < n_scenes; s++) out_ids[s] = ids[s];
+    return PMBS_OK;
+}
+
+pmbs_status eval_common(pmbs_ctx* ctx, int mode, int n_envs, const int32_t* box_offset, const float* states,
+                        const float* half, const float* pusher_xy, const int32_t* target, const uint64_t* seeds,
+                        int k, const float* starts, int32_t* out_pairs, int32_t* out_n_pairs, int32_t* out_plane,
+                        int32_t* out_n_plane, int32_t* out_pusher, int32_t* out_n_pusher, uint8_t* out_u8,
+                        float* out_push, int32_t* out_attempt) {
+    if (n_envs < 0 || !box_offset || !states || !half) return fail(ctx, PMBS_E_INVALID, "bad arguments");
+    if (n_envs == 0) return PMBS_OK;
+    int nb = 1;
+    for (int e = 0; e < n_envs; e++) {
+        const int n = box_offset[e + 1] - box_offset[e];
+        if (n < 1 || n > kMaxBoxes) return fail(ctx, PMBS_E_INVALID, "box count out of range");
+        nb = std::max(nb, n);
+    }
+    const int B = box_offset[n_envs] - box_offset[0];
+    const pmbs_config& c = ctx->cfg;
+    std::vector<int32_t> off(box_offset, box_offset + n_envs + 1);
+    for (auto& o : off) o -= box_offset[0];
+    // device staging in one arena block
+    size_t sz = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = sz;
+        sz += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_off = take(sizeof(int32_t) * (n_envs + 1)), o_st = take(sizeof(float) * 13 * B),
+                 o_h = take(sizeof(float) * 3 * B), o_pxy = take(sizeof(float) * 2 * n_envs),
+                 o_t = take(sizeof(int32_t) * n_envs), o_seed = take(sizeof(uint64_t) * n_envs),
+                 o_st2 = take(sizeof(float) * 2 * n_envs),
+                 o_pairs = take(sizeof(int32_t) * 2 * (size_t)c.pair_cap * n_envs),
+                 o_np = take(sizeof(int32_t) * 3 * n_envs), o_pl = take(sizeof(int32_t) * 2 * B),
+                 o_u8 = take(n_envs), o_push = take(sizeof(float) * 4 * n_envs), o_at = take(sizeof(int32_t) * n_envs);
+    const size_t boff = ctx->arena.alloc(sz);
+    if (boff == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "evaluation staging does not fit");
+    char* base = (char*)arena_ptr(ctx, boff);
+    auto h2d = [&](size_t o, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    };
+    cudaError_t e = h2d(o_off, off.data(), sizeof(int32_t) * (n_envs + 1));
+    if (e == cudaSuccess) e = h2d(o_st, states, sizeof(float) * 13 * B);
+    if (e == cudaSuccess) e = h2d(o_h, half, sizeof(float) * 3 * B);
+    if (e == cudaSuccess && pusher_xy) e = h2d(o_pxy, pusher_xy, sizeof(float) * 2 * n_envs);
+    if (e == cudaSuccess && target) e = h2d(o_t, target, sizeof(int32_t) * n_envs);
+    if (e == cudaSuccess && seeds) e = h2d(o_seed, seeds, sizeof(uint64_t) * n_envs);
+    if (e == cudaSuccess && starts) e = h2d(o_st2, starts, sizeof(float) * 2 * n_envs);
+    EvalArgs a;
+    a.C = ctx->C;
+    a.L = make_layout(nb, c.pair_cap, 0, 0, 1);
+    a.n_envs = n_envs;
+    a.mode = mode;
+    a.k = k;
+    a.box_offset = (int32_t*)(base + o_off);
+    a.states = (float*)(base + o_st);
+    a.half = (float*)(base + o_h);
+    a.pusher_xy = pusher_xy ? (float*)(base + o_pxy) : nullptr;
+    a.target = (int32_t*)(base + o_t);
+    a.seeds = (uint64_t*)(base + o_seed);
+    a.starts = (float*)(base + o_st2);
+    a.out_pairs = (int32_t*)(base + o_pairs);
+    a.out_n_pairs = (int32_t*)(base + o_np);
+    a.out_n_plane = a.out_n_pairs + n_envs;
+    a.out_n_pusher = a.out_n_pairs + 2 * n_envs;
+    a.out_plane = (int32_t*)(base + o_pl);
+    a.out_pusher = a.out_plane + B;
+    a.out_u8 = (uint8_t*)(base + o_u8);
+    a.out_push = (float*)(base + o_push);
+    a.out_attempt = (int32_t*)(base + o_at);
+    if (e == cudaSuccess) {
+        const int wpb = 4;
+        const int blocks = std::min((n_envs + wpb - 1) / wpb, 4 * ctx->num_sms);
+        eval_kernel<<<blocks, 32 * wpb, (size_t)a.L.bytes * wpb, ctx->stream>>>(a);
+        e = cudaGetLastError();
+    }
+    auto d2h = [&](void* dst, size_t o, size_t bytes) {
+        return cudaMemcpyAsync(dst, base + o, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    };
+    if (e == cudaSuccess && mode == 0) {
+        if (out_pairs) e = d2h(out_pairs, o_pairs, sizeof(int32_t) * 2 * (size_t)c.pair_cap * n_envs);
+        if (e == cudaSuccess && out_n_pairs) e = d2h(out_n_pairs, o_np, sizeof(int32_t) * n_envs);
+        if (e == cudaSuccess && out_n_plane) e = d2h(out_n_plane, o_np + sizeof(int32_t) * n_envs, sizeof(int32_t) * n_envs);
+        if (e == cudaSuccess && out_n_pusher)
+            e = d2h(out_n_pusher, o_np + 2 * sizeof(int32_t) * n_envs, sizeof(int32_t) * n_envs);
+        if (e == cudaSuccess && out_plane) e = d2h(out_plane, o_pl, sizeof(int32_t) * B);
+        if (e == cudaSuccess && out_pusher) e = d2h(out_pusher, o_pl + sizeof(int32_t) * B, sizeof(int32_t) * B);
+    } else if (e == cudaSuccess && (mode == 1 || mode == 3)) {
+        if (out_u8) e = d2h(out_u8, o_u8, n_envs);
+    } else if (e == cudaSuccess && mode == 2) {
+        if (out_push) e = d2h(out_push, o_push, sizeof(float) * 4 * n_envs);
+        if (e == cudaSuccess && out_attempt) e = d2h(out_attempt, o_at, sizeof(int32_t) * n_envs);
+    }
+    const cudaError_t es = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = es;
+    ctx->arena.release(boff, sz);
+    if (e != cudaSuccess) return fail(ctx, PMBS_E_CUDA, std::string("evaluation: ") + cudaGetErrorString(e));
+    return PMBS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void pmbs_default_config(pmbs_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->device = 0;
+    c->max_envs = 1 << 16;
+    c->max_boxes_per_env = 64;
+    c->mem_budget_bytes = (size_t)4 << 30;
+    c->dt = 1.f / 240.f;
+    c->substeps_per_push = 240;
+    c->pgs_iters = 10;
+    c->gravity[0] = 0.f;
+    c->gravity[1] = 0.f;
+    c->gravity[2] = -9.81f;
+    c->table_half[0] = 0.2f;
+    c->table_half[1] = 0.2f;
+    c->table_mu = 0.5f;
+    c->pusher_mu = 0.5f;
+    c->pusher_radius = 0.01f;
+    c->pusher_z0 = 0.01f;
+    c->pusher_z1 = 0.20f;
+    c->pusher_speed = 0.1f;
+    c->push_length = 0.1f;
+    c->gamma = 0.8f;
+    c->grasp_opening = 0.085f;
+    c->grasp_clearance = 0.002f;
+    c->finger_depth = 0.01f;
+    c->finger_width = 0.022f;
+    c->grasp_angles = 16;
+    c->margin = 1e-3f;
+    c->slop = 5e-4f;
+    c->baumgarte = 0.2f;
+    c->sample_clearance = 0.005f;
+    c->sample_attempts = 8;
+    c->contour_points = 16;
+    c->contact_cap = 512;
+    c->manifold_cap = 256;
+    c->pair_cap = 1024;
+    c->warps_per_block = 0;
+    c->smem_points = -1;
+    c->smem_manifolds = -1;
+}
+
+pmbs_status pmbs_create(const pmbs_config* cfg, void* cuda_stream, pmbs_ctx** out) {
+    return create_common(cfg, cuda_stream, nullptr, 0, out);
+}
+
+pmbs_status pmbs_create_with_arena(const pmbs_config* cfg, void* cuda_stream, void* d_arena, size_t arena_bytes,
+                                   pmbs_ctx** out) {
+    if (!d_arena || arena_bytes < ((size_t)32 << 20)) return PMBS_E_INVALID;
+    return create_common(cfg, cuda_stream, d_arena, arena_bytes, out);
+}
+
+void pmbs_destroy(pmbs_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->batches)
+        if (kv.second.graph) cudaGraphExecDestroy(kv.second.graph);
+    if (ctx->own_arena && ctx->arena.base) cudaFree(ctx->arena.base);
+    delete ctx;
+}
+
+const char* pmbs_last_error(const pmbs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pmbs_status pmbs_load_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offset, const float* pose,
+                             const float* vel, const float* half_ext, const float* mass, const float* mu,
+                             const int32_t* target, int32_t* out_scene_ids) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n_scenes < 0 || (n_scenes > 0 && (!box_offset || !pose || !half_ext || !mass || !mu || !target || !out_scene_ids)))
+        return fail(ctx, PMBS_E_INVALID, "missing scene array");
+    if (n_scenes == 0) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    const int b0 = box_offset[0];
+    for (int s = 0; s < n_scenes; s++) {
+        const int n = box_offset[s + 1] - box_offset[s];
+        if (n < 1 || n > ctx->cfg.max_boxes_per_env)
+            return fail(ctx, PMBS_E_INVALID, "scene " + std::to_string(s) + " has " + std::to_string(n) + " boxes");
+        if (target[s] < 0 || target[s] >= n) return fail(ctx, PMBS_E_INVALID, "target out of range");
+    }
+    const int total = box_offset[n_scenes] - b0;
+    std::vector<float> rec((size_t)kRecFloats * total);
+    for (int i = 0; i < total; i++) {
+        const float* p = pose + 7 * (size_t)(b0 + i);
+        const float* h = half_ext + 3 * (size_t)(b0 + i);
+        float* r = rec.data() + (size_t)kRecFloats * i;
+        for (int k = 0; k < 7; k++) r[k] = p[k];
+        for (int k = 0; k < 6; k++) r[7 + k] = vel ? vel[6 * (size_t)(b0 + i) + k] : 0.f;
+        r[13] = h[0];
+        r[14] = h[1];
+        r[15] = h[2];
+        r[16] = mass[b0 + i];
+        r[17] = mu[b0 + i];
+        for (int k = 0; k < kRecFloats; k++)
+            if (!finite(r[k])) return fail(ctx, PMBS_E_INVALID, "non-finite scene value");
+        const double qn = std::sqrt((double)r[3] * r[3] + (double)r[4] * r[4] + (double)r[5] * r[5] + (double)r[6] * r[6]);
+        if (std::fabs(qn - 1.0) > 1e-3) return fail(ctx, PMBS_E_INVALID, "quaternion is not unit length");
+        if (!(h[0] > 0 && h[1] > 0 && h[2] > 0) || !(r[16] > 0) || !(r[17] >= 0))
+            return fail(ctx, PMBS_E_INVALID, "non-positive half extent or mass, or negative friction");
+    }
+    return register_scenes(ctx, n_scenes, box_offset, rec.data(), target, out_scene_ids);
+}
+
+pmbs_status pmbs_free_scenes(pmbs_ctx* ctx, int n, const int32_t* scene_ids) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && !scene_ids)) return fail(ctx, PMBS_E_INVALID, "bad arguments");
+    for (int i = 0; i < n; i++) {
+        const int s = scene_ids[i];
+        if (s < 0 || s >= (int)ctx->scenes.size() || !ctx->scenes[s].live)
+            return fail(ctx, PMBS_E_INVALID, "unknown scene id " + std::to_string(s));
+        if (ctx->scenes[s].uses > 0) return fail(ctx, PMBS_E_BUSY, "scene in use by a batch");
+    }
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n; i++) {
+        SceneRec& r = ctx->scenes[scene_ids[i]];
+        if (!r.live) continue;
+        ctx->arena.release(r.off, r.bytes);
+        r.live = false;
+        r.host.clear();
+        const SceneDesc z{nullptr, 0, 0};
+        CU(cudaMemcpyAsync(ctx->d_table + scene_ids[i], &z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream));
+        ctx->free_ids.push_back(scene_ids[i]);
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_rollout_pushes(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push,
+                                int depth, const uint64_t* seeds, int64_t* out_batch) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    CU(cudaSetDevice(ctx->device));
+    return rollout_common(ctx, n_envs, scene_ids, first_push, depth, seeds, false, out_batch);
+}
+
+pmbs_status pmbs_rollout_pushes_device(pmbs_ctx* ctx, int n_envs, const int32_t* d_scene_ids,
+                                       const float* d_first_push, int depth, const uint64_t* d_seeds,
+                                       int64_t* out_batch) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    CU(cudaSetDevice(ctx->device));
+    return rollout_common(ctx, n_envs, d_scene_ids, d_first_push, depth, d_seeds, true, out_batch);
+}
+
+pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    if (b->finished) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    const pmbs_status st = launch_rollout(ctx, *b, max_substeps);
+    if (st != PMBS_OK) return st;
+    if (max_substeps <= 0) {
+        b->finished = true;
+        return PMBS_OK;
+    }
+    int done = 0;
+    CU(cudaMemcpyAsync(&done, b->counters + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (done >= b->n_envs) {
+        b->finished = true;
+        return PMBS_OK;
+    }
+    return PMBS_E_NOT_READY;
+}
+
+pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, float* out_reward, uint8_t* out_flags,
+                            float* out_child_states, int32_t* out_child_scene_ids) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (!b->finished) return fail(ctx, PMBS_E_NOT_READY, "batch not finished");
+    const int n = b->n_envs;
+    if (n == 0) return PMBS_OK;
+    if (out_cost) CU(cudaMemcpyAsync(out_cost, b->cost, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out_reward) CU(cudaMemcpyAsync(out_reward, b->reward, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out_flags) CU(cudaMemcpyAsync(out_flags, b->flags, n, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<float> child;
+    std::vector<EnvIn> env;
+    if (out_child_states || out_child_scene_ids) {
+        env.resize(n);
+        CU(cudaMemcpyAsync(env.data(), b->env, sizeof(EnvIn) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        int total = 0;
+        for (const EnvIn& e : env) total += e.n;
+        child.resize((size_t)13 * std::max(total, 1));
+        CU(cudaMemcpyAsync(child.data(), b->child, sizeof(float) * 13 * total, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (out_child_states && !child.empty()) std::memcpy(out_child_states, child.data(), sizeof(float) * (child.size()));
+    if (out_child_scene_ids) {
+        // register each env's state after push 1 as a new scene (statics from the parent)
+        std::vector<int32_t> off(n + 1, 0), tgt(n);
+        for (int e = 0; e < n; e++) {
+            off[e + 1] = off[e] + env[e].n;
+            tgt[e] = env[e].target;
+        }
+        std::vector<float> rec((size_t)kRecFloats * off[n]);
+        for (int e = 0; e < n; e++) {
+            const SceneRec* parent = (env[e].scene >= 0 && env[e].scene < (int)ctx->scenes.size())
+                                         ? &ctx->scenes[env[e].scene] : nullptr;
+            for (int i = 0; i < env[e].n; i++) {
+                float* r = rec.data() + (size_t)kRecFloats * (off[e] + i);
+                const float* s = child.data() + (size_t)13 * (env[e].box_off + i);
+                for (int k = 0; k < 13; k++) r[k] = s[k];
+                for (int k = 13; k < kRecFloats; k++)
+                    r[k] = (parent && parent->live) ? parent->host[(size_t)kRecFloats * i + k] : 1.f;
+            }
+        }
+        const pmbs_status st = register_scenes(ctx, n, off.data(), rec.data(), tgt.data(), out_child_scene_ids);
+        if (st != PMBS_OK) return st;
+    }
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_query_cost_device(pmbs_ctx* ctx, int64_t batch, int32_t* d_cost, float* d_reward, uint8_t* d_flags) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    if (!b->finished) return fail(ctx, PMBS_E_NOT_READY, "batch not finished");
+    const int n = b->n_envs;
+    if (n == 0) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    if (d_cost) CU(cudaMemcpyAsync(d_cost, b->cost, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (d_reward) CU(cudaMemcpyAsync(d_reward, b->reward, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (d_flags) CU(cudaMemcpyAsync(d_flags, b->flags, n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_query_states(pmbs_ctx* ctx, int64_t batch, float* out_states, int32_t* out_env_steps) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    CU(cudaSetDevice(ctx->device));
+    const int n = b->n_envs;
+    if (n == 0) return PMBS_OK;
+    int total = 0;
+    CU(cudaMemcpyAsync(&total, b->counters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    // environments that have not started yet still hold their scene's initial state
+    std::vector<EnvProg> prog(n);
+    std::vector<EnvIn> env(n);
+    CU(cudaMemcpyAsync(prog.data(), b->prog, sizeof(EnvProg) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(env.data(), b->env, sizeof(EnvIn) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out_env_steps) CU(cudaMemcpyAsync(out_env_steps, b->steps, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out_states) CU(cudaMemcpyAsync(out_states, b->state, sizeof(float) * 13 * total, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (out_states) {
+        for (int e = 0; e < n; e++) {
+            if (prog[e].k != 0) continue;
+            const SceneRec* r = (env[e].scene >= 0 && env[e].scene < (int)ctx->scenes.size()) ? &ctx->scenes[env[e].scene] : nullptr;
+            if (!r || !r->live) continue;
+            for (int i = 0; i < env[e].n; i++)
+                for (int k = 0; k < 13; k++)
+                    out_states[(size_t)13 * (env[e].box_off + i) + k] = r->host[(size_t)kRecFloats * i + k];
+        }
+    }
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_query_events(pmbs_ctx* ctx, int64_t batch, uint64_t* out_events) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b || !out_events) return fail(ctx, PMBS_E_INVALID, "unknown batch or null output");
+    if (b->n_envs == 0) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaMemcpyAsync(out_events, b->events, sizeof(uint64_t) * kNumEvents * b->n_envs, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_batch_info(pmbs_ctx* ctx, int64_t batch, int32_t* out_n_envs, int32_t* out_n_boxes) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Batch* b = find_batch(ctx, batch);
+    if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    if (out_n_envs) *out_n_envs = b->n_envs;
+    if (out_n_boxes) {
+        int total = 0;
+        if (b->n_envs > 0) {
+            CU(cudaSetDevice(ctx->device));
+            CU(cudaMemcpyAsync(&total, b->counters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+        }
+        *out_n_boxes = total;
+    }
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_release_batch(pmbs_ctx* ctx, int64_t batch) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    auto it = ctx->batches.find(batch);
+    if (it == ctx->batches.end()) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->stream));
+    release_batch_mem(ctx, it->second);
+    ctx->batches.erase(it);
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_eval_pairs(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                            const float* half_ext, const float* pusher_xy, int32_t* out_pairs, int32_t* out_n_pairs,
+                            int32_t* out_plane, int32_t* out_n_plane, int32_t* out_pusher, int32_t* out_n_pusher) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    CU(cudaSetDevice(ctx->device));
+    return eval_common(ctx, 0, n_envs, box_offset, states, half_ext, pusher_xy, nullptr, nullptr, 0, nullptr, out_pairs,
+                       out_n_pairs, out_plane, out_n_plane, out_pusher, out_n_pusher, nullptr, nullptr, nullptr);
+}
+
+pmbs_status pmbs_eval_grasp(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                            const float* half_ext, const int32_t* target, uint8_t* out_graspable) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n_envs > 0 && !target) return fail(ctx, PMBS_E_INVALID, "missing targets");
+    for (int e = 0; e < n_envs; e++)
+        if (target[e] < 0 || target[e] >= box_offset[e + 1] - box_offset[e])
+            return fail(ctx, PMBS_E_INVALID, "target out of range");
+    CU(cudaSetDevice(ctx->device));
+    return eval_common(ctx, 1, n_envs, box_offset, states, half_ext, nullptr, target, nullptr, 0, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, out_graspable, nullptr, nullptr);
+}
+
+pmbs_status pmbs_eval_sample(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                             const float* half_ext, const uint64_t* seeds, int k, float* out_push,
+                             int32_t* out_attempt) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (k < 2 || (n_envs > 0 && !seeds)) return fail(ctx, PMBS_E_INVALID, "k must be >= 2 and seeds given");
+    CU(cudaSetDevice(ctx->device));
+    return eval_common(ctx, 2, n_envs, box_offset, states, half_ext, nullptr, nullptr, seeds, k, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, out_push, out_attempt);
+}
+
+pmbs_status pmbs_eval_start_blocked(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                                    const float* half_ext, const float* starts, uint8_t* out_blocked) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n_envs > 0 && !starts) return fail(ctx, PMBS_E_INVALID, "missing starts");
+    CU(cudaSetDevice(ctx->device));
+    return eval_common(ctx, 3, n_envs, box_offset, states, half_ext, nullptr, nullptr, nullptr, 0, starts, nullptr,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, out_blocked, nullptr, nullptr);
+}
+
+pmbs_status pmbs_launch_shape(pmbs_ctx* ctx, int max_boxes, int32_t* out_wpb, int32_t* out_Ps, int32_t* out_Ms,
+                              int32_t* out_smem) {
+    if (!ctx || max_boxes < 1 || max_boxes > kMaxBoxes) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int wpb, Ms, Ps;
+    choose_shape(ctx, max_boxes, wpb, Ms, Ps);
+    const int pairS = std::min(ctx->cfg.pair_cap, std::max(1, max_boxes * (max_boxes - 1) / 2));
+    if (out_wpb) *out_wpb = wpb;
+    if (out_Ps) *out_Ps = Ps;
+    if (out_Ms) *out_Ms = Ms;
+    if (out_smem) *out_smem = make_layout(max_boxes, pairS, Ms, Ps, ctx->cfg.manifold_cap).bytes * wpb;
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int warps_per_block, int smem_points, int smem_manifolds) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!(warps_per_block == 0 || warps_per_block == 1 || warps_per_block == 2 || warps_per_block == 4 ||
+          warps_per_block == 8))
+        return fail(ctx, PMBS_E_INVALID, "warps_per_block must be 0, 1, 2, 4 or 8");
+    ctx->fixed_wpb = warps_per_block;
+    ctx->fixed_Ps = smem_points;
+    ctx->fixed_Ms = smem_manifolds;
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_fp32_peak(pmbs_ctx* ctx, double* out_tflops) {
+    if (!ctx || !out_tflops) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    CU(cudaSetDevice(ctx->device));
+    const size_t off = ctx->arena.alloc(sizeof(float) * 65536);
+    if (off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "no room for the probe");
+    float* out = (float*)arena_ptr(ctx, off);
+    const int blocks = ctx->num_sms * 8, threads = 256, iters = 4096;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    fma_peak_kernel<<<blocks, threads, 0, ctx->stream>>>(out, iters / 8, 1.f);
+    CU(cudaEventRecord(e0, ctx->stream));
+    fma_peak_kernel<<<blocks, threads, 0, ctx->stream>>>(out, iters, 1.f);
+    CU(cudaEventRecord(e1, ctx->stream));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->arena.release(off, sizeof(float) * 65536);
+    const double flops = (double)blocks * threads * iters * 16.0 * 8.0 * 2.0;
+    *out_tflops = flops / (ms * 1e-3) / 1e12;
+    return PMBS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,745 @@
+// Warp-level environment solver: one warp advances one environment through whole
+// pushes.  Bodies live in shared memory; contact manifolds and points live in shared
+// memory up to a per-launch capacity and in a per-warp global scratch region beyond it
+// (addressed through generic pointers, so the solver code is the same either way).
+//
+// Substep (dt), following the transition of Sec. III-A as read by this library:
+//   pusher kinematics -> gravity -> frames + AABB -> broadphase (pairs, plane, pusher)
+//   -> narrowphase + ordered emission -> contact preparation -> greedy colouring
+//   -> projected Gauss-Seidel over colours -> semi-implicit integration.
+// Within one colour the manifolds touch disjoint dynamic bodies, so the lanes solve
+// them concurrently and the result equals the sequential order exactly.
+#pragma once
+#include <cstdint>
+
+#include "pmbs_collide.cuh"
+#include "pmbs_exact.cuh"
+
+namespace pmbs {
+
+constexpr int kMaxBoxes = 64;
+constexpr int kMaxColours = 32;
+constexpr int kPlane = 255;   // body id of the table plane (static)
+constexpr int kPusher = 254;  // body id of the kinematic pusher
+constexpr int kNumEvents = 16;
+enum {
+    EV_SUBSTEPS = 0, EV_BOX_STEPS, EV_PAIR_TESTS, EV_SAT, EV_FACE, EV_EDGE, EV_PLANE, EV_PUSHER,
+    EV_POINTS, EV_MANIFOLDS, EV_PGS_MAN, EV_PGS_PTS, EV_PUSH_EVALS, EV_SAMPLE_ATTEMPTS,
+    EV_CLIP_VERTS, EV_COLOURS
+};
+enum { FLAG_GRASP1 = 1, FLAG_INVALID_START = 2, FLAG_OUT_OF_WS = 4, FLAG_OVERFLOW = 8, FLAG_NOOP = 16 };
+
+// Physical and algorithmic constants of a launch.
+struct SimConst {
+    float dt, gx, gy, gz;
+    float table_hx, table_hy, table_mu, pusher_mu;
+    float pr, pz0, pz1, pspeed, plen, gamma;
+    float grasp_W, grasp_c, grasp_f, grasp_fw;
+    float margin, slop, baumgarte, sample_clear;
+    int substeps, iters, grasp_K, attempts, npts;
+    int Pcap, Mcap, pair_cap;
+    float gcos[32], gsin[32];
+};
+
+// Per-warp shared-memory layout (sizes fixed per launch).
+struct Layout {
+    int NB;        // boxes per environment capacity
+    int pairS;     // broadphase pair capacity (<= pair_cap)
+    int Ms, Ps;    // manifolds / points kept in shared memory
+    int Mcap;      // manifold capacity (lists)
+    int bytes;     // total bytes per warp
+    int o_bv, o_bw, o_bI0, o_bI1, o_x, o_q, o_h, o_ib, o_R, o_lo, o_hi, o_mask, o_plane, o_pusher,
+        o_pairs, o_mAB, o_mcol, o_order, o_cstart, o_scal, o_man, o_pts;
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Ps, int Mcap) {
+    Layout L;
+    L.NB = NB;
+    L.pairS = pairS;
+    L.Ms = Ms;
+    L.Ps = Ps;
+    L.Mcap = Mcap;
+    int o = 0;
+    L.o_bv = o; o += 16 * NB;
+    L.o_bw = o; o += 16 * NB;
+    L.o_bI0 = o; o += 16 * NB;
+    L.o_bI1 = o; o += 16 * NB;
+    L.o_man = o; o += 48 * Ms;
+    L.o_pts = o; o += 64 * Ps;
+    L.o_x = o; o += 12 * NB;
+    L.o_q = o; o += 16 * NB;
+    L.o_h = o; o += 12 * NB;
+    L.o_ib = o; o += 12 * NB;
+    L.o_R = o; o += 36 * NB;
+    L.o_lo = o; o += 12 * NB;
+    L.o_hi = o; o += 12 * NB;
+    L.o_mask = o; o += 4 * NB;
+    L.o_scal = o; o += 4 * 16;
+    L.o_mAB = o; o += 2 * Mcap;
+    L.o_order = o; o += 2 * Mcap;
+    L.o_cstart = o; o += 2 * (2 * kMaxColours + 2);
+    o = align_up(o, 4);
+    L.o_pairs = o; o += 2 * pairS;
+    L.o_mcol = o; o += Mcap;
+    L.o_plane = o; o += NB;
+    L.o_pusher = o; o += NB;
+    L.bytes = align_up(o, 16);
+    return L;
+}
+
+// Pointers into one warp's shared region and its global scratch.
+struct WarpMem {
+    float4 *bv, *bw, *bI0, *bI1;  // v+invm, w+mu, inv inertia (00 01 02 11), (12 22 . .)
+    float *x, *q, *h, *ib, *R, *lo, *hi;  // SoA with stride NB (q: 4 rows, R: 9 rows)
+    uint32_t* mask;
+    int* scal;
+    uint16_t *mAB, *order, *cstart, *pairs;
+    uint8_t *mcol, *plane, *pusher;
+    float4 *man_s, *pts_s, *man_g, *pts_g;
+    int NB, Ms, Ps, pairS;
+};
+
+__device__ __forceinline__ WarpMem bind_mem(const Layout& L, char* base, float4* gscratch) {
+    WarpMem W;
+    W.bv = (float4*)(base + L.o_bv);
+    W.bw = (float4*)(base + L.o_bw);
+    W.bI0 = (float4*)(base + L.o_bI0);
+    W.bI1 = (float4*)(base + L.o_bI1);
+    W.x = (float*)(base + L.o_x);
+    W.q = (float*)(base + L.o_q);
+    W.h = (float*)(base + L.o_h);
+    W.ib = (float*)(base + L.o_ib);
+    W.R = (float*)(base + L.o_R);
+    W.lo = (float*)(base + L.o_lo);
+    W.hi = (float*)(base + L.o_hi);
+    W.mask = (uint32_t*)(base + L.o_mask);
+    W.scal = (int*)(base + L.o_scal);
+    W.mAB = (uint16_t*)(base + L.o_mAB);
+    W.order = (uint16_t*)(base + L.o_order);
+    W.cstart = (uint16_t*)(base + L.o_cstart);
+    W.pairs = (uint16_t*)(base + L.o_pairs);
+    W.mcol = (uint8_t*)(base + L.o_mcol);
+    W.plane = (uint8_t*)(base + L.o_plane);
+    W.pusher = (uint8_t*)(base + L.o_pusher);
+    W.man_s = (float4*)(base + L.o_man);
+    W.pts_s = (float4*)(base + L.o_pts);
+    W.man_g = gscratch;
+    W.pts_g = gscratch ? gscratch + 3 * L.Mcap : nullptr;
+    W.NB = L.NB;
+    W.Ms = L.Ms;
+    W.Ps = L.Ps;
+    W.pairS = L.pairS;
+    return W;
+}
+
+__device__ __forceinline__ float4* man_ptr(const WarpMem& W, int m) {
+    return m < W.Ms ? W.man_s + 3 * m : W.man_g + 3 * m;
+}
+__device__ __forceinline__ float4* pt_ptr(const WarpMem& W, int p) {
+    return p < W.Ps ? W.pts_s + 4 * p : W.pts_g + 4 * p;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
+    int s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+    }
+    total = __shfl_sync(0xffffffffu, s, 31);
+    return s - v;
+}
+
+__device__ __forceinline__ CBox load_cbox(const WarpMem& W, int i) {
+    const int NB = W.NB;
+    CBox b;
+    b.c = f3(W.x[i], W.x[NB + i], W.x[2 * NB + i]);
+#pragma unroll
+    for (int k = 0; k < 9; k++) b.R[k] = W.R[k * NB + i];
+    b.h[0] = W.h[i];
+    b.h[1] = W.h[NB + i];
+    b.h[2] = W.h[2 * NB + i];
+    return b;
+}
+
+// Per-push pusher state (warp-uniform).
+struct Pusher {
+    bool active;
+    float sx, sy, dx, dy;
+    int moving;
+};
+
+__device__ __forceinline__ Pusher make_pusher(const SimConst& C, const float* push, bool noop) {
+    Pusher p;
+    const float dx = push[2] - push[0], dy = push[3] - push[1];
+    const float L = sqrtf(dx * dx + dy * dy);
+    p.active = !noop && (L > 1e-9f);
+    p.sx = push[0];
+    p.sy = push[1];
+    p.dx = p.active ? dx / L : 0.f;
+    p.dy = p.active ? dy / L : 0.f;
+    long mv = p.active ? lroundf(L / (C.pspeed * C.dt)) : 0;
+    if (mv > C.substeps) mv = C.substeps;
+    if (mv < 0) mv = 0;
+    p.moving = (int)mv;
+    return p;
+}
+
+// ------------------------------------------------------------------ frames + broadphase
+// Per box: rotation (exact), world inverse inertia, AABB (exact).
+__device__ __forceinline__ void frames_and_aabb(const WarpMem& W, int n, int lane, float margin) {
+    const int NB = W.NB;
+    for (int i = lane; i < n; i += 32) {
+        float R[9];
+        quat_to_R_exact(W.q[i], W.q[NB + i], W.q[2 * NB + i], W.q[3 * NB + i], R);
+#pragma unroll
+        for (int k = 0; k < 9; k++) W.R[k * NB + i] = R[k];
+        const float i0 = W.ib[i], i1 = W.ib[NB + i], i2 = W.ib[2 * NB + i];
+        // R diag(ib) R^T
+        const float I00 = R[0] * i0 * R[0] + R[1] * i1 * R[1] + R[2] * i2 * R[2];
+        const float I01 = R[0] * i0 * R[3] + R[1] * i1 * R[4] + R[2] * i2 * R[5];
+        const float I02 = R[0] * i0 * R[6] + R[1] * i1 * R[7] + R[2] * i2 * R[8];
+        const float I11 = R[3] * i0 * R[3] + R[4] * i1 * R[4] + R[5] * i2 * R[5];
+        const float I12 = R[3] * i0 * R[6] + R[4] * i1 * R[7] + R[5] * i2 * R[8];
+        const float I22 = R[6] * i0 * R[6] + R[7] * i1 * R[7] + R[8] * i2 * R[8];
+        W.bI0[i] = make_float4(I00, I01, I02, I11);
+        W.bI1[i] = make_float4(I12, I22, 0.f, 0.f);
+        const float h0 = W.h[i], h1 = W.h[NB + i], h2 = W.h[2 * NB + i];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float e = aabb_half_exact(R + 3 * k, h0, h1, h2);
+            const float c = W.x[k * NB + i];
+            W.lo[k * NB + i] = xs(xs(c, e), margin);
+            W.hi[k * NB + i] = xa(xa(c, e), margin);
+        }
+    }
+}
+
+// Pair lists at the current AABBs: box-box pairs (i<j, lexicographic, capped), boxes
+// reaching below the plane, boxes meeting the pusher's AABB.  Writes counts to scal[0..2]
+// and returns true if the pair cap dropped pairs.
+__device__ __forceinline__ bool broadphase(const WarpMem& W, int n, int lane, int pair_cap, bool pusher_on,
+                                           float Px, float Py, const SimConst& C) {
+    const int NB = W.NB;
+    const int cap = min(pair_cap, W.pairS);
+    int np = 0;
+    bool overflow = false;
+    for (int i = 0; i + 1 < n; i++) {
+        const float li0 = W.lo[i], li1 = W.lo[NB + i], li2 = W.lo[2 * NB + i];
+        const float hi0 = W.hi[i], hi1 = W.hi[NB + i], hi2 = W.hi[2 * NB + i];
+        for (int jb = i + 1; jb < n; jb += 32) {
+            const int j = jb + lane;
+            bool ov = false;
+            if (j < n) {
+                ov = li0 <= W.hi[j] && W.lo[j] <= hi0 && li1 <= W.hi[NB + j] && W.lo[NB + j] <= hi1 &&
+                     li2 <= W.hi[2 * NB + j] && W.lo[2 * NB + j] <= hi2;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ov);
+            const int pos = np + __popc(m & lanemask_lt());
+            if (ov) {
+                if (pos < cap) W.pairs[pos] = (uint16_t)(i | (j << 8));
+                else overflow = true;
+            }
+            np += __popc(m);
+        }
+    }
+    overflow = __any_sync(0xffffffffu, overflow);
+    int npl = 0, npu = 0;
+    const float rm = xa(C.pr, C.margin);
+    const float plo0 = xs(Px, rm), plo1 = xs(Py, rm), plo2 = xs(C.pz0, rm);
+    const float phi0 = xa(Px, rm), phi1 = xa(Py, rm), phi2 = xa(C.pz1, rm);
+    for (int b = 0; b < n; b += 32) {
+        const int i = b + lane;
+        const bool pl = i < n && W.lo[2 * NB + i] < 0.f;
+        bool pu = false;
+        if (pusher_on && i < n)
+            pu = W.lo[i] <= phi0 && plo0 <= W.hi[i] && W.lo[NB + i] <= phi1 && plo1 <= W.hi[NB + i] &&
+                 W.lo[2 * NB + i] <= phi2 && plo2 <= W.hi[2 * NB + i];
+        const unsigned mp = __ballot_sync(0xffffffffu, pl);
+        const unsigned mu = __ballot_sync(0xffffffffu, pu);
+        if (pl) W.plane[npl + __popc(mp & lanemask_lt())] = (uint8_t)i;
+        if (pu) W.pusher[npu + __popc(mu & lanemask_lt())] = (uint8_t)i;
+        npl += __popc(mp);
+        npu += __popc(mu);
+    }
+    if (lane == 0) {
+        W.scal[0] = min(np, cap);
+        W.scal[1] = npl;
+        W.scal[2] = npu;
+    }
+    __syncwarp();
+    return overflow;
+}
+
+// ------------------------------------------------------------------ narrowphase + emission
+struct NarrowStats {
+    int sat, face, edge, plane, pusher, clip_verts;
+};
+
+// Candidates in order (box-box pairs, plane, pusher); each yields at most four points
+// sharing a normal.  Manifolds are emitted in candidate order until the manifold or
+// point capacity would be exceeded; that manifold and every later one are dropped.
+// Writes M, P to scal[3], scal[4]; returns true on overflow.
+__device__ __forceinline__ bool narrowphase(const WarpMem& W, int lane, const SimConst& C, float Px, float Py,
+                                            NarrowStats& st) {
+    const int NB = W.NB;
+    const int npairs = W.scal[0], nplane = W.scal[1], npush = W.scal[2];
+    const int ncand = npairs + nplane + npush;
+    int M = 0, P = 0;
+    bool stop = false;
+    int sat = 0, face = 0, edge = 0, clipv = 0;
+    for (int base = 0; base < ncand && !stop; base += 32) {
+        const int c = base + lane;
+        CManifold cm;
+        cm.np = 0;
+        int A = 0, B = 0;
+        float mu = 0.f;
+        float3 cA = f3(0.f, 0.f, 0.f), cB = f3(0.f, 0.f, 0.f);
+        int kind = 0;  // 0 box-box, 1 plane, 2 pusher
+        if (c < npairs) {
+            const int pr = W.pairs[c];
+            A = pr & 255;
+            B = pr >> 8;
+            const CBox a = load_cbox(W, A), b = load_cbox(W, B);
+            sat++;
+            const int kd = collide_box_box(a, b, C.margin, cm, clipv);
+            if (kd == 1) face++;
+            if (kd == 2) edge++;
+            mu = sqrtf(W.bw[A].w * W.bw[B].w);
+            cA = a.c;
+            cB = b.c;
+        } else if (c < npairs + nplane) {
+            B = W.plane[c - npairs];
+            A = kPlane;
+            kind = 1;
+            const CBox b = load_cbox(W, B);
+            collide_box_plane(b, C.margin, cm);
+            mu = sqrtf(W.bw[B].w * C.table_mu);
+            cB = b.c;
+        } else if (c < ncand) {
+            A = W.pusher[c - npairs - nplane];
+            B = kPusher;
+            kind = 2;
+            const CBox a = load_cbox(W, A);
+            collide_capsule_box(a, Px, Py, C.pz0, C.pz1, C.pr, C.margin, cm);
+            mu = sqrtf(W.bw[A].w * C.pusher_mu);
+            cA = a.c;
+        }
+        const bool has = cm.np > 0;
+        const unsigned hm = __ballot_sync(0xffffffffu, has);
+        const int mpre = __popc(hm & lanemask_lt());
+        int ptot;
+        const int ppre = warp_excl_scan(cm.np, lane, ptot);
+        const bool fits = (M + mpre + 1 <= C.Mcap) && (P + ppre + cm.np <= C.Pcap);
+        const unsigned viol = __ballot_sync(0xffffffffu, has && !fits);
+        const int first = viol ? __ffs(viol) - 1 : 32;
+        const bool ok = has && lane < first;
+        if (ok) {
+            const int mi = M + mpre, pi = P + ppre;
+            float4* mh = man_ptr(W, mi);
+            mh[0] = make_float4(cm.n.x, cm.n.y, cm.n.z, mu);
+            mh[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(A | (B << 8) | (cm.np << 16)));
+            mh[2] = make_float4(0.f, 0.f, 0.f, __int_as_float(pi));
+            W.mAB[mi] = (uint16_t)(A | (B << 8));
+            for (int k = 0; k < cm.np; k++) {
+                float3 rA, rB;
+                if (kind == 1) {  // plane: p holds the offset from the box centre
+                    rA = f3(0.f, 0.f, 0.f);
+                    rB = cm.p[k];
+                } else if (kind == 2) {
+                    rA = cm.p[k] - cA;
+                    rB = f3(0.f, 0.f, 0.f);
+                } else {
+                    rA = cm.p[k] - cA;
+                    rB = cm.p[k] - cB;
+                }
+                float4* pp = pt_ptr(W, pi + k);
+                pp[0] = make_float4(rA.x, rA.y, rA.z, 0.f);
+                pp[1] = make_float4(rB.x, rB.y, rB.z, 0.f);
+                pp[3] = make_float4(0.f, cm.d[k], 0.f, 0.f);
+            }
+        }
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        int pemit;
+        warp_excl_scan(ok ? cm.np : 0, lane, pemit);
+        M += __popc(okm);
+        P += pemit;
+        if (viol) stop = true;
+    }
+    st.sat += __reduce_add_sync(0xffffffffu, sat);
+    st.face += __reduce_add_sync(0xffffffffu, face);
+    st.edge += __reduce_add_sync(0xffffffffu, edge);
+    st.clip_verts += __reduce_add_sync(0xffffffffu, clipv);
+    st.plane += nplane;
+    st.pusher += npush;
+    if (lane == 0) {
+        W.scal[3] = M;
+        W.scal[4] = P;
+    }
+    __syncwarp();
+    return stop;
+}
+
+// ------------------------------------------------------------------ contact preparation
+__device__ __forceinline__ float3 sym_mul(float4 I0, float4 I1, float3 v) {
+    return f3(I0.x * v.x + I0.y * v.y + I0.z * v.z, I0.y * v.x + I0.w * v.y + I1.x * v.z,
+              I0.z * v.x + I1.x * v.y + I1.y * v.z);
+}
+
+// Tangent basis from the world axis least aligned with n; inverse effective masses along
+// n, t1, t2; target normal velocity (speculative -d/dt when separated, Baumgarte
+// beta/dt * max(-d - slop, 0) when penetrating); impulses start at zero.
+__device__ __forceinline__ void prepare(const WarpMem& W, int lane, const SimConst& C) {
+    const int M = W.scal[3];
+    for (int m = lane; m < M; m += 32) {
+        float4* mh = man_ptr(W, m);
+        const float4 h0 = mh[0], h1 = mh[1], h2 = mh[2];
+        const float3 n = f3(h0.x, h0.y, h0.z);
+        const int ids = __float_as_int(h1.w);
+        const int A = ids & 255, B = (ids >> 8) & 255, np = (ids >> 16) & 255;
+        const int p0 = __float_as_int(h2.w);
+        const float an0 = fabsf(n.x), an1 = fabsf(n.y), an2 = fabsf(n.z);
+        int k = 0;
+        float amin = an0;
+        if (an1 < amin) { k = 1; amin = an1; }
+        if (an2 < amin) k = 2;
+        const float3 e = f3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f);
+        float3 t1 = cross3(n, e);
+        t1 = t1 * (1.f / norm3(t1));
+        const float3 t2 = cross3(n, t1);
+        mh[1] = make_float4(t1.x, t1.y, t1.z, h1.w);
+        mh[2] = make_float4(t2.x, t2.y, t2.z, h2.w);
+        const bool dA = A < kPusher, dB = B < kPusher;
+        float4 IA0 = make_float4(0.f, 0.f, 0.f, 0.f), IA1 = IA0, IB0 = IA0, IB1 = IA0;
+        float imA = 0.f, imB = 0.f;
+        if (dA) { IA0 = W.bI0[A]; IA1 = W.bI1[A]; imA = W.bv[A].w; }
+        if (dB) { IB0 = W.bI0[B]; IB1 = W.bI1[B]; imB = W.bv[B].w; }
+        for (int p = 0; p < np; p++) {
+            float4* pp = pt_ptr(W, p0 + p);
+            const float4 q0 = pp[0], q1 = pp[1], q3 = pp[3];
+            const float3 rA = f3(q0.x, q0.y, q0.z), rB = f3(q1.x, q1.y, q1.z);
+            const float d = q3.y;
+            float kk[3];
+            const float3 dirs[3] = {n, t1, t2};
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                float s = 0.f;
+                if (dA) {
+                    const float3 rn = cross3(rA, dirs[j]);
+                    s += imA + dot3(rn, sym_mul(IA0, IA1, rn));
+                }
+                if (dB) {
+                    const float3 rn = cross3(rB, dirs[j]);
+                    s += imB + dot3(rn, sym_mul(IB0, IB1, rn));
+                }
+                kk[j] = 1.f / s;
+            }
+            const float bias = d > 0.f ? -d / C.dt : (C.baumgarte / C.dt) * fmaxf(-d - C.slop, 0.f);
+            pp[0] = make_float4(rA.x, rA.y, rA.z, kk[0]);
+            pp[1] = make_float4(rB.x, rB.y, rB.z, bias);
+            pp[2] = make_float4(0.f, 0.f, 0.f, kk[1]);
+            pp[3] = make_float4(kk[2], d, 0.f, 0.f);
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ colouring
+// Greedy colouring in manifold order (smallest colour unused by earlier manifolds on a
+// shared dynamic body), then a stable bucket sort of manifold ids by colour.  Lane 0
+// walks the list; the lists are short (hundreds at most).  Returns true on colour
+// overflow (manifold dropped).  Writes the colour count to scal[5] and the number of
+// coloured manifolds to scal[6].
+__device__ __forceinline__ bool colour_manifolds(const WarpMem& W, int n, int lane) {
+    const int M = W.scal[3];
+    for (int i = lane; i < n; i += 32) W.mask[i] = 0u;
+    uint16_t* cnt = W.cstart + (kMaxColours + 2);  // per-colour counters / fill cursors
+    cnt[lane] = 0;
+    __syncwarp();
+    bool overflow = false;
+    if (lane == 0) {
+        int ncol = 0;
+        for (int m = 0; m < M; m++) {
+            const int ab = W.mAB[m];
+            const int A = ab & 255, B = ab >> 8;
+            uint32_t u = 0u;
+            if (A < kPusher) u |= W.mask[A];
+            if (B < kPusher) u |= W.mask[B];
+            const uint32_t freeb = ~u;
+            if (freeb == 0u) {
+                W.mcol[m] = 255;
+                overflow = true;
+                continue;
+            }
+            const int c = __ffs(freeb) - 1;
+            W.mcol[m] = (uint8_t)c;
+            if (A < kPusher) W.mask[A] = W.mask[A] | (1u << c);
+            if (B < kPusher) W.mask[B] = W.mask[B] | (1u << c);
+            if (c + 1 > ncol) ncol = c + 1;
+            cnt[c] = cnt[c] + 1;
+        }
+        int acc = 0;
+        for (int c = 0; c < ncol; c++) {
+            const int k = cnt[c];
+            W.cstart[c] = (uint16_t)acc;
+            cnt[c] = (uint16_t)acc;
+            acc += k;
+        }
+        W.cstart[ncol] = (uint16_t)acc;
+        for (int m = 0; m < M; m++) {
+            const int c = W.mcol[m];
+            if (c == 255) continue;
+            const int f = cnt[c];
+            cnt[c] = (uint16_t)(f + 1);
+            W.order[f] = (uint16_t)m;
+        }
+        W.scal[5] = ncol;
+        W.scal[6] = acc;
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, (int)overflow, 0) != 0;
+}
+
+// ------------------------------------------------------------------ PGS
+__device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pusherV) {
+    const float4* mh = man_ptr(W, m);
+    const float4 h0 = mh[0], h1 = mh[1], h2 = mh[2];
+    const float3 n = f3(h0.x, h0.y, h0.z), t1 = f3(h1.x, h1.y, h1.z), t2 = f3(h2.x, h2.y, h2.z);
+    const float mu = h0.w;
+    const int ids = __float_as_int(h1.w);
+    const int A = ids & 255, B = (ids >> 8) & 255, np = (ids >> 16) & 255;
+    const int p0 = __float_as_int(h2.w);
+    const bool dA = A < kPusher, dB = B < kPusher;
+    float3 vA = f3(0.f, 0.f, 0.f), wA = vA, vB = vA, wB = vA;
+    float imA = 0.f, imB = 0.f, muA = 0.f, muB = 0.f;
+    float4 IA0 = make_float4(0.f, 0.f, 0.f, 0.f), IA1 = IA0, IB0 = IA0, IB1 = IA0;
+    if (dA) {
+        const float4 a = W.bv[A], b = W.bw[A];
+        vA = f3(a.x, a.y, a.z);
+        imA = a.w;
+        wA = f3(b.x, b.y, b.z);
+        muA = b.w;
+        IA0 = W.bI0[A];
+        IA1 = W.bI1[A];
+    }
+    if (dB) {
+        const float4 a = W.bv[B], b = W.bw[B];
+        vB = f3(a.x, a.y, a.z);
+        imB = a.w;
+        wB = f3(b.x, b.y, b.z);
+        muB = b.w;
+        IB0 = W.bI0[B];
+        IB1 = W.bI1[B];
+    } else if (B == kPusher) {
+        vB = pusherV;
+    }
+    for (int p = 0; p < np; p++) {
+        float4* pp = pt_ptr(W, p0 + p);
+        const float4 q0 = pp[0], q1 = pp[1];
+        float4 q2 = pp[2];
+        const float3 rA = f3(q0.x, q0.y, q0.z), rB = f3(q1.x, q1.y, q1.z);
+        const float3 vr = (vB + cross3(wB, rB)) - (vA + cross3(wA, rA));
+        const float vn = dot3(n, vr);
+        const float delta = -(vn - q1.w) * q0.w;
+        const float l = fmaxf(q2.x + delta, 0.f);
+        const float dl = l - q2.x;
+        q2.x = l;
+        pp[2] = q2;
+        const float3 P = n * dl;
+        vA = vA - P * imA;
+        wA = wA - sym_mul(IA0, IA1, cross3(rA, P));
+        vB = vB + P * imB;
+        wB = wB + sym_mul(IB0, IB1, cross3(rB, P));
+    }
+    for (int p = 0; p < np; p++) {
+        float4* pp = pt_ptr(W, p0 + p);
+        const float4 q0 = pp[0], q1 = pp[1], q3 = pp[3];
+        float4 q2 = pp[2];
+        const float3 rA = f3(q0.x, q0.y, q0.z), rB = f3(q1.x, q1.y, q1.z);
+        const float3 vr = (vB + cross3(wB, rB)) - (vA + cross3(wA, rA));
+        const float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
+        float c1 = q2.y - vt1 * q2.w;
+        float c2 = q2.z - vt2 * q3.x;
+        const float lim = mu * q2.x;
+        const float l2 = c1 * c1 + c2 * c2;
+        if (l2 > lim * lim) {
+            const float s = lim / sqrtf(l2);
+            c1 *= s;
+            c2 *= s;
+        }
+        const float d1 = c1 - q2.y, d2 = c2 - q2.z;
+        q2.y = c1;
+        q2.z = c2;
+        pp[2] = q2;
+        const float3 P = t1 * d1 + t2 * d2;
+        vA = vA - P * imA;
+        wA = wA - sym_mul(IA0, IA1, cross3(rA, P));
+        vB = vB + P * imB;
+        wB = wB + sym_mul(IB0, IB1, cross3(rB, P));
+    }
+    if (dA) {
+        W.bv[A] = make_float4(vA.x, vA.y, vA.z, imA);
+        W.bw[A] = make_float4(wA.x, wA.y, wA.z, muA);
+    }
+    if (dB) {
+        W.bv[B] = make_float4(vB.x, vB.y, vB.z, imB);
+        W.bw[B] = make_float4(wB.x, wB.y, wB.z, muB);
+    }
+    return np;
+}
+
+// Returns the number of point visits (normal + friction row pairs) of this lane.
+__device__ __forceinline__ int pgs(const WarpMem& W, int lane, int iters, float3 pusherV) {
+    const int ncol = W.scal[5];
+    int visits = 0;
+    for (int it = 0; it < iters; it++) {
+        for (int c = 0; c < ncol; c++) {
+            const int a = W.cstart[c], b = W.cstart[c + 1];
+            for (int k = a + lane; k < b; k += 32) visits += solve_manifold(W, W.order[k], pusherV);
+            __syncwarp();
+        }
+    }
+    return visits;
+}
+
+// ------------------------------------------------------------------ integration
+__device__ __forceinline__ void integrate(const WarpMem& W, int n, int lane, float dt) {
+    const int NB = W.NB;
+    for (int i = lane; i < n; i += 32) {
+        const float4 v = W.bv[i], w = W.bw[i];
+        W.x[i] += v.x * dt;
+        W.x[NB + i] += v.y * dt;
+        W.x[2 * NB + i] += v.z * dt;
+        const float q0 = W.q[i], q1 = W.q[NB + i], q2 = W.q[2 * NB + i], q3 = W.q[3 * NB + i];
+        const float3 om = f3(w.x, w.y, w.z), qv = f3(q1, q2, q3);
+        const float dw = -dot3(om, qv);
+        const float3 dv = om * q0 + cross3(om, qv);
+        const float hd = 0.5f * dt;
+        const float a0 = q0 + hd * dw, a1 = q1 + hd * dv.x, a2 = q2 + hd * dv.y, a3 = q3 + hd * dv.z;
+        const float l = sqrtf(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
+        W.q[i] = a0 / l;
+        W.q[NB + i] = a1 / l;
+        W.q[2 * NB + i] = a2 / l;
+        W.q[3 * NB + i] = a3 / l;
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ footprints & tests
+// Footprints of every box at the current state into the R area (8 floats per box).
+__device__ __forceinline__ void compute_footprints(const WarpMem& W, int n, int lane) {
+    const int NB = W.NB;
+    for (int i = lane; i < n; i += 32) {
+        float R[9];
+        quat_to_R_exact(W.q[i], W.q[NB + i], W.q[2 * NB + i], W.q[3 * NB + i], R);
+        const Foot f = footprint_exact(W.x[i], W.x[NB + i], R, W.h[i], W.h[NB + i], W.h[2 * NB + i]);
+        float* o = W.R;
+        o[0 * NB + i] = f.cx;
+        o[1 * NB + i] = f.cy;
+        o[2 * NB + i] = f.ux;
+        o[3 * NB + i] = f.uy;
+        o[4 * NB + i] = f.vx;
+        o[5 * NB + i] = f.vy;
+        o[6 * NB + i] = f.su;
+        o[7 * NB + i] = f.sv;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ Foot load_foot(const WarpMem& W, int i) {
+    const int NB = W.NB;
+    const float* o = W.R;
+    Foot f;
+    f.cx = o[i];
+    f.cy = o[NB + i];
+    f.ux = o[2 * NB + i];
+    f.uy = o[3 * NB + i];
+    f.vx = o[4 * NB + i];
+    f.vy = o[5 * NB + i];
+    f.su = o[6 * NB + i];
+    f.sv = o[7 * NB + i];
+    return f;
+}
+
+// Grasp-clearance decision on the footprints (Sec. IV-B grasp evaluation stand-in):
+// lane pairs (angle k, finger side) test the finger sweep against every other footprint.
+__device__ __forceinline__ bool grasp_check(const WarpMem& W, int n, int t, int lane, const SimConst& C) {
+    const Foot ft = load_foot(W, t);
+    const float halfW = xm(C.grasp_W, 0.5f), hfw = xm(C.grasp_fw, 0.5f);
+    bool any = false;
+    for (int kb = 0; kb < C.grasp_K; kb += 16) {
+        const int k = kb + (lane >> 1);
+        const float s = (lane & 1) ? -1.f : 1.f;
+        bool ok = false;
+        if (k < C.grasp_K) {
+            const float ax = C.gcos[k], ay = C.gsin[k];
+            const float bx = -ay, by = ax;
+            const float wa = xa(xm(fabsf(xdot2(ft.ux, ft.uy, ax, ay)), ft.su), xm(fabsf(xdot2(ft.vx, ft.vy, ax, ay)), ft.sv));
+            if (xm(xa(wa, C.grasp_c), 2.f) <= C.grasp_W) {
+                const float off = xm(xa(xa(wa, halfW), C.grasp_f), 0.5f);
+                const float hl = xm(xs(xa(halfW, C.grasp_f), wa), 0.5f);
+                const float fcx = xa(ft.cx, s * xm(ax, off));
+                const float fcy = xa(ft.cy, s * xm(ay, off));
+                ok = true;
+                for (int o = 0; o < n; o++) {
+                    if (o == t) continue;
+                    if (finger_overlaps_exact(load_foot(W, o), fcx, fcy, ax, ay, bx, by, hl, hfw)) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+        }
+        const bool pair_ok = ok && __shfl_xor_sync(0xffffffffu, ok, 1);
+        any = any || __any_sync(0xffffffffu, pair_ok);
+    }
+    return any;
+}
+
+// Start-pose check of a push starting at (px, py): any footprint within the pusher
+// radius (Sec. IV-B: only the start pose is collision-checked).
+__device__ __forceinline__ bool start_blocked(const WarpMem& W, int n, int lane, float px, float py, float r) {
+    bool hit = false;
+    for (int i = lane; i < n; i += 32) hit = hit || disc_hits_foot_exact(load_foot(W, i), px, py, r);
+    return __any_sync(0xffffffffu, hit);
+}
+
+// Contour sampler for push k >= 2 (Sec. IV-B): lane a evaluates attempt a; the lowest
+// unblocked attempt wins.  Returns the attempt (or -1) and the push in out[4].
+__device__ __forceinline__ int sample_push(const WarpMem& W, int n, int lane, uint64_t seed, int k,
+                                           const SimConst& C, float* out) {
+    int best = -1;
+    for (int ab = 0; ab < C.attempts && best < 0; ab += 32) {
+        const int a = ab + lane;
+        float push[4] = {0.f, 0.f, 0.f, 0.f};
+        bool good = false;
+        if (a < C.attempts) {
+            int j, p;
+            sampler_draws(seed, k, a, n, C.npts, j, p);
+            contour_push_exact(load_foot(W, j), p, C.npts, C.pr, C.sample_clear, C.plen, push);
+            good = true;
+            for (int o = 0; o < n; o++)
+                if (disc_hits_foot_exact(load_foot(W, o), push[0], push[1], C.pr)) {
+                    good = false;
+                    break;
+                }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, good);
+        if (m) {
+            const int src = __ffs(m) - 1;
+            best = ab + src;
+            for (int i = 0; i < 4; i++) out[i] = __shfl_sync(0xffffffffu, push[i], src);
+        }
+    }
+    return best;
+}
+
+}  // namespace pmbs

@@ -1,0 +1,390 @@
+"""GPU (CUDA, through the C ABI) against the FP64 oracle.
+
+Bit-exact: broadphase pair lists, grasp decisions, start-pose checks and sampled pushes on
+identical FP32 snapshots (the oracle's binary32 twins).  Tolerances: state after one
+substep within 1e-4 m / 1e-3 rad; non-chaotic scenes after 240 substeps within
+1e-3 m / 1e-2 rad; tiny-config cost agreement >= 90 %.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import _geom as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2207_06649_b300 import pmbs
+    e = pmbs.Engine(device=0, mem_budget_bytes=2 << 30)
+    yield e
+    e.close()
+
+
+def _pm():
+    from paper_2207_06649_b300 import pmbs
+    return pmbs
+
+
+def _sg():
+    from paper_2207_06649_b300 import scenegen
+    return scenegen
+
+
+def _snapshots(seed, n_envs, n_lo=2, n_hi=40):
+    sg = _sg()
+    rng = np.random.default_rng(seed)
+    sts, hs, off = [], [], [0]
+    for e in range(n_envs):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        pose, vel, half = sg.random_state_snapshot(rng, n, spread=0.02 + 0.004 * n)
+        sts.append(np.concatenate([pose, vel], 1))
+        hs.append(half)
+        off.append(off[-1] + n)
+    return np.array(off, np.int32), np.concatenate(sts), np.concatenate(hs)
+
+
+def _clutter_batch(seed, n_envs, n_lo=5, n_hi=20, squeeze=1.0):
+    sg = _sg()
+    rng = np.random.default_rng(seed)
+    parts = []
+    for e in range(n_envs):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        sc = sg.make_scene(rng, n, half_lo=0.01, half_hi=0.035, yaw_hi=math.pi / 2,
+                           density_scale=rng.uniform(0.3, 0.6))
+        sc.pose[:, :2] *= squeeze
+        parts.append(sc)
+    return sg.concat(parts)
+
+
+# ------------------------------------------------------------------ bit-exact predicates
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pairs_bit_exact(eng, orc, seed):
+    off, st, h = _snapshots(seed, 96)
+    rng = np.random.default_rng(seed + 7)
+    pxy = rng.uniform(-0.05, 0.05, size=(len(off) - 1, 2)).astype(np.float32)
+    got = eng.eval_pairs(off, st, h, pusher_xy=pxy)
+    for e in range(len(off) - 1):
+        a, b = off[e], off[e + 1]
+        bb, pl, pu, _ = orc.pairs(st[a:b], h[a:b], pusher_xy=pxy[e], f32=True)
+        assert np.array_equal(got[e][0], bb), f"env {e} pairs"
+        assert np.array_equal(got[e][1], pl), f"env {e} plane"
+        assert np.array_equal(got[e][2], pu), f"env {e} pusher"
+
+
+def test_pairs_without_pusher_and_single_box(eng, orc):
+    off = np.array([0, 1, 3], np.int32)
+    st = np.stack([G.box_row(0, 0, 0.02), G.box_row(0, 0, 0.02), G.box_row(0.03, 0, 0.02)]).astype(np.float32)
+    h = np.full((3, 3), 0.015, np.float32)
+    got = eng.eval_pairs(off, st, h)
+    assert len(got[0][0]) == 0 and list(got[0][1]) == [0] and len(got[0][2]) == 0
+    assert got[1][0].tolist() == [[0, 1]]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_grasp_decisions_bit_exact(eng, orc, seed):
+    sc = _clutter_batch(100 + seed, 128, 3, 25)
+    st = _sg().state13(sc)
+    rng = np.random.default_rng(seed)
+    st[:, :2] += rng.normal(scale=0.002, size=(len(st), 2)).astype(np.float32)
+    tgt = np.array([rng.integers(0, sc.box_offset[e + 1] - sc.box_offset[e]) for e in range(sc.n_scenes)],
+                   np.int32)
+    got = eng.eval_grasp(sc.box_offset, st, sc.half, tgt)
+    want = [orc.grasp(st[sc.box_offset[e]:sc.box_offset[e + 1]], sc.half[sc.box_offset[e]:sc.box_offset[e + 1]],
+                      int(tgt[e]), f32=True) for e in range(sc.n_scenes)]
+    assert got.tolist() == want
+    assert 0 < sum(want) < len(want), "cases must include both outcomes"
+
+
+@pytest.mark.parametrize("k", [2, 3, 9])
+def test_sampled_pushes_bit_exact(eng, orc, k):
+    sc = _clutter_batch(200 + k, 128, 2, 30)
+    st = _sg().state13(sc)
+    seeds = np.random.default_rng(k).integers(0, 2 ** 63, size=sc.n_scenes, dtype=np.uint64)
+    att, push = eng.eval_sample(sc.box_offset, st, sc.half, seeds, k)
+    for e in range(sc.n_scenes):
+        a, b = sc.box_offset[e], sc.box_offset[e + 1]
+        wa, wp = orc.sample_push(st[a:b], sc.half[a:b], int(seeds[e]), k, f32=True)
+        assert att[e] == wa
+        if wa >= 0:
+            assert np.array_equal(push[e].view(np.uint32), wp.view(np.uint32))
+
+
+def test_start_checks_bit_exact(eng, orc):
+    sc = _clutter_batch(300, 200, 3, 30)
+    st = _sg().state13(sc)
+    rng = np.random.default_rng(5)
+    starts = np.zeros((sc.n_scenes, 2), np.float32)
+    for e in range(sc.n_scenes):
+        i = sc.box_offset[e] + rng.integers(0, sc.box_offset[e + 1] - sc.box_offset[e])
+        starts[e] = st[i, :2] + rng.normal(scale=0.03, size=2)
+    got = eng.eval_start_blocked(sc.box_offset, st, sc.half, starts)
+    want = [orc.start_blocked(st[sc.box_offset[e]:sc.box_offset[e + 1]], sc.half[sc.box_offset[e]:sc.box_offset[e + 1]],
+                              starts[e, 0], starts[e, 1], f32=True) for e in range(sc.n_scenes)]
+    assert got.tolist() == want and 0 < sum(want) < len(want)
+
+
+# ------------------------------------------------------------------ trajectories
+def _angle_err(qa, qb):
+    d = np.abs(np.sum(qa * qb, axis=-1)).clip(0, 1)
+    return 2 * np.arccos(d)
+
+
+def _run_gpu_substeps(eng, sc, pushes, count, depth=1, seeds=None):
+    ids = eng.load(sc)
+    b = eng.rollout_pushes(ids, pushes, depth, seeds)
+    eng.step(b, count)
+    st, steps = eng.query_states(b)
+    eng.release_batch(b)
+    eng.free_scenes(ids)
+    return st, steps
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_one_substep_state_parity(eng, orc, seed):
+    sg = _sg()
+    sc = _clutter_batch(400 + seed, 64, 3, 30, squeeze=0.95)
+    rng = np.random.default_rng(seed)
+    pushes = np.stack([sg._random_valid_push(rng, sc, e) for e in range(sc.n_scenes)])
+    st, steps = _run_gpu_substeps(eng, sc, pushes, 1)
+    s0 = sg.state13(sc)
+    for e in range(sc.n_scenes):
+        a, b = sc.box_offset[e], sc.box_offset[e + 1]
+        ref, _, _ = orc.run_substeps(s0[a:b], sc.half[a:b], sc.mass[a:b], sc.mu[a:b], push=pushes[e].astype(float),
+                                     count=1)
+        assert steps[e] == 1
+        assert np.abs(st[a:b, :3] - ref[:, :3]).max() <= 1e-4
+        assert _angle_err(st[a:b, 3:7].astype(float), ref[:, 3:7]).max() <= 1e-3
+
+
+def _single_env(rows, halves, mass=0.1, mu=0.5):
+    sg = _sg()
+    st = np.stack([G.box_row(*r) for r in rows]).astype(np.float32)
+    n = len(rows)
+    return sg.Scenes(np.array([0, n], np.int32), st[:, :7].copy(), st[:, 7:].copy(), np.array(halves, np.float32),
+                     np.full(n, mass, np.float32), np.full(n, mu, np.float32), np.array([0], np.int32))
+
+
+@pytest.mark.parametrize("case", ["rest", "slide", "push", "stack", "tilted"])
+def test_non_chaotic_240_substeps(eng, orc, case):
+    far = np.array([[0.19, 0.19, 0.19, 0.19]], np.float32)   # zero-length push: pusher inactive
+    if case == "rest":
+        sc = _single_env([(0.05, -0.02, 0.015)], [[0.02, 0.03, 0.015]])
+        push = far
+    elif case == "slide":
+        sc = _single_env([(0, 0, 0.02, (1, 0, 0, 0), (0.3, 0.2, 0))], [[0.02, 0.02, 0.02]])
+        push = far
+    elif case == "push":
+        sc = _single_env([(0, 0, 0.02)], [[0.02, 0.02, 0.02]])
+        push = np.array([[-0.05, 0.0, 0.05, 0.0]], np.float32)
+    elif case == "stack":
+        sc = _single_env([(0, 0, 0.02), (0.005, -0.004, 0.055)], [[0.03, 0.03, 0.02], [0.02, 0.02, 0.015]])
+        push = far
+    else:
+        q = G.quat_from_rotvec([0.0, 0.15, 0.0])
+        v = G.vertices(G.box_row(0, 0, 0, q=q), [0.03, 0.02, 0.01])
+        sc = _single_env([(0, 0, -v[:, 2].min() + 0.002, tuple(q))], [[0.03, 0.02, 0.01]])
+        push = far
+    st, steps = _run_gpu_substeps(eng, sc, push, 240)
+    s0 = _sg().state13(sc)
+    ref, _, _ = orc.run_substeps(s0, sc.half, sc.mass, sc.mu, push=push[0].astype(float), count=240)
+    assert steps[0] == 240
+    assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-3
+    assert _angle_err(st[:, 3:7].astype(float), ref[:, 3:7]).max() <= 1e-2
+
+
+def test_tiny_config_cost_agreement(eng, orc):
+    sg = _sg()
+    agree, total, errs = 0, 0, []
+    for seed in range(1, 9):
+        sc, pushes = sg.config_tiny(seed=seed)
+        ids = eng.load(sc)
+        out = eng.rollout(np.repeat(ids, len(pushes)), pushes, depth=1)
+        eng.free_scenes(ids)
+        envs = sc.gather([0] * len(pushes))
+        ref = orc.rollout(envs.box_offset, sg.state13(envs), envs.half, envs.mass, envs.mu, envs.target, pushes,
+                          depth=1, threads=8)
+        agree += int(np.sum(out["cost"] == ref.cost))
+        total += len(pushes)
+        errs.append(np.abs(out["state"][:, :3] - ref.state[:, :3]).max())
+        # flags that do not depend on the trajectory agree exactly
+        assert np.array_equal(out["flags"] & 2, ref.flags & 2)
+        # decisions on the GPU's own final states are bit-exact with the binary32 twin
+        for e in range(len(pushes)):
+            a, b = envs.box_offset[e], envs.box_offset[e + 1]
+            if out["flags"][e] & 6:
+                continue
+            assert orc.grasp(out["state"][a:b], envs.half[a:b], 0, f32=True) == (out["cost"][e] == 1)
+    print(f"tiny config: cost agreement {agree}/{total}, max end-state error {max(errs):.2e} m")
+    assert agree >= 0.9 * total
+
+
+# ------------------------------------------------------------------ batching invariance
+def _config3_small(seed=7, n_envs=96):
+    sg = _sg()
+    scenes, pushes, seeds = sg.config_uneven(seed=seed, n_envs=n_envs, n_lo=5, n_hi=40)
+    return scenes, pushes, seeds
+
+
+def test_results_identical_across_launch_shapes(eng):
+    scenes, pushes, seeds = _config3_small()
+    ids = eng.load(scenes)
+    outs = []
+    for shape in [(0, -1, -1), (1, 0, 0), (2, 32, 8), (8, 0, 0), (4, 200, 60)]:
+        eng.set_launch_shape(*shape)
+        outs.append(eng.rollout(ids, pushes, depth=2, seeds=seeds))
+    eng.set_launch_shape(0, -1, -1)
+    eng.free_scenes(ids)
+    for o in outs[1:]:
+        assert np.array_equal(o["cost"], outs[0]["cost"])
+        assert np.array_equal(o["state"].view(np.uint32), outs[0]["state"].view(np.uint32))
+        assert np.array_equal(o["events"], outs[0]["events"])
+
+
+def test_results_identical_alone_and_in_mix(eng):
+    scenes, pushes, seeds = _config3_small(seed=9, n_envs=64)
+    ids = eng.load(scenes)
+    mix = eng.rollout(ids, pushes, depth=2, seeds=seeds)
+    for e in [0, 5, 17, 63]:
+        alone = eng.rollout(ids[e:e + 1], pushes[e:e + 1], depth=2, seeds=seeds[e:e + 1])
+        a, b = scenes.box_offset[e], scenes.box_offset[e + 1]
+        assert alone["cost"][0] == mix["cost"][e]
+        assert np.array_equal(alone["state"].view(np.uint32), mix["state"][a:b].view(np.uint32))
+    eng.free_scenes(ids)
+
+
+def test_resumed_stepping_equals_one_launch(eng):
+    scenes, pushes, seeds = _config3_small(seed=11, n_envs=32)
+    ids = eng.load(scenes)
+    one = eng.rollout(ids, pushes, depth=2, seeds=seeds)
+    b = eng.rollout_pushes(ids, pushes, 2, seeds)
+    n_calls = 0
+    while not eng.step(b, 97):
+        n_calls += 1
+        assert n_calls < 20
+    st, _ = eng.query_states(b)
+    res = eng.query_cost(b)
+    eng.release_batch(b)
+    eng.free_scenes(ids)
+    assert np.array_equal(res["cost"], one["cost"])
+    assert np.array_equal(st.view(np.uint32), one["state"].view(np.uint32))
+
+
+# ------------------------------------------------------------------ edge cases and ABI
+def test_empty_batch_and_degenerate_inputs(eng):
+    pm = _pm()
+    b = eng.rollout_pushes(np.zeros(0, np.int32), np.zeros((0, 4), np.float32), 3)
+    assert eng.step(b, 0)
+    r = eng.query_cost(b)
+    assert r["cost"].shape == (0,)
+    eng.release_batch(b)
+    sc = _single_env([(0, 0, 0.02)], [[0.02, 0.02, 0.02]])
+    bad = sc.pose.copy()
+    bad[0, 3] = 0.9
+    with pytest.raises(pm.PmbsError) as ei:
+        eng.load_scenes(sc.box_offset, bad, sc.half, sc.mass, sc.mu, sc.target)
+    assert ei.value.status == pm.PMBS_E_INVALID
+    bad = sc.pose.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(pm.PmbsError):
+        eng.load_scenes(sc.box_offset, bad, sc.half, sc.mass, sc.mu, sc.target)
+    with pytest.raises(pm.PmbsError):
+        eng.rollout_pushes(np.array([12345], np.int32), np.zeros((1, 4), np.float32), 1)
+    ids = eng.load(sc)
+    b = eng.rollout_pushes(ids, np.array([[0.02, 0.0, 0.12, 0.0]], np.float32), 2, np.array([1], np.uint64))
+    with pytest.raises(pm.PmbsError) as ei:
+        eng.free_scenes(ids)
+    assert ei.value.status == pm.PMBS_E_BUSY
+    eng.step(b, 0)
+    r = eng.query_cost(b)
+    assert r["flags"][0] & pm.FLAG_INVALID_START and r["cost"][0] == 3
+    _, steps = eng.query_states(b)
+    assert steps[0] == 0
+    eng.release_batch(b)
+    eng.free_scenes(ids)
+
+
+def test_max_size_scene_runs(eng, orc):
+    sg = _sg()
+    rng = np.random.default_rng(3)
+    sc = sg.make_scene(rng, 64, half_lo=0.008, half_hi=0.012, region_half=0.19)
+    assert sc.box_offset[-1] == 64
+    push = sg._random_valid_push(rng, sc, 0)[None]
+    st, steps = _run_gpu_substeps(eng, sc, push, 1)
+    ref, _, _ = orc.run_substeps(sg.state13(sc), sc.half, sc.mass, sc.mu, push=push[0].astype(float), count=1)
+    assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-4
+
+
+def test_child_states_equal_state_after_first_push(eng):
+    scenes, pushes, seeds = _config3_small(seed=13, n_envs=24)
+    ids = eng.load(scenes)
+    one = eng.rollout(ids, pushes, depth=1)
+    b = eng.rollout_pushes(ids, pushes, 3, seeds)
+    eng.step(b, 0)
+    r = eng.query_cost(b, child_states=True, child_scenes=True)
+    eng.release_batch(b)
+    valid = (one["flags"] & 2) == 0
+    for e in np.nonzero(valid)[0]:
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        assert np.array_equal(r["child_states"][a:z].view(np.uint32), one["state"][a:z].view(np.uint32))
+    # the registered child scenes continue from the child state
+    cid = r["child_scene_ids"]
+    assert len(set(cid.tolist())) == len(cid)
+    eng.free_scenes(cid)
+    eng.free_scenes(ids)
+
+
+def test_event_counts_match_oracle_on_simple_scene(eng, orc):
+    sc = _single_env([(0, 0, 0.02), (0.1, 0.05, 0.02)], [[0.02, 0.02, 0.02], [0.015, 0.02, 0.02]])
+    push = np.array([[-0.05, 0.0, 0.05, 0.0]], np.float32)
+    ids = eng.load(sc)
+    out = eng.rollout(ids, push, depth=1)
+    eng.free_scenes(ids)
+    ref = orc.rollout(sc.box_offset, _sg().state13(sc), sc.half, sc.mass, sc.mu, sc.target, push, depth=1)
+    names = _pm().EVENT_NAMES
+    for k in ["substeps", "box_steps", "pair_tests", "plane", "push_evals"]:
+        assert out["events"][0, names.index(k)] == ref.events[0, names.index(k)], k
+    for k in ["points", "manifolds", "pgs_points", "pusher"]:
+        g, w = float(out["events"][0, names.index(k)]), float(ref.events[0, names.index(k)])
+        assert abs(g - w) <= 0.02 * w + 2, k
+
+
+# ------------------------------------------------------------------ full-size workloads
+def test_uneven_4096_env_launch_sampled_parity(eng, orc):
+    """The 4096-env uneven workload in the benchmark's launch configuration: one launch
+    to completion; sampled environments are re-checked (grasp decisions on the final
+    states bit-exact, flags and step counts consistent, sampled envs equal when re-run
+    alone), and one substep of the whole batch against the oracle on a sample."""
+    sg = _sg()
+    scenes, pushes, seeds = sg.config_uneven(seed=3, n_envs=4096)
+    ids = eng.load(scenes)
+    b = eng.rollout_pushes(ids, pushes, 1)
+    eng.step(b, 1)
+    st1, _ = eng.query_states(b)
+    eng.release_batch(b)
+    s0 = sg.state13(scenes)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(4096, size=24, replace=False)
+    for e in sample:
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        ref, _, _ = orc.run_substeps(s0[a:z], scenes.half[a:z], scenes.mass[a:z], scenes.mu[a:z],
+                                     push=pushes[e].astype(float), count=1)
+        assert np.abs(st1[a:z, :3] - ref[:, :3]).max() <= 1e-4
+    out = eng.rollout(ids, pushes, depth=3, seeds=seeds)
+    assert ((out["flags"] & 2) == 0).mean() > 0.95
+    for e in sample:
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        c = out["cost"][e]
+        assert 1 <= c <= 4
+        assert out["steps"][e] == 240 * min(c, 3) or out["flags"][e] & 6
+        if c <= 3 and not out["flags"][e] & 6:
+            assert orc.grasp(out["state"][a:z], scenes.half[a:z], int(scenes.target[e]), f32=True)
+            assert out["reward"][e] == pytest.approx(0.8 ** (c - 1), rel=1e-6)
+        alone = eng.rollout(ids[e:e + 1], pushes[e:e + 1], depth=3, seeds=seeds[e:e + 1])
+        assert alone["cost"][0] == c
+        assert np.array_equal(alone["state"].view(np.uint32), out["state"][a:z].view(np.uint32))
+    eng.free_scenes(ids)
