@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark of the batched push-rollout path (one JSON line on stdout, rank 0).
+
+Workload: 4096 independent cluttered scenes with uneven box counts (n ~ U{5..40},
+half extents U[0.01, 0.04] m, mu U[0.3, 0.8], yaw U[0, pi/2), clutter density
+U[0.2, 0.6]), one random valid first push per environment, then two device-sampled
+pushes (depth 3), 240 substeps of 1/240 s per push, 10 PGS iterations.  A step is one
+batched rollout of all environments.  Metric: simulated environment-substeps per second
+(env-steps/s).
+
+  value   device-resident inputs (scene store loaded once; environment ids, first pushes
+          and seeds in device memory), timed with CUDA events on the launching stream;
+          the L2 cache is flushed (256 MB write) before every step.
+  e2e     the same metric through the C ABI from host buffers: scenes loaded, batch
+          submitted, results copied back and memory released inside the timed region.
+  roofline  the rollout kernel against the FP32 CUDA-core peak (ALU bound).
+  cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on the same
+workload and metric.  Under torchrun each rank runs its own 4096-environment workload on
+its own GPU (weak scaling, no data-path collective).
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel source it was measured on.
+TRAFFIC = {"source_sha": None, "bytes_per_launch": None, "note": None}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2207_06649_b300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--depth", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=768)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+WORKLOAD = "uneven rollout: 4096 scenes x U{5..40} boxes, depth 3 x 240 substeps"
+METRIC = "env-steps/s at 4096 uneven envs"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(scenes, pushes, seeds, depth, sample, label):
+    import oracle
+    from paper_2207_06649_b300 import scenegen as sg
+    n = min(sample, scenes.n_scenes)
+    sub = scenes.gather(range(n))
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    r = oracle.rollout(sub.box_offset, sg.state13(sub), sub.half, sub.mass, sub.mu, sub.target, pushes[:n], depth,
+                       seeds[:n], threads=cores)
+    dt = time.perf_counter() - t
+    es = int(r.steps.sum())
+    return {"value": es / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of the {label} environments ({es} env-steps, FP64, {cores} threads, "
+                      f"{dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    from paper_2207_06649_b300 import scenegen as sg
+    scenes, pushes, seeds = sg.config_uneven(seed=args.seed, n_envs=args.envs)
+    per_step = min(args.cpu_sample, scenes.n_scenes)
+    for _ in range(args.warmup):
+        cpu_baseline(scenes, pushes, seeds, args.depth, max(8, per_step // 8), "workload's")
+    vals, t_total, es_total = [], 0.0, 0
+    for _ in range(args.steps):
+        b = cpu_baseline(scenes, pushes, seeds, args.depth, per_step, "workload's")
+        vals.append(b)
+    v = float(np.mean([b["value"] for b in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "envs": args.envs, "depth": args.depth,
+                       "per_step_sample": per_step},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": v,
+                             "unit": "env-steps/s"},
+            "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2207_06649_b300 import flops, pmbs, scenegen as sg
+
+    scenes, pushes, seeds = sg.config_uneven(seed=args.seed + 1000 * rank, n_envs=args.envs)
+    stream = torch.cuda.current_stream()
+    eng = pmbs.Engine(device=local, mem_budget_bytes=8 << 30, max_envs=max(args.envs, 1),
+                      stream=pmbs.C.c_void_p(stream.cuda_stream))
+    ids = eng.load(scenes)
+    d_ids = torch.from_numpy(ids.astype(np.int32)).to(dev)
+    d_push = torch.from_numpy(pushes.astype(np.float32)).to(dev)
+    d_seed = torch.from_numpy(seeds.view(np.int64)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        b = eng.rollout_pushes_device(args.envs, d_ids.data_ptr(), d_push.data_ptr(), args.depth, d_seed.data_ptr())
+        eng.step(b, 0)
+        return b
+
+    # warm-up (untimed); the first batch also gives the per-step work counts
+    batches = []
+    for w in range(max(args.warmup, 1)):
+        flush.zero_()
+        batches.append(one_step())
+    torch.cuda.synchronize()
+    st, steps = eng.query_states(batches[0])
+    env_steps = int(steps.sum())
+    ev = eng.query_events(batches[0])
+    flops_per_launch = flops.algorithmic_flops(ev, pmbs.EVENT_NAMES)
+    boxes = scenes.counts()
+    for b in batches:
+        eng.release_batch(b)
+    batches = []
+
+    # timed region
+    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0.record()
+        for i in range(args.steps):
+            flush.zero_()
+            k0[i].record()
+            batches.append(one_step())
+            k1[i].record()
+        t1.record()
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    kernel_s = float(np.mean([a.elapsed_time(b) for a, b in zip(k0, k1)])) / 1e3
+    for b in batches:
+        eng.release_batch(b)
+    total_env_steps = env_steps * args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        s = torch.tensor([total_env_steps], device=dev, dtype=torch.float64)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        total_env_steps = int(s.item())
+    value = total_env_steps / elapsed
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_off, h_pose, h_vel = pin(scenes.box_offset), pin(scenes.pose), pin(scenes.vel)
+        h_half, h_mass, h_mu, h_tgt = pin(scenes.half), pin(scenes.mass), pin(scenes.mu), pin(scenes.target)
+        h_push, h_seed = pin(pushes.astype(np.float32)), pin(seeds)
+        h2d = sum(a.nbytes for a in (h_off, h_pose, h_vel, h_half, h_mass, h_mu, h_tgt, h_push, h_seed)) + 4 * args.envs
+        d2h = 9 * args.envs
+
+        def e2e_step():
+            sid = eng.load_scenes(h_off, h_pose, h_half, h_mass, h_mu, h_tgt, vel=h_vel)
+            b = eng.rollout_pushes(sid, h_push, args.depth, h_seed)
+            eng.step(b, 0)
+            r = eng.query_cost(b)
+            eng.release_batch(b)
+            eng.free_scenes(sid)
+            return r
+
+        for _ in range(max(1, args.warmup - 1)):
+            e2e_step()
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - ts
+        e2e = {"value": env_steps * args.steps * ws / te, "unit": "env-steps/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    peak_fma = eng.fp32_peak()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary()
+    max_mhz = clocks["sm_max_mhz"] or 2032.0
+    peak = flops.fp32_peak_tflops(sms, max_mhz)
+    achieved = flops_per_launch / kernel_s / 1e12
+    sha = kernel_source_sha()
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha else None
+    state_bytes = float(boxes.sum()) * (72 + 52 + 52) + args.envs * (28 + 64 + 13)
+    line = {
+        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "envs": args.envs, "boxes_per_env_mean": float(boxes.mean()),
+                   "boxes_per_env_range": [int(boxes.min()), int(boxes.max())], "depth": args.depth,
+                   "substeps_per_push": 240, "pgs_iters": 10, "env_steps_per_step": env_steps,
+                   "box_steps_per_s": value * float(boxes.mean()),
+                   "l2": "flushed before every step (256 MB device write)",
+                   "parallelism": f"one environment per warp, persistent launch; {ws} GPU(s), weak scaling"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "rollout_kernel", "kernel_ms": kernel_s * 1e3,
+                     "flops_per_launch": flops_per_launch,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                     "fma_probe_tflops": peak_fma,
+                     "hbm_achieved_gbs": state_bytes / kernel_s / 1e9},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scenes, pushes, seeds, args.depth, args.cpu_sample, "workload's")
+    eng.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

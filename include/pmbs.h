@@ -65,7 +65,7 @@ enum {
 };
 
 /* Event counters per environment (pmbs_query_events), in this order. */
-#define PMBS_NUM_EVENTS 16
+#define PMBS_NUM_EVENTS 18
 
 typedef struct {
     int device;                 /* CUDA device ordinal */
@@ -185,7 +185,8 @@ pmbs_status pmbs_query_states(pmbs_ctx* ctx, int64_t batch, float* out_states,
 /* Event counters [n_envs][PMBS_NUM_EVENTS] (substeps, box-steps, pair tests, SAT tests,
  * face contacts, edge contacts, plane candidates, pusher candidates, contact points,
  * manifolds, PGS manifold visits, PGS point visits, push evaluations, sampler attempts,
- * clipped vertices, colours) used to count the algorithmic flops of a launch. */
+ * clipped vertices, colours, box-box contact points, PGS point visits between two boxes)
+ * used to count the algorithmic flops of a launch. */
 pmbs_status pmbs_query_events(pmbs_ctx* ctx, int64_t batch, uint64_t* out_events);
 
 /* Number of environments and boxes in the batch. */

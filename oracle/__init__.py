@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 EVENT_NAMES = ["substeps", "box_steps", "pair_tests", "sat", "face", "edge", "plane",
                "pusher", "points", "manifolds", "pgs_manifolds", "pgs_points",
-               "push_evals", "sample_attempts", "clip_verts", "colours"]
+               "push_evals", "sample_attempts", "clip_verts", "colours", "bb_points", "pgs_bb_points"]
 F_GRASP1, F_INVALID_START, F_OUT_OF_WS, F_OVERFLOW, F_NOOP = 1, 2, 4, 8, 16
 
 
@@ -234,28 +234,3 @@ def footprints(state13, half, f32=True):
     out = np.zeros((st.shape[0], 8), np.float64)
     lib().oracle_footprints(1 if f32 else 0, st.shape[0], _ptr(st), _ptr(half), _ptr(out))
     return out
-
-
-# Hand-counted floating-point operations per event of the oracle's algorithm (FMA
-# counted as 2 = one multiply + one add, sqrt and divide as 1, compares as 0).  The
-# engine's event counters multiplied by these give the algorithmic flops of a launch.
-FLOPS_PER_EVENT = {
-    "box_steps": 3 + 30 + 45 + 18 + 34,   # gravity, R + world inverse inertia, AABB, integrate
-    "pair_tests": 0,                      # interval compares only
-    "sat": 420,                           # 15 axes with the 3x3 |C| matrix
-    "face": 160,                          # incident face, 4 side clips setup
-    "clip_verts": 20,                     # per clipped vertex: clip + depth
-    "edge": 90,
-    "plane": 8 * 16,
-    "pusher": 2 * 45,
-    "points": 3 * 40 + 15,                # per point: three effective masses + bias
-    "manifolds": 20,                      # tangent basis
-    "pgs_points": 2 * 50 + 14,            # normal row + 2-D friction row with disk clamp
-    "pgs_manifolds": 0,
-    "push_evals": 16 * 30,                # grasp angles (plus footprints, small)
-}
-
-
-def algorithmic_flops(events_row) -> float:
-    ev = dict(zip(EVENT_NAMES, [float(x) for x in events_row]))
-    return sum(FLOPS_PER_EVENT.get(k, 0) * v for k, v in ev.items())

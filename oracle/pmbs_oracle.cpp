@@ -60,7 +60,7 @@ enum { PLANE = -1, PUSHER = -2 };
 enum {
     EV_SUBSTEPS = 0, EV_BOX_STEPS, EV_PAIR_TESTS, EV_SAT, EV_FACE, EV_EDGE, EV_PLANE,
     EV_PUSHER, EV_POINTS, EV_MANIFOLDS, EV_PGS_MAN, EV_PGS_PTS, EV_PUSH_EVALS,
-    EV_SAMPLE_ATTEMPTS, EV_CLIP_VERTS, EV_COLOURS, NEV
+    EV_SAMPLE_ATTEMPTS, EV_CLIP_VERTS, EV_COLOURS, EV_BB_POINTS, EV_PGS_BB_POINTS, NEV
 };
 enum { F_GRASP1 = 1, F_INVALID_START = 2, F_OUT_OF_WS = 4, F_OVERFLOW = 8, F_NOOP = 16 };
 const int MAX_COLOURS = 32;
@@ -753,7 +753,9 @@ std::vector<Manifold> collide(Env& E, const oracle_params& P) {
         if (box_box(E.b[i], i, E.b[j], j, P, M, E.ev)) {
             const double mu = std::sqrt(E.b[i].mu * E.b[j].mu);
             M.mu = mu;
+            const size_t before = ms.size();
             emit(M);
+            if (ms.size() > before) E.ev[EV_BB_POINTS] += M.np;
         }
     }
     for (int i : pl.plane) {
@@ -897,6 +899,7 @@ void pgs(Env& E, std::vector<Manifold>& ms, int ncol, int iters, bool reverse_wi
                 solve_manifold(E, M);
                 E.ev[EV_PGS_MAN]++;
                 E.ev[EV_PGS_PTS] += M.np;
+                if (M.A >= 0 && M.B >= 0) E.ev[EV_PGS_BB_POINTS] += M.np;
             }
         }
 }

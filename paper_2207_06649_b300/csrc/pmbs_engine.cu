@@ -71,6 +71,8 @@ struct RolloutArgs {
     unsigned long long* events;
     float4* gscratch;
     int scratch_f4_per_warp;
+    long long watchdog_cycles;  // per environment and launch; exceeded -> counters[4] = 1
+    int* watchdog_flag;
 };
 
 // ------------------------------------------------------------------ device: one env
@@ -143,11 +145,12 @@ __device__ bool substep(const RolloutArgs& a, const WarpMem& W, int n, const Pus
     frames_and_aabb(W, n, lane, C.margin);
     __syncwarp();
     bool ovf = broadphase(W, n, lane, C.pair_cap, pu.active, Px, Py, C);
-    NarrowStats st{0, 0, 0, 0, 0, 0};
+    NarrowStats st{0, 0, 0, 0, 0, 0, 0};
     ovf |= narrowphase(W, lane, C, Px, Py, st);
     prepare(W, lane, C);
     ovf |= colour_manifolds(W, n, lane);
-    const int visits = pgs(W, lane, C.iters, V);
+    int bb_visits = 0;
+    const int visits = pgs(W, lane, C.iters, V, bb_visits);
     integrate(W, n, lane, C.dt);
     cnt.ev[EV_SUBSTEPS] += 1;
     cnt.ev[EV_BOX_STEPS] += n;
@@ -163,6 +166,8 @@ __device__ bool substep(const RolloutArgs& a, const WarpMem& W, int n, const Pus
     cnt.ev[EV_PGS_PTS] += __reduce_add_sync(0xffffffffu, visits);
     cnt.ev[EV_CLIP_VERTS] += st.clip_verts;
     cnt.ev[EV_COLOURS] += W.scal[5];
+    cnt.ev[EV_BB_POINTS] += st.bb_points;
+    cnt.ev[EV_PGS_BB_POINTS] += __reduce_add_sync(0xffffffffu, bb_visits);
     __syncwarp();
     return ovf;
 }
@@ -183,7 +188,9 @@ __device__ void run_env(const RolloutArgs& a, const WarpMem& W, int e, int lane)
     for (int k = 0; k < kNumEvents; k++) cnt.ev[k] = 0;
     bool ovf = false;
     int budget = a.max_substeps > 0 ? a.max_substeps : INT_MAX;
-    while (!pg.done && budget > 0) {
+    const long long t_start = clock64();
+    bool timed_out = false;
+    while (!pg.done && budget > 0 && !timed_out) {
         if (!pg.push_ready) {
             compute_footprints(W, n, lane);
             float push[4];
@@ -218,7 +225,11 @@ __device__ void run_env(const RolloutArgs& a, const WarpMem& W, int e, int lane)
             pg.s++;
             pg.steps++;
             budget--;
+            // bounded run time: give up (and report) instead of spinning indefinitely
+            timed_out = __shfl_sync(0xffffffffu, (int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
+            if (timed_out) break;
         }
+        if (timed_out) break;
         if (pg.s == C.substeps) {
             cnt.ev[EV_PUSH_EVALS] += 1;
             if (pg.k == 1 && a.child_on) store_state(W, n, a.child + (size_t)ei.box_off * 13, lane);
@@ -251,6 +262,7 @@ __device__ void run_env(const RolloutArgs& a, const WarpMem& W, int e, int lane)
         }
     }
     if (ovf) pg.flags |= FLAG_OVERFLOW;
+    if (timed_out && lane == 0) atomicExch(a.watchdog_flag, 1);
     store_state(W, n, a.state + (size_t)ei.box_off * 13, lane);
     if (lane == 0) {
         a.prog[e] = pg;
@@ -347,6 +359,12 @@ __global__ void __launch_bounds__(1024) prepare_batch_kernel(int n_envs, const i
         const int pos = atomicAdd(&hist[b], 1);
         order[pos] = e;
     }
+}
+
+// Scene table update: table[ids[i]] = desc[i].
+__global__ void scatter_desc_kernel(int n, const int32_t* ids, const SceneDesc* desc, SceneDesc* table) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) table[ids[i]] = desc[i];
 }
 
 // ------------------------------------------------------------------ snapshot evaluation
@@ -494,10 +512,16 @@ struct Arena {
 
 struct SceneRec {
     bool live = false;
-    size_t off = 0, bytes = 0;
+    size_t block = 0;             // arena block holding this scene's records
+    size_t rec_off = 0;           // byte offset of its records inside the arena
     int n = 0, target = 0;
     int uses = 0;                 // batches referencing it (host-submitted ids only)
     std::vector<float> host;      // records, kRecFloats per box
+};
+
+struct SceneBlock {
+    size_t bytes = 0;
+    int live = 0;                 // scenes of this block not yet freed
 };
 
 struct Batch {
@@ -534,6 +558,7 @@ struct pmbs_ctx {
     bool own_arena = false;
     Arena arena;
     std::vector<SceneRec> scenes;
+    std::map<size_t, SceneBlock> blocks;
     std::vector<int> free_ids;
     SceneDesc* d_table = nullptr;
     size_t table_off = 0;
@@ -845,6 +870,8 @@ pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps) {
     a.events = b.events;
     a.gscratch = ctx->gscratch;
     a.scratch_f4_per_warp = 3 * c.manifold_cap + 4 * c.contact_cap;
+    a.watchdog_cycles = 20LL * 1000 * 1000 * 1000;  // about 10 s of SM clock per env and launch
+    a.watchdog_flag = b.counters + 4;
     CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), ctx->stream));
     rollout_kernel<<<blocks, threads, smem, ctx->stream>>>(a);
     CU(cudaGetLastError());
@@ -856,11 +883,19 @@ Batch* find_batch(pmbs_ctx* ctx, int64_t id) {
     return it == ctx->batches.end() ? nullptr : &it->second;
 }
 
+// Copy the records of n_scenes scenes into one arena block, assign ids and publish the
+// descriptors to the device scene table (one copy of the records, one scatter).
 pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offset, const float* rec_host,
                             const int32_t* target, int32_t* out_ids) {
     const int total = box_offset[n_scenes] - box_offset[0];
-    const size_t bytes = sizeof(float) * kRecFloats * std::max(total, 1);
-    // one arena block per scene keeps freeing simple
+    const size_t rec_bytes = sizeof(float) * kRecFloats * (size_t)std::max(total, 1);
+    const size_t meta = sizeof(int32_t) * n_scenes, meta_al = (meta + 255) & ~(size_t)255;
+    const size_t desc_bytes = sizeof(SceneDesc) * n_scenes;
+    const size_t rec_al = (rec_bytes + 255) & ~(size_t)255;
+    // block layout: records | staging ids | staging descriptors (staging reused per call)
+    const size_t bytes = rec_al + meta_al + desc_bytes;
+    const size_t off = ctx->arena.alloc(bytes);
+    if (off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "scene store is full");
     std::vector<int> ids(n_scenes);
     for (int s = 0; s < n_scenes; s++) {
         int id;
@@ -869,40 +904,39 @@ pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offs
             ctx->free_ids.pop_back();
         } else {
             id = (int)ctx->scenes.size();
-            if (id >= kSceneTableCap) return fail(ctx, PMBS_E_OOM, "scene table full");
+            if (id >= kSceneTableCap) {
+                for (int t = 0; t < s; t++) ctx->free_ids.push_back(ids[t]);
+                ctx->arena.release(off, bytes);
+                return fail(ctx, PMBS_E_OOM, "scene table full");
+            }
             ctx->scenes.emplace_back();
         }
         ids[s] = id;
-        SceneRec& r = ctx->scenes[id];
+    }
+    char* base = (char*)arena_ptr(ctx, off);
+    std::vector<SceneDesc> desc(n_scenes);
+    for (int s = 0; s < n_scenes; s++) {
+        SceneRec& r = ctx->scenes[ids[s]];
         r.n = box_offset[s + 1] - box_offset[s];
         r.target = target[s];
-        r.bytes = sizeof(float) * kRecFloats * r.n;
-        r.off = ctx->arena.alloc(r.bytes);
-        if (r.off == SIZE_MAX) {
-            ctx->free_ids.push_back(id);
-            for (int t = 0; t < s; t++) {
-                SceneRec& q = ctx->scenes[ids[t]];
-                ctx->arena.release(q.off, q.bytes);
-                q.live = false;
-                ctx->free_ids.push_back(ids[t]);
-            }
-            return fail(ctx, PMBS_E_OOM, "scene store is full");
-        }
+        r.block = off;
+        r.rec_off = off + sizeof(float) * kRecFloats * (size_t)(box_offset[s] - box_offset[0]);
         r.host.assign(rec_host + (size_t)kRecFloats * (box_offset[s] - box_offset[0]),
                       rec_host + (size_t)kRecFloats * (box_offset[s + 1] - box_offset[0]));
         r.live = true;
         r.uses = 0;
+        desc[s] = SceneDesc{(const float*)arena_ptr(ctx, r.rec_off), r.n, r.target};
     }
-    (void)bytes;
-    std::vector<SceneDesc> desc(n_scenes);
-    for (int s = 0; s < n_scenes; s++) {
-        SceneRec& r = ctx->scenes[ids[s]];
-        float* dptr = (float*)arena_ptr(ctx, r.off);
-        CU(cudaMemcpyAsync(dptr, r.host.data(), r.bytes, cudaMemcpyHostToDevice, ctx->stream));
-        desc[s] = SceneDesc{dptr, r.n, r.target};
-    }
-    for (int s = 0; s < n_scenes; s++)
-        CU(cudaMemcpyAsync(ctx->d_table + ids[s], &desc[s], sizeof(SceneDesc), cudaMemcpyHostToDevice, ctx->stream));
+    SceneBlock blk;
+    blk.bytes = bytes;
+    blk.live = n_scenes;
+    ctx->blocks[off] = blk;
+    CU(cudaMemcpyAsync(base, rec_host, sizeof(float) * kRecFloats * (size_t)total, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(base + rec_al, ids.data(), meta, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(base + rec_al + meta_al, desc.data(), desc_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    scatter_desc_kernel<<<(n_scenes + 255) / 256, 256, 0, ctx->stream>>>(
+        n_scenes, (const int32_t*)(base + rec_al), (const SceneDesc*)(base + rec_al + meta_al), ctx->d_table);
+    CU(cudaGetLastError());
     CU(cudaStreamSynchronize(ctx->stream));
     for (int s = 0; s < n_scenes; s++) out_ids[s] = ids[s];
     return PMBS_OK;
@@ -1126,17 +1160,41 @@ pmbs_status pmbs_free_scenes(pmbs_ctx* ctx, int n, const int32_t* scene_ids) {
     }
     CU(cudaSetDevice(ctx->device));
     CU(cudaStreamSynchronize(ctx->stream));
+    std::vector<int32_t> ids;
     for (int i = 0; i < n; i++) {
         SceneRec& r = ctx->scenes[scene_ids[i]];
         if (!r.live) continue;
-        ctx->arena.release(r.off, r.bytes);
         r.live = false;
         r.host.clear();
-        const SceneDesc z{nullptr, 0, 0};
-        CU(cudaMemcpyAsync(ctx->d_table + scene_ids[i], &z, sizeof(z), cudaMemcpyHostToDevice, ctx->stream));
-        ctx->free_ids.push_back(scene_ids[i]);
+        r.host.shrink_to_fit();
+        ids.push_back(scene_ids[i]);
+        auto it = ctx->blocks.find(r.block);
+        if (it != ctx->blocks.end() && --it->second.live == 0) {
+            ctx->arena.release(it->first, it->second.bytes);
+            ctx->blocks.erase(it);
+        }
     }
-    CU(cudaStreamSynchronize(ctx->stream));
+    if (!ids.empty()) {
+        const size_t nb = ids.size();
+        const size_t meta_al = (sizeof(int32_t) * nb + 255) & ~(size_t)255;
+        const size_t off = ctx->arena.alloc(meta_al + sizeof(SceneDesc) * nb);
+        if (off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "no room to update the scene table");
+        char* base = (char*)arena_ptr(ctx, off);
+        std::vector<SceneDesc> z(nb, SceneDesc{nullptr, 0, 0});
+        cudaError_t e = cudaMemcpyAsync(base, ids.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + meta_al, z.data(), sizeof(SceneDesc) * nb, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) {
+            scatter_desc_kernel<<<(int)((nb + 255) / 256), 256, 0, ctx->stream>>>((int)nb, (const int32_t*)base,
+                                                                                 (const SceneDesc*)(base + meta_al),
+                                                                                 ctx->d_table);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        ctx->arena.release(off, meta_al + sizeof(SceneDesc) * nb);
+        if (e != cudaSuccess) return fail(ctx, PMBS_E_CUDA, std::string("free scenes: ") + cudaGetErrorString(e));
+        for (int32_t id : ids) ctx->free_ids.push_back(id);
+    }
     return PMBS_OK;
 }
 
@@ -1173,9 +1231,11 @@ pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps) {
         b->finished = true;
         return PMBS_OK;
     }
-    int done = 0;
-    CU(cudaMemcpyAsync(&done, b->counters + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    int cnt[5] = {0, 0, 0, 0, 0};
+    CU(cudaMemcpyAsync(cnt, b->counters, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    if (cnt[4]) return fail(ctx, PMBS_E_TIMEOUT, "an environment exceeded the per-launch time limit");
+    const int done = cnt[3];
     if (done >= b->n_envs) {
         b->finished = true;
         return PMBS_OK;
@@ -1195,6 +1255,9 @@ pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, flo
     if (!b->finished) return fail(ctx, PMBS_E_NOT_READY, "batch not finished");
     const int n = b->n_envs;
     if (n == 0) return PMBS_OK;
+    int wd = 0;
+    CU(cudaMemcpy(&wd, b->counters + 4, sizeof(int), cudaMemcpyDeviceToHost));
+    if (wd) return fail(ctx, PMBS_E_TIMEOUT, "an environment exceeded the per-launch time limit");
     if (out_cost) CU(cudaMemcpyAsync(out_cost, b->cost, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
     if (out_reward) CU(cudaMemcpyAsync(out_reward, b->reward, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
     if (out_flags) CU(cudaMemcpyAsync(out_flags, b->flags, n, cudaMemcpyDeviceToHost, ctx->stream));

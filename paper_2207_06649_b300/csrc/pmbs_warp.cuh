@@ -21,11 +21,11 @@ constexpr int kMaxBoxes = 64;
 constexpr int kMaxColours = 32;
 constexpr int kPlane = 255;   // body id of the table plane (static)
 constexpr int kPusher = 254;  // body id of the kinematic pusher
-constexpr int kNumEvents = 16;
+constexpr int kNumEvents = 18;
 enum {
     EV_SUBSTEPS = 0, EV_BOX_STEPS, EV_PAIR_TESTS, EV_SAT, EV_FACE, EV_EDGE, EV_PLANE, EV_PUSHER,
     EV_POINTS, EV_MANIFOLDS, EV_PGS_MAN, EV_PGS_PTS, EV_PUSH_EVALS, EV_SAMPLE_ATTEMPTS,
-    EV_CLIP_VERTS, EV_COLOURS
+    EV_CLIP_VERTS, EV_COLOURS, EV_BB_POINTS, EV_PGS_BB_POINTS
 };
 enum { FLAG_GRASP1 = 1, FLAG_INVALID_START = 2, FLAG_OUT_OF_WS = 4, FLAG_OVERFLOW = 8, FLAG_NOOP = 16 };
 
@@ -281,7 +281,7 @@ __device__ __forceinline__ bool broadphase(const WarpMem& W, int n, int lane, in
 
 // ------------------------------------------------------------------ narrowphase + emission
 struct NarrowStats {
-    int sat, face, edge, plane, pusher, clip_verts;
+    int sat, face, edge, plane, pusher, clip_verts, bb_points;
 };
 
 // Candidates in order (box-box pairs, plane, pusher); each yields at most four points
@@ -372,6 +372,7 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, int lane, const Si
         warp_excl_scan(ok ? cm.np : 0, lane, pemit);
         M += __popc(okm);
         P += pemit;
+        st.bb_points += __reduce_add_sync(0xffffffffu, (ok && kind == 0) ? cm.np : 0);
         if (viol) stop = true;
     }
     st.sat += __reduce_add_sync(0xffffffffu, sat);
@@ -509,7 +510,8 @@ __device__ __forceinline__ bool colour_manifolds(const WarpMem& W, int n, int la
 }
 
 // ------------------------------------------------------------------ PGS
-__device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pusherV) {
+// Returns the number of points; bb_pts gets them too when both bodies are dynamic.
+__device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pusherV, int& bb_pts) {
     const float4* mh = man_ptr(W, m);
     const float4 h0 = mh[0], h1 = mh[1], h2 = mh[2];
     const float3 n = f3(h0.x, h0.y, h0.z), t1 = f3(h1.x, h1.y, h1.z), t2 = f3(h2.x, h2.y, h2.z);
@@ -593,17 +595,19 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
         W.bv[B] = make_float4(vB.x, vB.y, vB.z, imB);
         W.bw[B] = make_float4(wB.x, wB.y, wB.z, muB);
     }
+    if (dA && dB) bb_pts += np;
     return np;
 }
 
-// Returns the number of point visits (normal + friction row pairs) of this lane.
-__device__ __forceinline__ int pgs(const WarpMem& W, int lane, int iters, float3 pusherV) {
+// Returns the number of point visits (normal + friction row pairs) of this lane, and
+// in bb_visits those of manifolds between two dynamic bodies.
+__device__ __forceinline__ int pgs(const WarpMem& W, int lane, int iters, float3 pusherV, int& bb_visits) {
     const int ncol = W.scal[5];
     int visits = 0;
     for (int it = 0; it < iters; it++) {
         for (int c = 0; c < ncol; c++) {
             const int a = W.cstart[c], b = W.cstart[c + 1];
-            for (int k = a + lane; k < b; k += 32) visits += solve_manifold(W, W.order[k], pusherV);
+            for (int k = a + lane; k < b; k += 32) visits += solve_manifold(W, W.order[k], pusherV, bb_visits);
             __syncwarp();
         }
     }
@@ -698,8 +702,10 @@ __device__ __forceinline__ bool grasp_check(const WarpMem& W, int n, int t, int 
                 }
             }
         }
-        const bool pair_ok = ok && __shfl_xor_sync(0xffffffffu, ok, 1);
-        any = any || __any_sync(0xffffffffu, pair_ok);
+        // every lane must execute the collectives (no short-circuit around them)
+        const bool partner = __shfl_xor_sync(0xffffffffu, ok, 1) != 0;
+        const bool found = __any_sync(0xffffffffu, ok && partner) != 0;
+        any = any || found;
     }
     return any;
 }

@@ -18,10 +18,10 @@ LIB_PATH = os.path.join(HERE, "libpmbs.so")
 PMBS_OK, PMBS_E_INVALID, PMBS_E_OOM, PMBS_E_CUDA, PMBS_E_NOT_READY, PMBS_E_TIMEOUT, PMBS_E_BUSY = range(7)
 FLAG_GRASP_AFTER_PUSH1, FLAG_INVALID_START, FLAG_OUT_OF_WORKSPACE, FLAG_CONTACT_OVERFLOW, FLAG_NOOP_PUSH = \
     1, 2, 4, 8, 16
-NUM_EVENTS = 16
+NUM_EVENTS = 18
 EVENT_NAMES = ["substeps", "box_steps", "pair_tests", "sat", "face", "edge", "plane",
                "pusher", "points", "manifolds", "pgs_manifolds", "pgs_points",
-               "push_evals", "sample_attempts", "clip_verts", "colours"]
+               "push_evals", "sample_attempts", "clip_verts", "colours", "bb_points", "pgs_bb_points"]
 
 EXPORTED = ["pmbs_default_config", "pmbs_create", "pmbs_create_with_arena", "pmbs_destroy",
             "pmbs_last_error", "pmbs_load_scenes", "pmbs_free_scenes", "pmbs_rollout_pushes",

@@ -73,27 +73,46 @@ def concat(parts) -> Scenes:
                    else np.zeros(0, np.int32)).astype(np.int32))
 
 
-def _rect_corners(cx, cy, hx, hy, yaw):
-    c, s = math.cos(yaw), math.sin(yaw)
-    pts = []
-    for sx, sy in ((1, 1), (-1, 1), (-1, -1), (1, -1)):
-        lx, ly = sx * hx, sy * hy
-        pts.append((cx + c * lx - s * ly, cy + s * lx + c * ly))
-    return np.array(pts)
+def _corners(cx, cy, hx, hy, yaw):
+    """Corners [..., 4, 2] of yawed rectangles (broadcast over leading dims)."""
+    c, s = np.cos(yaw), np.sin(yaw)
+    sx = np.array([1, -1, -1, 1], np.float64)
+    sy = np.array([1, 1, -1, -1], np.float64)
+    lx = sx * np.asarray(hx)[..., None]
+    ly = sy * np.asarray(hy)[..., None]
+    x = np.asarray(cx)[..., None] + np.asarray(c)[..., None] * lx - np.asarray(s)[..., None] * ly
+    y = np.asarray(cy)[..., None] + np.asarray(s)[..., None] * lx + np.asarray(c)[..., None] * ly
+    return np.stack([x, y], -1)
 
 
-def _rects_overlap(a, b, gap):
-    """Placement test between two yawed rectangles (cx, cy, hx, hy, yaw), each grown by
-    gap/2.  Separating-axis test over the four edge normals; used only to place boxes."""
-    ca = _rect_corners(a[0], a[1], a[2] + gap / 2, a[3] + gap / 2, a[4])
-    cb = _rect_corners(b[0], b[1], b[2] + gap / 2, b[3] + gap / 2, b[4])
-    for yaw in (a[4], b[4]):
-        for ax in ((math.cos(yaw), math.sin(yaw)), (-math.sin(yaw), math.cos(yaw))):
-            pa = ca @ np.array(ax)
-            pb = cb @ np.array(ax)
-            if pa.max() <= pb.min() or pb.max() <= pa.min():
-                return False
-    return True
+def _overlaps(cand, placed, gap):
+    """Placement test: candidate rectangles [K] (cx, cy, hx, hy, yaw) against placed
+    rectangles [P], each grown by gap/2.  Pairs whose circumscribed circles are apart
+    are free, pairs whose inscribed circles meet overlap, the rest go through the
+    separating-axis test over the four edge normals.  Returns bool [K, P] (True =
+    overlap).  Used only to place boxes."""
+    K, P = cand.shape[0], placed.shape[0]
+    g2 = gap / 2
+    d = np.hypot(cand[:, None, 0] - placed[None, :, 0], cand[:, None, 1] - placed[None, :, 1])
+    Rc = np.hypot(cand[:, 2] + g2, cand[:, 3] + g2)
+    Rp = np.hypot(placed[:, 2] + g2, placed[:, 3] + g2)
+    rc = np.minimum(cand[:, 2], cand[:, 3]) + g2
+    rp = np.minimum(placed[:, 2], placed[:, 3]) + g2
+    out = d < (rc[:, None] + rp[None, :])
+    amb = ~out & (d <= (Rc[:, None] + Rp[None, :]))
+    ki, pi = np.nonzero(amb)
+    if ki.size:
+        a, b = cand[ki], placed[pi]
+        ca = _corners(a[:, 0], a[:, 1], a[:, 2] + g2, a[:, 3] + g2, a[:, 4])
+        cb = _corners(b[:, 0], b[:, 1], b[:, 2] + g2, b[:, 3] + g2, b[:, 4])
+        sep = np.zeros(ki.size, bool)
+        for yaw in (a[:, 4], b[:, 4]):
+            for ax in ((np.cos(yaw), np.sin(yaw)), (-np.sin(yaw), np.cos(yaw))):
+                pa = ca[..., 0] * ax[0][:, None] + ca[..., 1] * ax[1][:, None]
+                pb = cb[..., 0] * ax[0][:, None] + cb[..., 1] * ax[1][:, None]
+                sep |= (pa.max(-1) <= pb.min(-1)) | (pb.max(-1) <= pa.min(-1))
+        out[ki, pi] = ~sep
+    return out
 
 
 def _yaw_quat(yaw):
@@ -116,25 +135,30 @@ def make_scene(rng: np.random.Generator, n: int, *, half_lo=0.015, half_hi=0.03,
         area = float(np.sum(4 * halves[:, 0] * halves[:, 1]))
         region_half = min(math.sqrt(area / density_scale) / 2, TABLE_HALF)
     placed = []
+    arr = np.zeros((0, 5))
     for i in range(n):
         hx, hy = halves[i, 0], halves[i, 1]
         # conservative footprint radius, so the footprint stays inside the region
         rad = math.hypot(hx, hy) if yaws[i] != 0 else max(hx, hy)
         lim = region_half - rad
+        if i == 0:
+            lim = max(lim, 1e-3)   # the target always fits, even in a tiny dense region
         ok = False
-        for a in range(attempts):
-            if lim <= 0:
-                break
-            if i == 0 and target_at_centre and a == 0:
-                cx, cy = 0.0, 0.0
-            else:
-                cx, cy = rng.uniform(-lim, lim, size=2)
-            r = (cx, cy, hx, hy, yaws[i])
-            if all(not _rects_overlap(r, (p[0], p[1], p[2], p[3], p[4]), PLACEMENT_GAP)
-                   for p in placed):
+        tried = 0
+        while lim > 0 and tried < attempts and not ok:
+            k = min(250, attempts - tried)
+            xy = rng.uniform(-lim, lim, size=(k, 2))
+            if i == 0 and target_at_centre and tried == 0:
+                xy[0] = 0.0
+            tried += k
+            cand = np.column_stack([xy, np.full(k, hx), np.full(k, hy), np.full(k, yaws[i])])
+            free = ~_overlaps(cand, arr, PLACEMENT_GAP).any(1) if len(arr) else np.ones(k, bool)
+            if free.any():
+                j = int(np.argmax(free))
+                cx, cy = xy[j]
                 placed.append((cx, cy, hx, hy, yaws[i], halves[i, 2], masses[i], mus[i]))
+                arr = np.vstack([arr, [cx, cy, hx, hy, yaws[i]]])
                 ok = True
-                break
         if not ok and i == 0:
             raise RuntimeError("target could not be placed")
     m = len(placed)
@@ -228,23 +252,39 @@ def _random_valid_push(rng, sc: Scenes, s: int, attempts=200):
     return np.array([0.19, 0.19, 0.19, 0.09], np.float32)
 
 
-def config_uneven(seed: int = 3, n_envs: int = 4096, n_lo=5, n_hi=40):
+def _uneven_scene(args):
+    ss, n_lo, n_hi = args
+    rng = np.random.default_rng(ss)
+    n = int(rng.integers(n_lo, n_hi + 1))
+    rho = rng.uniform(0.2, 0.6)
+    sc = make_scene(rng, n, half_lo=0.01, half_hi=0.04, mu_lo=0.3, mu_hi=0.8,
+                    yaw_hi=math.pi / 2, density_scale=rho, attempts=1000)
+    return sc, _random_valid_push(rng, sc, 0)
+
+
+def config_uneven(seed: int = 3, n_envs: int = 4096, n_lo=5, n_hi=40, workers: int = 0):
     """4096 independent scenes: n ~ U{5..40}, half-extents U[0.01,0.04], mu U[0.3,0.8],
     yaw U[0, pi/2), mass U[0.05,0.2], clutter density rho ~ U[0.2,0.6] (sum of footprint
     areas over the area of a centred square region, clipped to the table); one random
-    valid push per env; seeds for the device-sampled pushes."""
-    rng = np.random.default_rng(seed)
-    parts, pushes = [], []
-    for e in range(n_envs):
-        n = int(rng.integers(n_lo, n_hi + 1))
-        rho = rng.uniform(0.2, 0.6)
-        sc = make_scene(rng, n, half_lo=0.01, half_hi=0.04, mu_lo=0.3, mu_hi=0.8,
-                        yaw_hi=math.pi / 2, density_scale=rho, attempts=1000)
-        parts.append(sc)
-        pushes.append(_random_valid_push(rng, sc, 0))
-    scenes = concat(parts)
-    seeds = rng.integers(0, 2 ** 63, size=n_envs, dtype=np.uint64)
-    return scenes, np.stack(pushes), seeds
+    valid push per env; seeds for the device-sampled pushes.  Scene e draws from its own
+    child stream of `seed`, so the result does not depend on `workers` (processes used
+    to generate; 0 = all cores for large batches)."""
+    root = np.random.SeedSequence(seed)
+    children = root.spawn(n_envs + 1)
+    jobs = [(children[e], n_lo, n_hi) for e in range(n_envs)]
+    if workers == 0:
+        import os
+        workers = (os.cpu_count() or 1) if n_envs >= 256 else 1
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_uneven_scene, jobs, chunksize=max(1, n_envs // (8 * workers)))
+    else:
+        res = [_uneven_scene(j) for j in jobs]
+    scenes = concat([r[0] for r in res])
+    pushes = np.stack([r[1] for r in res]) if res else np.zeros((0, 4), np.float32)
+    seeds = np.random.default_rng(children[-1]).integers(0, 2 ** 63, size=n_envs, dtype=np.uint64)
+    return scenes, pushes, seeds
 
 
 def random_state_snapshot(rng: np.random.Generator, n: int, spread=0.06, tilt=0.3):

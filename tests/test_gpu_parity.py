@@ -78,7 +78,7 @@ def test_pairs_bit_exact(eng, orc, seed):
 
 def test_pairs_without_pusher_and_single_box(eng, orc):
     off = np.array([0, 1, 3], np.int32)
-    st = np.stack([G.box_row(0, 0, 0.02), G.box_row(0, 0, 0.02), G.box_row(0.03, 0, 0.02)]).astype(np.float32)
+    st = np.stack([G.box_row(0, 0, 0.015), G.box_row(0, 0, 0.02), G.box_row(0.03, 0, 0.02)]).astype(np.float32)
     h = np.full((3, 3), 0.015, np.float32)
     got = eng.eval_pairs(off, st, h)
     assert len(got[0][0]) == 0 and list(got[0][1]) == [0] and len(got[0][2]) == 0
