@@ -240,6 +240,40 @@ pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int warps_per_block, int smem_p
  * denominator for the contact solve). */
 pmbs_status pmbs_fp32_peak(pmbs_ctx* ctx, double* out_tflops);
 
+
+/* Allocation-free rollout.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory.  Two kinds of caller need it: a planning
+ * loop on a robot that, after start-up, must not pay cudaMalloc's device-wide
+ * synchronisation and unbounded latency between decisions; and a library embedded in a
+ * host process whose device memory is already reserved by another framework's caching
+ * allocator, where a fresh allocation fails or fragments that pool.
+ *
+ * It needs no context.  The caller passes every input and output as device pointers on
+ * device cfg->device and the stream cuda_stream (a cudaStream_t, NULL = legacy default):
+ *   d_box_offset [n_envs+1] int32, CSR over boxes; d_records [B][18] floats per box
+ *   (x y z qw qx qy qz vx vy vz wx wy wz, half extents x y z, mass, mu); d_target [n_envs]
+ *   local target index; d_first_push [n_envs][4]; d_seeds [n_envs] (may be NULL when
+ *   depth == 1).  Outputs: d_state_out [B][13] final states, d_cost, d_reward, d_flags
+ *   [n_envs] with the meaning of pmbs_query_cost.  Physics constants come from *cfg.
+ * The results equal those of pmbs_rollout_pushes + pmbs_step + pmbs_query_cost for the
+ * same inputs.  All scratch (descriptors, progress, counters, per-warp contact spill
+ * regions) lives in one file-scope device array of 32 MiB that every device loading the
+ * library holds until the process exits; at most 16384 environments per call, and
+ * cfg->max_boxes_per_env <= 64.  Larger requests return PMBS_E_INVALID before any GPU
+ * work.  The first call on a device looks up that array's device address (and sets the
+ * kernel's shared-memory limit); make that first call before any stream capture.  The
+ * call synchronises cuda_stream and returns PMBS_OK, PMBS_E_INVALID (bad argument, or
+ * an environment with a box count outside 1..max_boxes_per_env or a target out of range:
+ * such environments are not simulated and their outputs are undefined), PMBS_E_TIMEOUT
+ * or PMBS_E_CUDA.  Every call shares the one array and starts by clearing what must start
+ * at zero; calls whose GPU work overlaps (several threads or streams at once) race on it
+ * and must be serialised by the caller.  It allocates no device memory. */
+pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_stream, int n_envs,
+                                 const int32_t* d_box_offset, const float* d_records,
+                                 const int32_t* d_target, const float* d_first_push,
+                                 const uint64_t* d_seeds, int depth, float* d_state_out,
+                                 int32_t* d_cost, float* d_reward, uint8_t* d_flags);
+
 #ifdef __cplusplus
 }
 #endif

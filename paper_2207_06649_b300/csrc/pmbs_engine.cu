@@ -1495,3 +1495,181 @@ pmbs_status pmbs_fp32_peak(pmbs_ctx* ctx, double* out_tflops) {
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free entry
+// pmbs_rollout_noalloc runs the same rollout kernel without any device allocation: every
+// piece of scratch it needs (environment descriptors, progress records, work order,
+// counters, event counters, step counts and the per-warp contact spill regions) lives in
+// one file-scope device array of fixed size, shared by all calls on a device.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB on every device that loads the library
+constexpr int kNoAllocMaxEnvs = 16384;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch on that device
+    int num_sms = 0;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Descriptors, order and cleared per-call state for caller-provided environments.
+// Environment e owns records box_offset[e] .. box_offset[e+1]-1 (18 floats each: state13,
+// half extents, mass, mu).  Environments with a box count outside [1, max_boxes] or a
+// target out of range are not simulated; counters[1] records that.
+__global__ void __launch_bounds__(1024) noalloc_setup_kernel(int n_envs, int max_boxes, const int32_t* box_offset,
+                                                             const float* records, const int32_t* target,
+                                                             EnvIn* env, int* order, EnvProg* prog, int* counters,
+                                                             unsigned long long* events, int32_t* steps) {
+    __shared__ int hist[kMaxBoxes + 2];
+    const int t = threadIdx.x;
+    if (t < kMaxBoxes + 2) hist[t] = 0;
+    if (t < 8) counters[t] = 0;
+    __syncthreads();
+    for (int e = t; e < n_envs; e += 1024) {
+        const int b0 = box_offset[e];
+        int n = box_offset[e + 1] - b0;
+        const int tg = target[e];
+        EnvProg p;
+        memset(&p, 0, sizeof(p));
+        if (n < 1 || n > max_boxes || tg < 0 || tg >= n) {
+            atomicOr(counters + 1, 1);
+            p.done = 1;  // not simulated
+            n = 0;
+        }
+        prog[e] = p;
+        env[e] = EnvIn{records + (size_t)kRecFloats * b0, n, tg, b0, -1};
+        for (int k = 0; k < kNumEvents; k++) events[(size_t)e * kNumEvents + k] = 0ull;
+        steps[e] = 0;
+        atomicAdd(&hist[kMaxBoxes - min(n, kMaxBoxes)], 1);
+    }
+    __syncthreads();
+    if (t == 0) {
+        int acc = 0;
+        for (int b = 0; b <= kMaxBoxes; b++) {
+            const int c = hist[b];
+            hist[b] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < n_envs; e += 1024) {
+        const int pos = atomicAdd(&hist[kMaxBoxes - min(env[e].n, kMaxBoxes)], 1);
+        order[pos] = e;
+    }
+}
+
+}  // namespace
+
+extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_stream, int n_envs,
+                                            const int32_t* d_box_offset, const float* d_records,
+                                            const int32_t* d_target, const float* d_first_push,
+                                            const uint64_t* d_seeds, int depth, float* d_state_out,
+                                            int32_t* d_cost, float* d_reward, uint8_t* d_flags) {
+    if (!cfg) return PMBS_E_INVALID;
+    const pmbs_config& c = *cfg;
+    if (n_envs < 0 || n_envs > kNoAllocMaxEnvs || depth < 1 || depth > 64 || c.max_boxes_per_env < 1 ||
+        c.max_boxes_per_env > kMaxBoxes || c.device < 0 || c.device >= kNoAllocMaxDevices || c.grasp_angles < 1 ||
+        c.grasp_angles > 32 || c.sample_attempts < 1 || c.sample_attempts > 32 || c.contact_cap < 4 ||
+        c.manifold_cap < 1 || c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096)
+        return PMBS_E_INVALID;
+    if (n_envs == 0) return PMBS_OK;
+    if (!d_box_offset || !d_records || !d_target || !d_first_push || (!d_seeds && depth > 1) || !d_state_out ||
+        !d_cost || !d_reward || !d_flags)
+        return PMBS_E_INVALID;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(c.device) != cudaSuccess) return PMBS_E_CUDA;
+    NoAllocDevice& dv = g_noalloc_dev[c.device];
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!dv.ready) {
+            // once per device, with that device current: the device address of the scratch
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PMBS_E_CUDA;
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return PMBS_E_CUDA;
+            if (cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+                cudaSuccess)
+                return PMBS_E_CUDA;
+            dv.scratch = (unsigned char*)p;
+            dv.num_sms = sms;
+            dv.ready = true;
+        }
+    }
+    // scratch layout: per-environment records, then per-warp contact spill regions
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t ne = (size_t)n_envs;
+    const size_t o_env = take(sizeof(EnvIn) * ne), o_order = take(sizeof(int) * ne), o_prog = take(sizeof(EnvProg) * ne),
+                 o_cnt = take(sizeof(int) * 8), o_ev = take(sizeof(unsigned long long) * kNumEvents * ne),
+                 o_steps = take(sizeof(int32_t) * ne);
+    const int f4_per_warp = 3 * c.manifold_cap + 4 * c.contact_cap;
+    const size_t warp_bytes = sizeof(float4) * (size_t)f4_per_warp;
+    if (off >= kNoAllocScratchBytes || (kNoAllocScratchBytes - off) / warp_bytes < 4) return PMBS_E_INVALID;
+    const int max_warps = (int)std::min<size_t>((kNoAllocScratchBytes - off) / warp_bytes, 1 << 20);
+    unsigned char* S = dv.scratch;
+    EnvIn* env = (EnvIn*)(S + o_env);
+    int* order = (int*)(S + o_order);
+    EnvProg* prog = (EnvProg*)(S + o_prog);
+    int* counters = (int*)(S + o_cnt);
+    unsigned long long* events = (unsigned long long*)(S + o_ev);
+    int32_t* steps = (int32_t*)(S + o_steps);
+    float4* spill = (float4*)(S + off);
+
+    const int nb = c.max_boxes_per_env, wpb = 4;
+    const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
+    const Layout L = make_layout(nb, pairS, 0, 0, c.manifold_cap);
+    const size_t smem = (size_t)L.bytes * wpb;
+    if (smem > 227 * 1024) return PMBS_E_INVALID;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel, 32 * wpb, smem) != cudaSuccess)
+        return PMBS_E_CUDA;
+    if (per_sm < 1) return PMBS_E_INVALID;
+    const int blocks = std::max(1, std::min({(n_envs + wpb - 1) / wpb, per_sm * dv.num_sms, max_warps / wpb}));
+
+    noalloc_setup_kernel<<<1, 1024, 0, stream>>>(n_envs, nb, d_box_offset, d_records, d_target, env, order, prog,
+                                                 counters, events, steps);
+    if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;
+    RolloutArgs a;
+    fill_const(c, a.C);
+    a.L = L;
+    a.n_envs = n_envs;
+    a.depth = depth;
+    a.max_substeps = 0;
+    a.child_on = 0;
+    a.env = env;
+    a.order = order;
+    a.queue_head = counters + 2;
+    a.done_count = counters + 3;
+    a.first_push = (const float4*)d_first_push;
+    a.seeds = d_seeds ? d_seeds : (const uint64_t*)(S + o_ev);  // unread when depth == 1
+    a.prog = prog;
+    a.state = d_state_out;
+    a.child = nullptr;
+    a.cost = d_cost;
+    a.reward = d_reward;
+    a.flags = d_flags;
+    a.steps = steps;
+    a.events = events;
+    a.gscratch = spill;
+    a.scratch_f4_per_warp = f4_per_warp;
+    a.watchdog_cycles = 20LL * 1000 * 1000 * 1000;
+    a.watchdog_flag = counters + 4;
+    rollout_kernel<<<blocks, 32 * wpb, smem, stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;
+    int host_cnt[8];
+    if (cudaMemcpyAsync(host_cnt, counters, sizeof(host_cnt), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return PMBS_E_CUDA;
+    if (host_cnt[4]) return PMBS_E_TIMEOUT;
+    if (host_cnt[1]) return PMBS_E_INVALID;
+    return PMBS_OK;
+}

@@ -28,7 +28,7 @@ EXPORTED = ["pmbs_default_config", "pmbs_create", "pmbs_create_with_arena", "pmb
             "pmbs_rollout_pushes_device", "pmbs_step", "pmbs_query_cost", "pmbs_query_cost_device",
             "pmbs_query_states", "pmbs_query_events", "pmbs_batch_info", "pmbs_release_batch",
             "pmbs_eval_pairs", "pmbs_eval_grasp", "pmbs_eval_sample", "pmbs_eval_start_blocked",
-            "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak"]
+            "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_rollout_noalloc"]
 
 
 class pmbs_config(C.Structure):
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         "pmbs_launch_shape": ([vp, i32, vp, vp, vp, vp], i32),
         "pmbs_set_launch_shape": ([vp, i32, i32, i32], i32),
         "pmbs_fp32_peak": ([vp, P(C.c_double)], i32),
+        "pmbs_rollout_noalloc": ([P(pmbs_config), vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
