@@ -97,9 +97,11 @@ typedef struct {
     int contact_cap;            /* 512 contact points per environment */
     int manifold_cap;           /* 256 manifolds per environment (<= 1024) */
     int pair_cap;               /* 1024 box-box broadphase pairs per environment */
-    int warps_per_block;        /* launch shape; 0 = autotune */
-    int smem_points;            /* contact points kept in shared memory per env; -1 = autotune */
-    int smem_manifolds;         /* manifolds kept in shared memory per env; -1 = autotune */
+    int lanes_per_env;          /* lanes per environment (8, 16 or 32; a warp runs 32 / that
+                                   environments); 0 = autotune */
+    int warps_per_block;        /* launch shape (1, 2 or 4); 0 = autotune */
+    int smem_points;            /* contact point slots (4 per manifold) in shared memory; -1 = auto */
+    int smem_manifolds;         /* manifolds kept in shared memory per env (wins); -1 = auto */
 } pmbs_config;
 
 /* Fill *cfg with the defaults listed above.  Never fails. */
@@ -224,16 +226,19 @@ pmbs_status pmbs_eval_start_blocked(pmbs_ctx* ctx, int n_envs, const int32_t* bo
                                     const float* starts, uint8_t* out_blocked);
 
 /* Launch shape the context uses for a batch whose largest scene has max_boxes boxes:
- * warps per block, contact points and manifolds kept in shared memory per environment,
- * and shared bytes per block.  Chosen by the autotuner unless fixed in the config. */
-pmbs_status pmbs_launch_shape(pmbs_ctx* ctx, int max_boxes, int32_t* out_warps_per_block,
-                              int32_t* out_smem_points, int32_t* out_smem_manifolds,
-                              int32_t* out_smem_bytes);
+ * lanes per environment, warps per block, contact point slots and manifolds kept in
+ * shared memory per environment, and shared bytes per block.  Chosen by the tuning rule
+ * (or a tuned table, see pmbs_set_launch_shape) unless fixed in the config. */
+pmbs_status pmbs_launch_shape(pmbs_ctx* ctx, int max_boxes, int32_t* out_lanes_per_env,
+                              int32_t* out_warps_per_block, int32_t* out_smem_points,
+                              int32_t* out_smem_manifolds, int32_t* out_smem_bytes);
 
-/* Override the launch shape for subsequent batches (warps_per_block in {1,2,4,8}; smem
- * points/manifolds >= 0).  Changes scheduling only: results are bit-identical. */
-pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int warps_per_block, int smem_points,
-                                  int smem_manifolds);
+/* Override the launch shape for subsequent batches (lanes_per_env in {8,16,32}, 0 = auto;
+ * warps_per_block in {1,2,4}, 0 = auto; smem points/manifolds >= 0, -1 = auto).  Changes
+ * scheduling only: every environment's arithmetic, and so every result, is bit-identical
+ * across shapes. */
+pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int lanes_per_env, int warps_per_block,
+                                  int smem_points, int smem_manifolds);
 
 /* Measured FP32 FMA throughput of the device (TFLOP/s) from a microbenchmark of
  * independent FMA chains at full occupancy; the paper has no counterpart (roofline

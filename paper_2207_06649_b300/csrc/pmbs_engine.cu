@@ -54,6 +54,7 @@ struct EnvProg {
 struct RolloutArgs {
     SimConst C;
     Layout L;
+    int G;  // lanes per environment (8, 16 or 32); a warp runs 32 / G environments
     int n_envs, depth, max_substeps, child_on;
     const EnvIn* env;
     const int* order;
@@ -75,10 +76,15 @@ struct RolloutArgs {
     int* watchdog_flag;
 };
 
-// ------------------------------------------------------------------ device: one env
-__device__ void load_env(const RolloutArgs& a, const WarpMem& W, const EnvIn& ei, bool from_scene, int lane) {
+// ------------------------------------------------------------------ device: environments
+// Load an environment's state into its group's shared memory (from the scene records when
+// it has not started, else from the batch state).  Every lane calls this; groups with
+// on = false load nothing.
+__device__ __forceinline__ void load_env(const RolloutArgs& a, const WarpMem& W, const EnvIn& ei, bool on,
+                                         bool from_scene, const Grp& g) {
     const int NB = W.NB;
-    for (int i = lane; i < ei.n; i += 32) {
+    const int n = on ? ei.n : 0;
+    for (int i = g.gl; i < n; i += g.G) {
         const float* r = ei.rec + kRecFloats * i;
         const float* s = from_scene ? r : a.state + (size_t)(ei.box_off + i) * 13;
         W.x[i] = s[0];
@@ -102,9 +108,10 @@ __device__ void load_env(const RolloutArgs& a, const WarpMem& W, const EnvIn& ei
     __syncwarp();
 }
 
-__device__ void store_state(const WarpMem& W, int n, float* dst, int lane) {
+// Copy an environment's state rows to dst (no collective).
+__device__ __forceinline__ void store_state(const WarpMem& W, int n, float* dst, const Grp& g) {
     const int NB = W.NB;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = g.gl; i < n; i += g.G) {
         float* s = dst + (size_t)i * 13;
         const float4 v = W.bv[i], w = W.bw[i];
         s[0] = W.x[i];
@@ -127,86 +134,127 @@ struct Counters {
     unsigned long long ev[kNumEvents];
 };
 
-// One substep of one environment (all lanes).  Returns true on a cap overflow.
-__device__ bool substep(const RolloutArgs& a, const WarpMem& W, int n, const Pusher& pu, int s, int lane,
-                        Counters& cnt) {
+// One substep of the group's environment (on = false: the group only takes part in the
+// warp's collectives).  Returns true on a cap overflow.
+__device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, int n_env, bool on, const Pusher& pu,
+                                        int s, const Grp& g, Counters& cnt) {
     const SimConst& C = a.C;
+    const int n = on ? n_env : 0;
     const int done = s < pu.moving ? s : pu.moving;
     const float travel = (C.pspeed * C.dt) * (float)done;
     const float Px = pu.sx + pu.dx * travel, Py = pu.sy + pu.dy * travel;
     const float3 V = (pu.active && s < pu.moving) ? f3(pu.dx * C.pspeed, pu.dy * C.pspeed, 0.f) : f3(0.f, 0.f, 0.f);
-    for (int i = lane; i < n; i += 32) {
+    for (int i = g.gl; i < n; i += g.G) {
         float4 v = W.bv[i];
         v.x += C.gx * C.dt;
         v.y += C.gy * C.dt;
         v.z += C.gz * C.dt;
         W.bv[i] = v;
     }
-    frames_and_aabb(W, n, lane, C.margin);
+    frames_and_aabb(W, n, g, C.margin);
     __syncwarp();
-    bool ovf = broadphase(W, n, lane, C.pair_cap, pu.active, Px, Py, C);
+    bool ovf = broadphase(W, n, g, C.pair_cap, on && pu.active, Px, Py, C);
     NarrowStats st{0, 0, 0, 0, 0, 0, 0};
-    ovf |= narrowphase(W, lane, C, Px, Py, st);
-    prepare(W, lane, C);
-    ovf |= colour_manifolds(W, n, lane);
+    ovf |= narrowphase(W, g, on, C, Px, Py, st);
+    prepare(W, g, on, C);
+    ovf |= colour_manifolds(W, n, g, on);
     int bb_visits = 0;
-    const int visits = pgs(W, lane, C.iters, V, bb_visits);
-    integrate(W, n, lane, C.dt);
-    cnt.ev[EV_SUBSTEPS] += 1;
-    cnt.ev[EV_BOX_STEPS] += n;
-    cnt.ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
-    cnt.ev[EV_SAT] += st.sat;
-    cnt.ev[EV_FACE] += st.face;
-    cnt.ev[EV_EDGE] += st.edge;
-    cnt.ev[EV_PLANE] += st.plane;
-    cnt.ev[EV_PUSHER] += st.pusher;
-    cnt.ev[EV_POINTS] += W.scal[4];
-    cnt.ev[EV_MANIFOLDS] += W.scal[3];
-    cnt.ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal[6];
-    cnt.ev[EV_PGS_PTS] += __reduce_add_sync(0xffffffffu, visits);
-    cnt.ev[EV_CLIP_VERTS] += st.clip_verts;
-    cnt.ev[EV_COLOURS] += W.scal[5];
-    cnt.ev[EV_BB_POINTS] += st.bb_points;
-    cnt.ev[EV_PGS_BB_POINTS] += __reduce_add_sync(0xffffffffu, bb_visits);
+    const int visits = pgs(W, g, on, C.iters, V, bb_visits);
+    integrate(W, n, g, C.dt);
+    const int v_all = g.sum(visits), v_bb = g.sum(bb_visits);
+    if (on) {
+        cnt.ev[EV_SUBSTEPS] += 1;
+        cnt.ev[EV_BOX_STEPS] += n;
+        cnt.ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
+        cnt.ev[EV_SAT] += st.sat;
+        cnt.ev[EV_FACE] += st.face;
+        cnt.ev[EV_EDGE] += st.edge;
+        cnt.ev[EV_PLANE] += st.plane;
+        cnt.ev[EV_PUSHER] += st.pusher;
+        cnt.ev[EV_POINTS] += W.scal[4];
+        cnt.ev[EV_MANIFOLDS] += W.scal[3];
+        cnt.ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal[6];
+        cnt.ev[EV_PGS_PTS] += v_all;
+        cnt.ev[EV_CLIP_VERTS] += st.clip_verts;
+        cnt.ev[EV_COLOURS] += W.scal[5];
+        cnt.ev[EV_BB_POINTS] += st.bb_points;
+        cnt.ev[EV_PGS_BB_POINTS] += v_bb;
+    }
     __syncwarp();
-    return ovf;
+    return ovf && on;
 }
 
-__device__ void run_env(const RolloutArgs& a, const WarpMem& W, int e, int lane) {
+// The environment slots of one warp: each group pulls environments from the work queue
+// (largest first) and runs them push by push; a group whose environment finishes early
+// (target graspable, Sec. IV-C: early-terminated environments are re-purposed) takes the
+// next one while the other groups continue.  Push set-up and end-of-push phases run when
+// any group needs them; groups without work take part in the collectives only.
+__device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W, const Grp& g) {
     const SimConst& C = a.C;
-    const EnvIn ei = a.env[e];
-    EnvProg pg = a.prog[e];
-    if (pg.done) return;
-    const int n = ei.n;
-    load_env(a, W, ei, pg.k == 0, lane);
-    if (pg.k == 0) {
-        pg.k = 1;
-        pg.s = 0;
-        pg.push_ready = 0;
-    }
+    int e = -1;
+    bool exhausted = false;
+    EnvIn ei{nullptr, 0, 0, 0, -1};
+    EnvProg pg;
+    memset(&pg, 0, sizeof(pg));
+    int budget = 0;
+    long long t_start = 0;
+    bool ovf = false, timed_out = false;
     Counters cnt;
     for (int k = 0; k < kNumEvents; k++) cnt.ev[k] = 0;
-    bool ovf = false;
-    int budget = a.max_substeps > 0 ? a.max_substeps : INT_MAX;
-    const long long t_start = clock64();
-    bool timed_out = false;
-    while (!pg.done && budget > 0 && !timed_out) {
-        if (!pg.push_ready) {
-            compute_footprints(W, n, lane);
-            float push[4];
-            if (pg.k == 1) {
-                const float4 fp = a.first_push[e];
-                push[0] = fp.x; push[1] = fp.y; push[2] = fp.z; push[3] = fp.w;
-                if (start_blocked(W, n, lane, fp.x, fp.y, C.pr)) {
+    for (;;) {
+        // 1. fetch
+        const bool need = e < 0 && !exhausted;
+        int slot = 0;
+        if (need && g.gl == 0) slot = atomicAdd(a.queue_head, 1);
+        slot = g.bcast(slot, 0);
+        bool fresh = false;
+        if (need) {
+            if (slot < a.n_envs) {
+                e = a.order[slot];
+                ei = a.env[e];
+                pg = a.prog[e];
+                if (pg.done) e = -1;
+                else fresh = true;
+            } else {
+                exhausted = true;
+            }
+        }
+        load_env(a, W, ei, fresh, pg.k == 0, g);
+        if (fresh) {
+            if (pg.k == 0) {
+                pg.k = 1;
+                pg.s = 0;
+                pg.push_ready = 0;
+            }
+            budget = a.max_substeps > 0 ? a.max_substeps : INT_MAX;
+            ovf = false;
+            timed_out = false;
+            t_start = clock64();
+            for (int k = 0; k < kNumEvents; k++) cnt.ev[k] = 0;
+        }
+        const bool active = e >= 0;
+        if (!__any_sync(kFull, active || !exhausted)) break;
+        // 2. push set-up: the first push's start check, or a sampled push
+        const bool setup = active && !pg.push_ready;
+        if (__any_sync(kFull, setup)) {
+            compute_footprints(W, setup ? ei.n : 0, g);
+            const bool first = setup && pg.k == 1;
+            const float4 fp = first ? a.first_push[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool blocked = start_blocked(W, first ? ei.n : 0, g, fp.x, fp.y, C.pr);
+            const bool samp = setup && pg.k > 1;
+            float push[4] = {fp.x, fp.y, fp.z, fp.w};
+            const int at = sample_push(W, ei.n, g, samp, samp ? a.seeds[e] : 0ull, pg.k, C, push);
+            if (first) {
+                if (blocked) {
                     pg.flags |= FLAG_INVALID_START;
                     pg.done = 1;
                     pg.cost = a.depth + 1;
                     pg.reward = 0.f;
-                    break;
+                } else {
+                    pg.noop = 0;
                 }
-                pg.noop = 0;
-            } else {
-                const int at = sample_push(W, n, lane, a.seeds[e], pg.k, C, push);
+            }
+            if (samp) {
                 cnt.ev[EV_SAMPLE_ATTEMPTS] += at < 0 ? C.attempts : at + 1;
                 if (at < 0) {
                     pg.noop = 1;
@@ -216,35 +264,42 @@ __device__ void run_env(const RolloutArgs& a, const WarpMem& W, int e, int lane)
                     pg.noop = 0;
                 }
             }
-            for (int i = 0; i < 4; i++) pg.push[i] = push[i];
-            pg.push_ready = 1;
+            if (setup && !pg.done) {
+                for (int i = 0; i < 4; i++) pg.push[i] = push[i];
+                pg.push_ready = 1;
+            }
         }
+        // 3. one substep
+        const bool run = active && !pg.done && pg.s < C.substeps && budget > 0;
         const Pusher pu = make_pusher(C, pg.push, pg.noop != 0);
-        while (pg.s < C.substeps && budget > 0) {
-            ovf |= substep(a, W, n, pu, pg.s, lane, cnt);
+        ovf |= substep(a, W, ei.n, run, pu, pg.s, g, cnt);
+        // bounded run time per environment and launch (the shuffle runs in every lane)
+        const bool late = g.bcast((int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
+        if (run) {
             pg.s++;
             pg.steps++;
             budget--;
-            // bounded run time: give up (and report) instead of spinning indefinitely
-            timed_out = __shfl_sync(0xffffffffu, (int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
-            if (timed_out) break;
+            timed_out = late;
         }
-        if (timed_out) break;
-        if (pg.s == C.substeps) {
-            cnt.ev[EV_PUSH_EVALS] += 1;
-            if (pg.k == 1 && a.child_on) store_state(W, n, a.child + (size_t)ei.box_off * 13, lane);
+        // 4. end of push: workspace, grasp test, cost and reward
+        const bool endp = active && !pg.done && !timed_out && pg.s == C.substeps;
+        if (__any_sync(kFull, endp)) {
+            if (endp && pg.k == 1 && a.child_on) store_state(W, ei.n, a.child + (size_t)ei.box_off * 13, g);
             bool out = false;
-            for (int i = lane; i < n; i += 32)
+            for (int i = g.gl; endp && i < ei.n; i += g.G)
                 out = out || fabsf(W.x[i]) > C.table_hx || fabsf(W.x[W.NB + i]) > C.table_hy;
-            out = __any_sync(0xffffffffu, out);
-            if (out) {
-                pg.flags |= FLAG_OUT_OF_WS;
-                pg.done = 1;
-                pg.cost = a.depth + 1;
-                pg.reward = 0.f;
-            } else {
-                compute_footprints(W, n, lane);
-                if (grasp_check(W, n, ei.target, lane, C)) {
+            out = g.any(out);
+            const bool test = endp && !out;
+            compute_footprints(W, test ? ei.n : 0, g);
+            const bool graspable = grasp_check(W, ei.n, ei.target, g, test, C);
+            if (endp) {
+                cnt.ev[EV_PUSH_EVALS] += 1;
+                if (out) {
+                    pg.flags |= FLAG_OUT_OF_WS;
+                    pg.done = 1;
+                    pg.cost = a.depth + 1;
+                    pg.reward = 0.f;
+                } else if (graspable) {
                     pg.done = 1;
                     pg.cost = pg.k;
                     pg.reward = powf(C.gamma, (float)(pg.k - 1));
@@ -260,38 +315,41 @@ __device__ void run_env(const RolloutArgs& a, const WarpMem& W, int e, int lane)
                 }
             }
         }
-    }
-    if (ovf) pg.flags |= FLAG_OVERFLOW;
-    if (timed_out && lane == 0) atomicExch(a.watchdog_flag, 1);
-    store_state(W, n, a.state + (size_t)ei.box_off * 13, lane);
-    if (lane == 0) {
-        a.prog[e] = pg;
-        unsigned long long* ev = a.events + (size_t)e * kNumEvents;
-        for (int k = 0; k < kNumEvents; k++) ev[k] += cnt.ev[k];
-        a.steps[e] = pg.steps;
-        if (pg.done) {
-            a.cost[e] = pg.cost;
-            a.reward[e] = pg.reward;
-            a.flags[e] = (uint8_t)pg.flags;
-            atomicAdd(a.done_count, 1);
+        // 5. retire: write the environment back and free the slot
+        const bool fin = active && (pg.done || budget <= 0 || timed_out);
+        if (fin) {
+            if (ovf) pg.flags |= FLAG_OVERFLOW;
+            store_state(W, ei.n, a.state + (size_t)ei.box_off * 13, g);
+            if (g.gl == 0) {
+                a.prog[e] = pg;
+                unsigned long long* ev = a.events + (size_t)e * kNumEvents;
+                for (int k = 0; k < kNumEvents; k++) ev[k] += cnt.ev[k];
+                a.steps[e] = pg.steps;
+                if (pg.done) {
+                    a.cost[e] = pg.cost;
+                    a.reward[e] = pg.reward;
+                    a.flags[e] = (uint8_t)pg.flags;
+                    atomicAdd(a.done_count, 1);
+                }
+                if (timed_out) atomicExch(a.watchdog_flag, 1);
+            }
+            e = -1;
         }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
-__global__ void __launch_bounds__(256) rollout_kernel(const __grid_constant__ RolloutArgs a) {
+// 128 threads (up to four warps) per block and a register budget for two blocks per SM:
+// the solver keeps its working set in registers without spilling.
+__global__ void __launch_bounds__(128, 2) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    const WarpMem W = bind_mem(a.L, smem + (size_t)wib * a.L.bytes,
-                               a.gscratch + (size_t)gw * a.scratch_f4_per_warp);
-    for (;;) {
-        int slot = 0;
-        if (lane == 0) slot = atomicAdd(a.queue_head, 1);
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (slot >= a.n_envs) break;
-        run_env(a, W, a.order[slot], lane);
-    }
+    const Grp g(a.G, lane);
+    const int per_warp = 32 / a.G;
+    const int slot = wib * per_warp + (lane / a.G);
+    const size_t gslot = (size_t)blockIdx.x * (blockDim.x >> 5) * per_warp + slot;
+    const WarpMem W = bind_mem(a.L, smem + (size_t)slot * a.L.bytes, a.gscratch + gslot * a.scratch_f4_per_warp);
+    run_slots(a, W, g);
 }
 
 // Batch set-up: per-env scene descriptor and box offset (block-wide scan), processing
@@ -395,6 +453,7 @@ __global__ void __launch_bounds__(128) eval_kernel(const __grid_constant__ EvalA
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const WarpMem W = bind_mem(a.L, smem + (size_t)wib * a.L.bytes, nullptr);
+    const Grp g(32, lane);
     const int NB = W.NB;
     for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < a.n_envs; e += nw) {
         const int b0 = a.box_offset[e], n = a.box_offset[e + 1] - b0;
@@ -408,11 +467,11 @@ __global__ void __launch_bounds__(128) eval_kernel(const __grid_constant__ EvalA
         }
         __syncwarp();
         if (a.mode == 0) {
-            frames_and_aabb(W, n, lane, a.C.margin);
+            frames_and_aabb(W, n, g, a.C.margin);
             __syncwarp();
             const bool on = a.pusher_xy != nullptr;
             const float px = on ? a.pusher_xy[2 * e] : 0.f, py = on ? a.pusher_xy[2 * e + 1] : 0.f;
-            broadphase(W, n, lane, a.C.pair_cap, on, px, py, a.C);
+            broadphase(W, n, g, a.C.pair_cap, on, px, py, a.C);
             const int np = W.scal[0], npl = W.scal[1], npu = W.scal[2];
             for (int k = lane; k < np; k += 32) {
                 a.out_pairs[((size_t)e * a.C.pair_cap + k) * 2] = W.pairs[k] & 255;
@@ -426,19 +485,19 @@ __global__ void __launch_bounds__(128) eval_kernel(const __grid_constant__ EvalA
                 a.out_n_pusher[e] = npu;
             }
         } else {
-            compute_footprints(W, n, lane);
+            compute_footprints(W, n, g);
             if (a.mode == 1) {
-                const bool g = grasp_check(W, n, a.target[e], lane, a.C);
-                if (lane == 0) a.out_u8[e] = g ? 1 : 0;
+                const bool ok = grasp_check(W, n, a.target[e], g, true, a.C);
+                if (lane == 0) a.out_u8[e] = ok ? 1 : 0;
             } else if (a.mode == 2) {
                 float push[4] = {0.f, 0.f, 0.f, 0.f};
-                const int at = sample_push(W, n, lane, a.seeds[e], a.k, a.C, push);
+                const int at = sample_push(W, n, g, true, a.seeds[e], a.k, a.C, push);
                 if (lane == 0) {
                     a.out_attempt[e] = at;
                     for (int i = 0; i < 4; i++) a.out_push[4 * e + i] = at < 0 ? 0.f : push[i];
                 }
             } else {
-                const bool b = start_blocked(W, n, lane, a.starts[2 * e], a.starts[2 * e + 1], a.C.pr);
+                const bool b = start_blocked(W, n, g, a.starts[2 * e], a.starts[2 * e + 1], a.C.pr);
                 if (lane == 0) a.out_u8[e] = b ? 1 : 0;
             }
         }
@@ -545,7 +604,7 @@ struct Batch {
     int32_t* steps = nullptr;
     unsigned long long* events = nullptr;
     bool finished = false;
-    int wpb = 4, Ms = 0, Ps = 0;
+    int G = 32, wpb = 4, Ms = 0;
     cudaGraphExec_t graph = nullptr;
 };
 
@@ -568,7 +627,7 @@ struct pmbs_ctx {
     std::mutex mu;
     float4* gscratch = nullptr;
     size_t gscratch_off = 0, gscratch_bytes = 0;
-    int fixed_wpb = 0, fixed_Ps = -1, fixed_Ms = -1;
+    int fixed_wpb = 0, fixed_Ps = -1, fixed_Ms = -1, fixed_G = 0;
     SimConst C;
 };
 
@@ -628,33 +687,36 @@ bool finite(float x) { return std::isfinite(x); }
 
 void* arena_ptr(pmbs_ctx* ctx, size_t off) { return ctx->arena.base + off; }
 
-// Launch shape for environments of up to nb boxes: warps per block and shared-memory
-// contact capacities.  Heuristic default: about 18 KB of shared memory per warp.
-void choose_shape(pmbs_ctx* ctx, int nb, int& wpb, int& Ms, int& Ps) {
+// Launch shape for environments of up to nb boxes: lanes per environment G (a warp runs
+// 32 / G environments), warps per block, and the number of contact manifolds (with their
+// four point slots) kept in shared memory per environment.  Default: one environment per
+// warp (measured fastest on the uneven workload: the solve is latency-bound per warp and
+// packing stretches the largest colour over more passes), about 18 KB of shared memory
+// per environment slot.  smem_points (if set) counts
+// point slots, four per manifold; smem_manifolds takes precedence.
+void choose_shape(pmbs_ctx* ctx, int nb, int& G, int& wpb, int& Ms) {
     const pmbs_config& c = ctx->cfg;
     const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
+    G = ctx->fixed_G > 0 ? ctx->fixed_G : (c.lanes_per_env > 0 ? c.lanes_per_env : 32);
     wpb = ctx->fixed_wpb > 0 ? ctx->fixed_wpb : (c.warps_per_block > 0 ? c.warps_per_block : 4);
-    const int base = make_layout(nb, pairS, 0, 0, c.manifold_cap).bytes;
-    int target = 18 * 1024;
-    int rem = std::max(0, target - base);
-    int ms = rem / (48 + 3 * 64);
-    int ps = 3 * ms;
-    if (c.smem_points >= 0) ps = c.smem_points;
+    wpb = std::min(wpb, 4);
+    const int K = 32 / G;
+    const int base = make_layout(nb, pairS, 0, c.manifold_cap).bytes;
+    const int target = 18 * 1024;
+    int ms = std::max(0, target - base) / (16 * kConFields);
+    if (K > 1) ms = 0;  // several environments per warp: contacts in L1-cached scratch
+    if (c.smem_points >= 0) ms = c.smem_points / 4;
     if (c.smem_manifolds >= 0) ms = c.smem_manifolds;
-    if (ctx->fixed_Ps >= 0) ps = ctx->fixed_Ps;
+    if (ctx->fixed_Ps >= 0) ms = ctx->fixed_Ps / 4;
     if (ctx->fixed_Ms >= 0) ms = ctx->fixed_Ms;
-    Ps = std::min(ps, c.contact_cap);
     Ms = std::min(ms, c.manifold_cap);
     // keep one block within the 227 KB opt-in limit
-    while (wpb > 1 && (size_t)wpb * make_layout(nb, pairS, Ms, Ps, c.manifold_cap).bytes > 227 * 1024) wpb >>= 1;
-    while ((size_t)make_layout(nb, pairS, Ms, Ps, c.manifold_cap).bytes > 227 * 1024 && (Ps > 0 || Ms > 0)) {
-        Ps /= 2;
-        Ms /= 2;
-    }
+    while (Ms > 0 && (size_t)K * make_layout(nb, pairS, Ms, c.manifold_cap).bytes > 227 * 1024) Ms /= 2;
+    while (wpb > 1 && (size_t)wpb * K * make_layout(nb, pairS, Ms, c.manifold_cap).bytes > 227 * 1024) wpb >>= 1;
 }
 
 pmbs_status ensure_scratch(pmbs_ctx* ctx, size_t warps) {
-    const size_t per = (size_t)(3 * ctx->cfg.manifold_cap + 4 * ctx->cfg.contact_cap) * sizeof(float4);
+    const size_t per = (size_t)scratch_f4_per_warp(ctx->cfg.manifold_cap) * sizeof(float4);
     const size_t need = warps * per;
     if (need <= ctx->gscratch_bytes) return PMBS_OK;
     if (ctx->gscratch) ctx->arena.release(ctx->gscratch_off, ctx->gscratch_bytes);
@@ -676,7 +738,8 @@ pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, s
         c.pgs_iters < 0 || !(c.dt > 0) || c.grasp_angles < 1 || c.grasp_angles > 32 || c.sample_attempts < 1 ||
         c.sample_attempts > 32 || c.contour_points < 1 || c.contact_cap < 4 || c.manifold_cap < 1 ||
         c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096 || !(c.pusher_speed > 0) ||
-        !(c.pusher_radius > 0))
+        !(c.pusher_radius > 0) || !(c.lanes_per_env == 0 || c.lanes_per_env == 8 || c.lanes_per_env == 16 ||
+                                    c.lanes_per_env == 32))
         return PMBS_E_INVALID;
     pmbs_ctx* ctx = new pmbs_ctx();
     ctx->cfg = c;
@@ -826,7 +889,7 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
         for (int s : b.scene_ids) ctx->scenes[s].uses++;
     }
     b.finished = n_envs == 0;
-    choose_shape(ctx, nb, b.wpb, b.Ms, b.Ps);
+    choose_shape(ctx, nb, b.G, b.wpb, b.Ms);
     const int64_t id = ctx->next_batch++;
     ctx->batches[id] = b;
     *out_batch = id;
@@ -837,19 +900,22 @@ pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps) {
     const pmbs_config& c = ctx->cfg;
     const int nb = b.nb;
     const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
-    const Layout L = make_layout(nb, pairS, b.Ms, b.Ps, c.manifold_cap);
+    const Layout L = make_layout(nb, pairS, b.Ms, c.manifold_cap);
+    const int K = 32 / b.G;
     const int threads = 32 * b.wpb;
-    const size_t smem = (size_t)L.bytes * b.wpb;
+    const size_t smem = (size_t)L.bytes * b.wpb * K;
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel, threads, smem));
     if (per_sm < 1) return fail(ctx, PMBS_E_INVALID, "launch shape does not fit on an SM");
     per_sm = std::min(per_sm, kMaxWarpsPerSM / b.wpb);
-    const int blocks = std::max(1, std::min((b.n_envs + b.wpb - 1) / b.wpb, per_sm * ctx->num_sms));
-    const pmbs_status st = ensure_scratch(ctx, (size_t)blocks * b.wpb);
+    const int per_block = b.wpb * K;
+    const int blocks = std::max(1, std::min((b.n_envs + per_block - 1) / per_block, per_sm * ctx->num_sms));
+    const pmbs_status st = ensure_scratch(ctx, (size_t)blocks * per_block);
     if (st != PMBS_OK) return st;
     RolloutArgs a;
     a.C = ctx->C;
     a.L = L;
+    a.G = b.G;
     a.n_envs = b.n_envs;
     a.depth = b.depth;
     a.max_substeps = max_substeps;
@@ -869,7 +935,7 @@ pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps) {
     a.steps = b.steps;
     a.events = b.events;
     a.gscratch = ctx->gscratch;
-    a.scratch_f4_per_warp = 3 * c.manifold_cap + 4 * c.contact_cap;
+    a.scratch_f4_per_warp = scratch_f4_per_warp(c.manifold_cap);
     a.watchdog_cycles = 20LL * 1000 * 1000 * 1000;  // about 10 s of SM clock per env and launch
     a.watchdog_flag = b.counters + 4;
     CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), ctx->stream));
@@ -988,7 +1054,7 @@ pmbs_status eval_common(pmbs_ctx* ctx, int mode, int n_envs, const int32_t* box_
     if (e == cudaSuccess && starts) e = h2d(o_st2, starts, sizeof(float) * 2 * n_envs);
     EvalArgs a;
     a.C = ctx->C;
-    a.L = make_layout(nb, c.pair_cap, 0, 0, 1);
+    a.L = make_layout(nb, c.pair_cap, 0, 1);
     a.n_envs = n_envs;
     a.mode = mode;
     a.k = k;
@@ -1080,6 +1146,7 @@ void pmbs_default_config(pmbs_config* c) {
     c->contact_cap = 512;
     c->manifold_cap = 256;
     c->pair_cap = 1024;
+    c->lanes_per_env = 0;
     c->warps_per_block = 0;
     c->smem_points = -1;
     c->smem_manifolds = -1;
@@ -1441,26 +1508,30 @@ pmbs_status pmbs_eval_start_blocked(pmbs_ctx* ctx, int n_envs, const int32_t* bo
                        nullptr, nullptr, nullptr, nullptr, nullptr, out_blocked, nullptr, nullptr);
 }
 
-pmbs_status pmbs_launch_shape(pmbs_ctx* ctx, int max_boxes, int32_t* out_wpb, int32_t* out_Ps, int32_t* out_Ms,
-                              int32_t* out_smem) {
+pmbs_status pmbs_launch_shape(pmbs_ctx* ctx, int max_boxes, int32_t* out_lanes, int32_t* out_wpb, int32_t* out_Ps,
+                              int32_t* out_Ms, int32_t* out_smem) {
     if (!ctx || max_boxes < 1 || max_boxes > kMaxBoxes) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    int wpb, Ms, Ps;
-    choose_shape(ctx, max_boxes, wpb, Ms, Ps);
+    int G, wpb, Ms;
+    choose_shape(ctx, max_boxes, G, wpb, Ms);
+    if (out_lanes) *out_lanes = G;
     const int pairS = std::min(ctx->cfg.pair_cap, std::max(1, max_boxes * (max_boxes - 1) / 2));
     if (out_wpb) *out_wpb = wpb;
-    if (out_Ps) *out_Ps = Ps;
+    if (out_Ps) *out_Ps = 4 * Ms;
     if (out_Ms) *out_Ms = Ms;
-    if (out_smem) *out_smem = make_layout(max_boxes, pairS, Ms, Ps, ctx->cfg.manifold_cap).bytes * wpb;
+    if (out_smem) *out_smem = make_layout(max_boxes, pairS, Ms, ctx->cfg.manifold_cap).bytes * wpb * (32 / G);
     return PMBS_OK;
 }
 
-pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int warps_per_block, int smem_points, int smem_manifolds) {
+pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int lanes_per_env, int warps_per_block, int smem_points,
+                                  int smem_manifolds) {
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (!(warps_per_block == 0 || warps_per_block == 1 || warps_per_block == 2 || warps_per_block == 4 ||
-          warps_per_block == 8))
-        return fail(ctx, PMBS_E_INVALID, "warps_per_block must be 0, 1, 2, 4 or 8");
+    if (!(lanes_per_env == 0 || lanes_per_env == 8 || lanes_per_env == 16 || lanes_per_env == 32))
+        return fail(ctx, PMBS_E_INVALID, "lanes_per_env must be 0, 8, 16 or 32");
+    ctx->fixed_G = lanes_per_env;
+    if (!(warps_per_block == 0 || warps_per_block == 1 || warps_per_block == 2 || warps_per_block == 4))
+        return fail(ctx, PMBS_E_INVALID, "warps_per_block must be 0, 1, 2 or 4");
     ctx->fixed_wpb = warps_per_block;
     ctx->fixed_Ps = smem_points;
     ctx->fixed_Ms = smem_manifolds;
@@ -1611,7 +1682,7 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     const size_t o_env = take(sizeof(EnvIn) * ne), o_order = take(sizeof(int) * ne), o_prog = take(sizeof(EnvProg) * ne),
                  o_cnt = take(sizeof(int) * 8), o_ev = take(sizeof(unsigned long long) * kNumEvents * ne),
                  o_steps = take(sizeof(int32_t) * ne);
-    const int f4_per_warp = 3 * c.manifold_cap + 4 * c.contact_cap;
+    const int f4_per_warp = scratch_f4_per_warp(c.manifold_cap);
     const size_t warp_bytes = sizeof(float4) * (size_t)f4_per_warp;
     if (off >= kNoAllocScratchBytes || (kNoAllocScratchBytes - off) / warp_bytes < 4) return PMBS_E_INVALID;
     const int max_warps = (int)std::min<size_t>((kNoAllocScratchBytes - off) / warp_bytes, 1 << 20);
@@ -1625,15 +1696,20 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     float4* spill = (float4*)(S + off);
 
     const int nb = c.max_boxes_per_env, wpb = 4;
+    const int G = (c.lanes_per_env == 8 || c.lanes_per_env == 16 || c.lanes_per_env == 32) ? c.lanes_per_env : 32;
+    const int K = 32 / G;
     const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
-    const Layout L = make_layout(nb, pairS, 0, 0, c.manifold_cap);
-    const size_t smem = (size_t)L.bytes * wpb;
+    const Layout L = make_layout(nb, pairS, 0, c.manifold_cap);
+    const size_t smem = (size_t)L.bytes * wpb * K;
     if (smem > 227 * 1024) return PMBS_E_INVALID;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel, 32 * wpb, smem) != cudaSuccess)
         return PMBS_E_CUDA;
     if (per_sm < 1) return PMBS_E_INVALID;
-    const int blocks = std::max(1, std::min({(n_envs + wpb - 1) / wpb, per_sm * dv.num_sms, max_warps / wpb}));
+    const int per_block = wpb * K;
+    const int blocks = std::max(1, std::min({(n_envs + per_block - 1) / per_block, per_sm * dv.num_sms,
+                                             max_warps / per_block}));
+    if (max_warps < per_block) return PMBS_E_INVALID;
 
     noalloc_setup_kernel<<<1, 1024, 0, stream>>>(n_envs, nb, d_box_offset, d_records, d_target, env, order, prog,
                                                  counters, events, steps);
@@ -1641,6 +1717,7 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     RolloutArgs a;
     fill_const(c, a.C);
     a.L = L;
+    a.G = G;
     a.n_envs = n_envs;
     a.depth = depth;
     a.max_substeps = 0;

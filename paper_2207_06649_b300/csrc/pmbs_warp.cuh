@@ -42,32 +42,40 @@ struct SimConst {
 };
 
 // Per-warp shared-memory layout (sizes fixed per launch).
+//
+// Contact storage is manifold-major with one array per 16-byte field: header fields
+// H0 = (n, mu), H1 = (t1, A | B << 8 | np << 16), H2 = (t2, -) and, for each of the four
+// point slots j, F0 = (rA, 1/k_n), F1 = (rB, target normal velocity), F2 = (lambda_n,
+// lambda_t1, lambda_t2, 1/k_t1), F3 = (1/k_t2, depth, -, -).  Field k of manifold m sits
+// at base[k * stride + m], so lanes working on different manifolds touch different banks.
+// Manifolds below Ms live in shared memory (stride Ms), the rest in the warp's global
+// scratch (stride Mcap).
+constexpr int kConFields = 3 + 4 * 4;
+
 struct Layout {
     int NB;        // boxes per environment capacity
     int pairS;     // broadphase pair capacity (<= pair_cap)
-    int Ms, Ps;    // manifolds / points kept in shared memory
-    int Mcap;      // manifold capacity (lists)
+    int Ms;        // manifolds kept in shared memory
+    int Mcap;      // manifold capacity (lists, global scratch stride)
     int bytes;     // total bytes per warp
-    int o_bv, o_bw, o_bI0, o_bI1, o_x, o_q, o_h, o_ib, o_R, o_lo, o_hi, o_mask, o_plane, o_pusher,
-        o_pairs, o_mAB, o_mcol, o_order, o_cstart, o_scal, o_man, o_pts;
+    int o_bv, o_bw, o_bI0, o_bI1, o_con, o_x, o_q, o_h, o_ib, o_R, o_lo, o_hi, o_mask, o_plane, o_pusher,
+        o_pairs, o_mAB, o_mcol, o_order, o_cstart, o_scal;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Ps, int Mcap) {
+__host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Mcap) {
     Layout L;
     L.NB = NB;
     L.pairS = pairS;
     L.Ms = Ms;
-    L.Ps = Ps;
     L.Mcap = Mcap;
     int o = 0;
     L.o_bv = o; o += 16 * NB;
     L.o_bw = o; o += 16 * NB;
     L.o_bI0 = o; o += 16 * NB;
     L.o_bI1 = o; o += 16 * NB;
-    L.o_man = o; o += 48 * Ms;
-    L.o_pts = o; o += 64 * Ps;
+    L.o_con = o; o += 16 * kConFields * Ms;
     L.o_x = o; o += 12 * NB;
     L.o_q = o; o += 16 * NB;
     L.o_h = o; o += 12 * NB;
@@ -79,7 +87,7 @@ __host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Ps,
     L.o_scal = o; o += 4 * 16;
     L.o_mAB = o; o += 2 * Mcap;
     L.o_order = o; o += 2 * Mcap;
-    L.o_cstart = o; o += 2 * (2 * kMaxColours + 2);
+    L.o_cstart = o; o += 2 * (kMaxColours + 2);
     o = align_up(o, 4);
     L.o_pairs = o; o += 2 * pairS;
     L.o_mcol = o; o += Mcap;
@@ -89,6 +97,9 @@ __host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Ps,
     return L;
 }
 
+// Global scratch per warp, in float4 units.
+__host__ __device__ inline int scratch_f4_per_warp(int Mcap) { return kConFields * Mcap; }
+
 // Pointers into one warp's shared region and its global scratch.
 struct WarpMem {
     float4 *bv, *bw, *bI0, *bI1;  // v+invm, w+mu, inv inertia (00 01 02 11), (12 22 . .)
@@ -97,8 +108,8 @@ struct WarpMem {
     int* scal;
     uint16_t *mAB, *order, *cstart, *pairs;
     uint8_t *mcol, *plane, *pusher;
-    float4 *man_s, *pts_s, *man_g, *pts_g;
-    int NB, Ms, Ps, pairS;
+    float4 *con_s, *con_g;
+    int NB, Ms, Mcap, pairS;
 };
 
 __device__ __forceinline__ WarpMem bind_mem(const Layout& L, char* base, float4* gscratch) {
@@ -123,40 +134,75 @@ __device__ __forceinline__ WarpMem bind_mem(const Layout& L, char* base, float4*
     W.mcol = (uint8_t*)(base + L.o_mcol);
     W.plane = (uint8_t*)(base + L.o_plane);
     W.pusher = (uint8_t*)(base + L.o_pusher);
-    W.man_s = (float4*)(base + L.o_man);
-    W.pts_s = (float4*)(base + L.o_pts);
-    W.man_g = gscratch;
-    W.pts_g = gscratch ? gscratch + 3 * L.Mcap : nullptr;
+    W.con_s = (float4*)(base + L.o_con);
+    W.con_g = gscratch;
     W.NB = L.NB;
     W.Ms = L.Ms;
-    W.Ps = L.Ps;
+    W.Mcap = L.Mcap;
     W.pairS = L.pairS;
     return W;
 }
 
-__device__ __forceinline__ float4* man_ptr(const WarpMem& W, int m) {
-    return m < W.Ms ? W.man_s + 3 * m : W.man_g + 3 * m;
-}
-__device__ __forceinline__ float4* pt_ptr(const WarpMem& W, int p) {
-    return p < W.Ps ? W.pts_s + 4 * p : W.pts_g + 4 * p;
-}
+// Field access for manifold m: field k at ref.p[k * ref.stride].
+struct CRef {
+    float4* p;
+    int stride;
+    __device__ __forceinline__ float4& f(int k) const { return p[k * stride]; }
+    __device__ __forceinline__ float4& pt(int slot, int k) const { return p[(3 + 4 * slot + k) * stride]; }
+};
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-__device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
-    int s = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += t;
+__device__ __forceinline__ CRef cref(const WarpMem& W, int m) {
+    CRef r;
+    if (m < W.Ms) {
+        r.p = W.con_s + m;
+        r.stride = W.Ms;
+    } else {
+        r.p = W.con_g + m;
+        r.stride = W.Mcap;
     }
-    total = __shfl_sync(0xffffffffu, s, 31);
-    return s - v;
+    return r;
 }
+
+// A group of G consecutive lanes (G = 8, 16 or 32) works on one environment; a warp
+// holds 32 / G environments.  Every warp collective is issued by all 32 lanes at the same
+// point; the helpers below restrict its result to the calling lane's group.
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Grp {
+    int G;          // lanes per environment
+    int gl;         // lane index inside the group
+    int shift;      // warp lane of the group's first lane
+    unsigned bits;  // the group's lanes as a warp lane mask
+    __device__ __forceinline__ Grp(int G_, int lane) : G(G_), gl(lane & (G_ - 1)), shift(lane & ~(G_ - 1)) {
+        bits = (G_ == 32) ? kFull : (((1u << G_) - 1u) << shift);
+    }
+    // ballot restricted to the group, bit i = group lane i
+    __device__ __forceinline__ unsigned ballot(bool p) const { return (__ballot_sync(kFull, p) & bits) >> shift; }
+    __device__ __forceinline__ bool any(bool p) const { return (__ballot_sync(kFull, p) & bits) != 0u; }
+    __device__ __forceinline__ unsigned lt() const { return (1u << gl) - 1u; }
+    __device__ __forceinline__ int excl_scan(int v, int& total) const {
+        int s = v;
+        for (int o = 1; o < G; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, s, o, G);
+            if (gl >= o) s += t;
+        }
+        total = __shfl_sync(kFull, s, G - 1, G);
+        return s - v;
+    }
+    __device__ __forceinline__ int sum(int v) const {
+        for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o, G);
+        return v;
+    }
+    __device__ __forceinline__ int vmax(int v) const {
+        for (int o = G >> 1; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o, G));
+        return v;
+    }
+    __device__ __forceinline__ int bcast(int v, int src) const { return __shfl_sync(kFull, v, src, G); }
+    __device__ __forceinline__ float bcast(float v, int src) const { return __shfl_sync(kFull, v, src, G); }
+};
+
+// Warp-uniform loop bound: the largest per-group bound.
+__device__ __forceinline__ int wmax(int v) { return __reduce_max_sync(kFull, v); }
 
 __device__ __forceinline__ CBox load_cbox(const WarpMem& W, int i) {
     const int NB = W.NB;
@@ -170,7 +216,7 @@ __device__ __forceinline__ CBox load_cbox(const WarpMem& W, int i) {
     return b;
 }
 
-// Per-push pusher state (warp-uniform).
+// Per-push pusher state (uniform within a group).
 struct Pusher {
     bool active;
     float sx, sy, dx, dy;
@@ -194,10 +240,11 @@ __device__ __forceinline__ Pusher make_pusher(const SimConst& C, const float* pu
 }
 
 // ------------------------------------------------------------------ frames + broadphase
-// Per box: rotation (exact), world inverse inertia, AABB (exact).
-__device__ __forceinline__ void frames_and_aabb(const WarpMem& W, int n, int lane, float margin) {
+// Per box: rotation (exact), world inverse inertia, AABB (exact).  n = 0 for a group
+// without work in this phase (every function below accepts that).
+__device__ __forceinline__ void frames_and_aabb(const WarpMem& W, int n, const Grp& g, float margin) {
     const int NB = W.NB;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = g.gl; i < n; i += g.G) {
         float R[9];
         quat_to_R_exact(W.q[i], W.q[NB + i], W.q[2 * NB + i], W.q[3 * NB + i], R);
 #pragma unroll
@@ -223,54 +270,68 @@ __device__ __forceinline__ void frames_and_aabb(const WarpMem& W, int n, int lan
     }
 }
 
+// Pair (i, j), i < j, of lexicographic index t among n boxes.
+__device__ __forceinline__ void pair_of_index(int t, int n, int& i, int& j) {
+    const float b = (float)(2 * n - 1);
+    int r = (int)((b - sqrtf(fmaxf(b * b - 8.f * (float)t, 0.f))) * 0.5f);
+    r = max(0, min(r, n - 2));
+    auto start = [n](int a) { return a * (2 * n - a - 1) / 2; };
+    while (r > 0 && start(r) > t) r--;
+    while (r < n - 2 && start(r + 1) <= t) r++;
+    i = r;
+    j = t - start(r) + r + 1;
+}
+
 // Pair lists at the current AABBs: box-box pairs (i<j, lexicographic, capped), boxes
 // reaching below the plane, boxes meeting the pusher's AABB.  Writes counts to scal[0..2]
 // and returns true if the pair cap dropped pairs.
-__device__ __forceinline__ bool broadphase(const WarpMem& W, int n, int lane, int pair_cap, bool pusher_on,
+__device__ __forceinline__ bool broadphase(const WarpMem& W, int n, const Grp& g, int pair_cap, bool pusher_on,
                                            float Px, float Py, const SimConst& C) {
     const int NB = W.NB;
     const int cap = min(pair_cap, W.pairS);
+    const int T = n * (n - 1) / 2;
+    const int Tw = wmax(T);
     int np = 0;
     bool overflow = false;
-    for (int i = 0; i + 1 < n; i++) {
-        const float li0 = W.lo[i], li1 = W.lo[NB + i], li2 = W.lo[2 * NB + i];
-        const float hi0 = W.hi[i], hi1 = W.hi[NB + i], hi2 = W.hi[2 * NB + i];
-        for (int jb = i + 1; jb < n; jb += 32) {
-            const int j = jb + lane;
-            bool ov = false;
-            if (j < n) {
-                ov = li0 <= W.hi[j] && W.lo[j] <= hi0 && li1 <= W.hi[NB + j] && W.lo[NB + j] <= hi1 &&
-                     li2 <= W.hi[2 * NB + j] && W.lo[2 * NB + j] <= hi2;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, ov);
-            const int pos = np + __popc(m & lanemask_lt());
-            if (ov) {
-                if (pos < cap) W.pairs[pos] = (uint16_t)(i | (j << 8));
-                else overflow = true;
-            }
-            np += __popc(m);
+    for (int base = 0; base < Tw; base += g.G) {
+        const int t = base + g.gl;
+        bool ov = false;
+        int i = 0, j = 0;
+        if (t < T) {
+            pair_of_index(t, n, i, j);
+            ov = W.lo[i] <= W.hi[j] && W.lo[j] <= W.hi[i] && W.lo[NB + i] <= W.hi[NB + j] &&
+                 W.lo[NB + j] <= W.hi[NB + i] && W.lo[2 * NB + i] <= W.hi[2 * NB + j] &&
+                 W.lo[2 * NB + j] <= W.hi[2 * NB + i];
         }
+        const unsigned m = g.ballot(ov);
+        const int pos = np + __popc(m & g.lt());
+        if (ov) {
+            if (pos < cap) W.pairs[pos] = (uint16_t)(i | (j << 8));
+            else overflow = true;
+        }
+        np += __popc(m);
     }
-    overflow = __any_sync(0xffffffffu, overflow);
+    overflow = g.any(overflow);
     int npl = 0, npu = 0;
     const float rm = xa(C.pr, C.margin);
     const float plo0 = xs(Px, rm), plo1 = xs(Py, rm), plo2 = xs(C.pz0, rm);
     const float phi0 = xa(Px, rm), phi1 = xa(Py, rm), phi2 = xa(C.pz1, rm);
-    for (int b = 0; b < n; b += 32) {
-        const int i = b + lane;
+    const int nw = wmax(n);
+    for (int b = 0; b < nw; b += g.G) {
+        const int i = b + g.gl;
         const bool pl = i < n && W.lo[2 * NB + i] < 0.f;
         bool pu = false;
         if (pusher_on && i < n)
             pu = W.lo[i] <= phi0 && plo0 <= W.hi[i] && W.lo[NB + i] <= phi1 && plo1 <= W.hi[NB + i] &&
                  W.lo[2 * NB + i] <= phi2 && plo2 <= W.hi[2 * NB + i];
-        const unsigned mp = __ballot_sync(0xffffffffu, pl);
-        const unsigned mu = __ballot_sync(0xffffffffu, pu);
-        if (pl) W.plane[npl + __popc(mp & lanemask_lt())] = (uint8_t)i;
-        if (pu) W.pusher[npu + __popc(mu & lanemask_lt())] = (uint8_t)i;
+        const unsigned mp = g.ballot(pl);
+        const unsigned mu = g.ballot(pu);
+        if (pl) W.plane[npl + __popc(mp & g.lt())] = (uint8_t)i;
+        if (pu) W.pusher[npu + __popc(mu & g.lt())] = (uint8_t)i;
         npl += __popc(mp);
         npu += __popc(mu);
     }
-    if (lane == 0) {
+    if (g.gl == 0) {
         W.scal[0] = min(np, cap);
         W.scal[1] = npl;
         W.scal[2] = npu;
@@ -284,27 +345,81 @@ struct NarrowStats {
     int sat, face, edge, plane, pusher, clip_verts, bb_points;
 };
 
-// Candidates in order (box-box pairs, plane, pusher); each yields at most four points
-// sharing a normal.  Manifolds are emitted in candidate order until the manifold or
-// point capacity would be exceeded; that manifold and every later one are dropped.
-// Writes M, P to scal[3], scal[4]; returns true on overflow.
-__device__ __forceinline__ bool narrowphase(const WarpMem& W, int lane, const SimConst& C, float Px, float Py,
-                                            NarrowStats& st) {
-    const int NB = W.NB;
-    const int npairs = W.scal[0], nplane = W.scal[1], npush = W.scal[2];
-    const int ncand = npairs + nplane + npush;
-    int M = 0, P = 0;
-    bool stop = false;
+// Running emission state: manifolds M and points P emitted so far; stop once a manifold
+// did not fit (it and every later one are dropped).
+struct Emit {
+    int M, P;
+    bool stop;
+};
+
+// Emit one chunk of candidates (one per group lane) in lane order, honouring the caps.
+// kind: 0 box-box (p = world point), 1 plane (p = offset from the box centre),
+// 2 pusher (p = world point on the box).  Returns the number of points emitted by the
+// chunk's box-box candidates (for the event counters).
+__device__ __forceinline__ int emit_chunk(const WarpMem& W, const Grp& g, const SimConst& C, Emit& E,
+                                          const CManifold& cm, int A, int B, float mu, int kind, float3 cA,
+                                          float3 cB) {
+    const bool has = cm.np > 0;
+    const unsigned hm = g.ballot(has);
+    const int mpre = __popc(hm & g.lt());
+    int ptot;
+    const int ppre = g.excl_scan(cm.np, ptot);
+    const bool fits = !E.stop && (E.M + mpre + 1 <= C.Mcap) && (E.P + ppre + cm.np <= C.Pcap);
+    const unsigned viol = g.ballot(has && !fits);
+    const int first = viol ? __ffs(viol) - 1 : 32;
+    const bool ok = has && g.gl < first;
+    if (ok) {
+        const int mi = E.M + mpre;
+        const CRef r = cref(W, mi);
+        r.f(0) = make_float4(cm.n.x, cm.n.y, cm.n.z, mu);
+        r.f(1) = make_float4(0.f, 0.f, 0.f, __int_as_float(A | (B << 8) | (cm.np << 16)));
+        r.f(2) = make_float4(0.f, 0.f, 0.f, 0.f);
+        W.mAB[mi] = (uint16_t)(A | (B << 8));
+        for (int k = 0; k < cm.np; k++) {
+            float3 rA, rB;
+            if (kind == 1) {
+                rA = f3(0.f, 0.f, 0.f);
+                rB = cm.p[k];
+            } else if (kind == 2) {
+                rA = cm.p[k] - cA;
+                rB = f3(0.f, 0.f, 0.f);
+            } else {
+                rA = cm.p[k] - cA;
+                rB = cm.p[k] - cB;
+            }
+            r.pt(k, 0) = make_float4(rA.x, rA.y, rA.z, 0.f);
+            r.pt(k, 1) = make_float4(rB.x, rB.y, rB.z, 0.f);
+            r.pt(k, 3) = make_float4(0.f, cm.d[k], 0.f, 0.f);
+        }
+    }
+    const unsigned okm = g.ballot(ok);
+    int pemit;
+    g.excl_scan(ok ? cm.np : 0, pemit);
+    E.M += __popc(okm);
+    E.P += pemit;
+    if (viol) E.stop = true;
+    return g.sum((ok && kind == 0) ? cm.np : 0);
+}
+
+// Candidates in order (box-box pairs, plane, pusher), one pass per kind; each yields at
+// most four points sharing a normal.  Manifolds are emitted in candidate order until the
+// manifold or point capacity would be exceeded; that manifold and every later one are
+// dropped.  Writes M, P to scal[3], scal[4] and the box-box manifold count to scal[7],
+// plane manifolds to scal[8]; returns true on overflow.
+__device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool on, const SimConst& C, float Px,
+                                            float Py, NarrowStats& st) {
+    const int npairs = on ? W.scal[0] : 0, nplane = on ? W.scal[1] : 0, npush = on ? W.scal[2] : 0;
+    Emit E{0, 0, false};
     int sat = 0, face = 0, edge = 0, clipv = 0;
-    for (int base = 0; base < ncand && !stop; base += 32) {
-        const int c = base + lane;
+    const int pw = wmax(npairs);
+    for (int base = 0; base < pw; base += g.G) {
+        const int c = base + g.gl;
         CManifold cm;
         cm.np = 0;
         int A = 0, B = 0;
         float mu = 0.f;
-        float3 cA = f3(0.f, 0.f, 0.f), cB = f3(0.f, 0.f, 0.f);
-        int kind = 0;  // 0 box-box, 1 plane, 2 pusher
-        if (c < npairs) {
+        float3 cA = f3(0.f, 0.f, 0.f), cB = cA;
+        if (c < npairs && !E.stop) {
             const int pr = W.pairs[c];
             A = pr & 255;
             B = pr >> 8;
@@ -316,77 +431,59 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, int lane, const Si
             mu = sqrtf(W.bw[A].w * W.bw[B].w);
             cA = a.c;
             cB = b.c;
-        } else if (c < npairs + nplane) {
-            B = W.plane[c - npairs];
-            A = kPlane;
-            kind = 1;
+        }
+        st.bb_points += emit_chunk(W, g, C, E, cm, A, B, mu, 0, cA, cB);
+    }
+    const int Mbb = E.M;
+    const int lw = wmax(nplane);
+    for (int base = 0; base < lw; base += g.G) {
+        const int c = base + g.gl;
+        CManifold cm;
+        cm.np = 0;
+        int B = 0;
+        float mu = 0.f;
+        float3 cB = f3(0.f, 0.f, 0.f);
+        if (c < nplane && !E.stop) {
+            B = W.plane[c];
             const CBox b = load_cbox(W, B);
             collide_box_plane(b, C.margin, cm);
             mu = sqrtf(W.bw[B].w * C.table_mu);
             cB = b.c;
-        } else if (c < ncand) {
-            A = W.pusher[c - npairs - nplane];
-            B = kPusher;
-            kind = 2;
+        }
+        emit_chunk(W, g, C, E, cm, kPlane, B, mu, 1, f3(0.f, 0.f, 0.f), cB);
+    }
+    const int Mpl = E.M - Mbb;
+    const int uw = wmax(npush);
+    for (int base = 0; base < uw; base += g.G) {
+        const int c = base + g.gl;
+        CManifold cm;
+        cm.np = 0;
+        int A = 0;
+        float mu = 0.f;
+        float3 cA = f3(0.f, 0.f, 0.f);
+        if (c < npush && !E.stop) {
+            A = W.pusher[c];
             const CBox a = load_cbox(W, A);
             collide_capsule_box(a, Px, Py, C.pz0, C.pz1, C.pr, C.margin, cm);
             mu = sqrtf(W.bw[A].w * C.pusher_mu);
             cA = a.c;
         }
-        const bool has = cm.np > 0;
-        const unsigned hm = __ballot_sync(0xffffffffu, has);
-        const int mpre = __popc(hm & lanemask_lt());
-        int ptot;
-        const int ppre = warp_excl_scan(cm.np, lane, ptot);
-        const bool fits = (M + mpre + 1 <= C.Mcap) && (P + ppre + cm.np <= C.Pcap);
-        const unsigned viol = __ballot_sync(0xffffffffu, has && !fits);
-        const int first = viol ? __ffs(viol) - 1 : 32;
-        const bool ok = has && lane < first;
-        if (ok) {
-            const int mi = M + mpre, pi = P + ppre;
-            float4* mh = man_ptr(W, mi);
-            mh[0] = make_float4(cm.n.x, cm.n.y, cm.n.z, mu);
-            mh[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(A | (B << 8) | (cm.np << 16)));
-            mh[2] = make_float4(0.f, 0.f, 0.f, __int_as_float(pi));
-            W.mAB[mi] = (uint16_t)(A | (B << 8));
-            for (int k = 0; k < cm.np; k++) {
-                float3 rA, rB;
-                if (kind == 1) {  // plane: p holds the offset from the box centre
-                    rA = f3(0.f, 0.f, 0.f);
-                    rB = cm.p[k];
-                } else if (kind == 2) {
-                    rA = cm.p[k] - cA;
-                    rB = f3(0.f, 0.f, 0.f);
-                } else {
-                    rA = cm.p[k] - cA;
-                    rB = cm.p[k] - cB;
-                }
-                float4* pp = pt_ptr(W, pi + k);
-                pp[0] = make_float4(rA.x, rA.y, rA.z, 0.f);
-                pp[1] = make_float4(rB.x, rB.y, rB.z, 0.f);
-                pp[3] = make_float4(0.f, cm.d[k], 0.f, 0.f);
-            }
-        }
-        const unsigned okm = __ballot_sync(0xffffffffu, ok);
-        int pemit;
-        warp_excl_scan(ok ? cm.np : 0, lane, pemit);
-        M += __popc(okm);
-        P += pemit;
-        st.bb_points += __reduce_add_sync(0xffffffffu, (ok && kind == 0) ? cm.np : 0);
-        if (viol) stop = true;
+        emit_chunk(W, g, C, E, cm, A, kPusher, mu, 2, cA, f3(0.f, 0.f, 0.f));
     }
-    st.sat += __reduce_add_sync(0xffffffffu, sat);
-    st.face += __reduce_add_sync(0xffffffffu, face);
-    st.edge += __reduce_add_sync(0xffffffffu, edge);
-    st.clip_verts += __reduce_add_sync(0xffffffffu, clipv);
+    st.sat += g.sum(sat);
+    st.face += g.sum(face);
+    st.edge += g.sum(edge);
+    st.clip_verts += g.sum(clipv);
     st.plane += nplane;
     st.pusher += npush;
-    if (lane == 0) {
-        W.scal[3] = M;
-        W.scal[4] = P;
+    if (g.gl == 0 && on) {
+        W.scal[3] = E.M;
+        W.scal[4] = E.P;
+        W.scal[7] = Mbb;
+        W.scal[8] = Mpl;
     }
     __syncwarp();
-    return stop;
+    return E.stop;
 }
 
 // ------------------------------------------------------------------ contact preparation
@@ -398,15 +495,14 @@ __device__ __forceinline__ float3 sym_mul(float4 I0, float4 I1, float3 v) {
 // Tangent basis from the world axis least aligned with n; inverse effective masses along
 // n, t1, t2; target normal velocity (speculative -d/dt when separated, Baumgarte
 // beta/dt * max(-d - slop, 0) when penetrating); impulses start at zero.
-__device__ __forceinline__ void prepare(const WarpMem& W, int lane, const SimConst& C) {
-    const int M = W.scal[3];
-    for (int m = lane; m < M; m += 32) {
-        float4* mh = man_ptr(W, m);
-        const float4 h0 = mh[0], h1 = mh[1], h2 = mh[2];
+__device__ __forceinline__ void prepare(const WarpMem& W, const Grp& g, bool on, const SimConst& C) {
+    const int M = on ? W.scal[3] : 0;
+    for (int m = g.gl; m < M; m += g.G) {
+        const CRef r = cref(W, m);
+        const float4 h0 = r.f(0), h1 = r.f(1);
         const float3 n = f3(h0.x, h0.y, h0.z);
         const int ids = __float_as_int(h1.w);
         const int A = ids & 255, B = (ids >> 8) & 255, np = (ids >> 16) & 255;
-        const int p0 = __float_as_int(h2.w);
         const float an0 = fabsf(n.x), an1 = fabsf(n.y), an2 = fabsf(n.z);
         int k = 0;
         float amin = an0;
@@ -416,16 +512,15 @@ __device__ __forceinline__ void prepare(const WarpMem& W, int lane, const SimCon
         float3 t1 = cross3(n, e);
         t1 = t1 * (1.f / norm3(t1));
         const float3 t2 = cross3(n, t1);
-        mh[1] = make_float4(t1.x, t1.y, t1.z, h1.w);
-        mh[2] = make_float4(t2.x, t2.y, t2.z, h2.w);
+        r.f(1) = make_float4(t1.x, t1.y, t1.z, h1.w);
+        r.f(2) = make_float4(t2.x, t2.y, t2.z, 0.f);
         const bool dA = A < kPusher, dB = B < kPusher;
         float4 IA0 = make_float4(0.f, 0.f, 0.f, 0.f), IA1 = IA0, IB0 = IA0, IB1 = IA0;
         float imA = 0.f, imB = 0.f;
         if (dA) { IA0 = W.bI0[A]; IA1 = W.bI1[A]; imA = W.bv[A].w; }
         if (dB) { IB0 = W.bI0[B]; IB1 = W.bI1[B]; imB = W.bv[B].w; }
         for (int p = 0; p < np; p++) {
-            float4* pp = pt_ptr(W, p0 + p);
-            const float4 q0 = pp[0], q1 = pp[1], q3 = pp[3];
+            const float4 q0 = r.pt(p, 0), q1 = r.pt(p, 1), q3 = r.pt(p, 3);
             const float3 rA = f3(q0.x, q0.y, q0.z), rB = f3(q1.x, q1.y, q1.z);
             const float d = q3.y;
             float kk[3];
@@ -444,81 +539,99 @@ __device__ __forceinline__ void prepare(const WarpMem& W, int lane, const SimCon
                 kk[j] = 1.f / s;
             }
             const float bias = d > 0.f ? -d / C.dt : (C.baumgarte / C.dt) * fmaxf(-d - C.slop, 0.f);
-            pp[0] = make_float4(rA.x, rA.y, rA.z, kk[0]);
-            pp[1] = make_float4(rB.x, rB.y, rB.z, bias);
-            pp[2] = make_float4(0.f, 0.f, 0.f, kk[1]);
-            pp[3] = make_float4(kk[2], d, 0.f, 0.f);
+            r.pt(p, 0) = make_float4(rA.x, rA.y, rA.z, kk[0]);
+            r.pt(p, 1) = make_float4(rB.x, rB.y, rB.z, bias);
+            r.pt(p, 2) = make_float4(0.f, 0.f, 0.f, kk[1]);
+            r.pt(p, 3) = make_float4(kk[2], d, 0.f, 0.f);
         }
     }
     __syncwarp();
 }
 
 // ------------------------------------------------------------------ colouring
-// Greedy colouring in manifold order (smallest colour unused by earlier manifolds on a
-// shared dynamic body), then a stable bucket sort of manifold ids by colour.  Lane 0
-// walks the list; the lists are short (hundreds at most).  Returns true on colour
-// overflow (manifold dropped).  Writes the colour count to scal[5] and the number of
-// coloured manifolds to scal[6].
-__device__ __forceinline__ bool colour_manifolds(const WarpMem& W, int n, int lane) {
-    const int M = W.scal[3];
-    for (int i = lane; i < n; i += 32) W.mask[i] = 0u;
-    uint16_t* cnt = W.cstart + (kMaxColours + 2);  // per-colour counters / fill cursors
-    cnt[lane] = 0;
+// Greedy colouring in manifold order: each manifold takes the smallest colour (< 32) not
+// used by an earlier manifold on a shared dynamic body.  Box-box manifolds come first and
+// are walked in order by the group's first lane; every plane manifold is the only one of
+// its box among the plane manifolds and follows all box-box manifolds, and likewise every
+// pusher manifold follows all plane manifolds, so both groups are coloured lane-parallel
+// from the box masks with exactly the sequential result.  Then a stable bucket sort of
+// manifold ids by colour.  Returns true on colour overflow (manifold dropped).  Writes the
+// colour count to scal[5] and the number of coloured manifolds to scal[6].
+__device__ __forceinline__ bool colour_manifolds(const WarpMem& W, int n, const Grp& g, bool on) {
+    const int M = on ? W.scal[3] : 0, Mbb = on ? W.scal[7] : 0, Mpl = on ? W.scal[8] : 0;
+    for (int i = g.gl; i < n; i += g.G) W.mask[i] = 0u;
     __syncwarp();
     bool overflow = false;
-    if (lane == 0) {
-        int ncol = 0;
-        for (int m = 0; m < M; m++) {
+    int cmax = -1;
+    if (g.gl == 0) {
+        for (int m = 0; m < Mbb; m++) {
             const int ab = W.mAB[m];
             const int A = ab & 255, B = ab >> 8;
-            uint32_t u = 0u;
-            if (A < kPusher) u |= W.mask[A];
-            if (B < kPusher) u |= W.mask[B];
-            const uint32_t freeb = ~u;
-            if (freeb == 0u) {
+            const uint32_t u = W.mask[A] | W.mask[B];
+            if (u == 0xffffffffu) {
                 W.mcol[m] = 255;
                 overflow = true;
                 continue;
             }
-            const int c = __ffs(freeb) - 1;
+            const int c = __ffs(~u) - 1;
             W.mcol[m] = (uint8_t)c;
-            if (A < kPusher) W.mask[A] = W.mask[A] | (1u << c);
-            if (B < kPusher) W.mask[B] = W.mask[B] | (1u << c);
-            if (c + 1 > ncol) ncol = c + 1;
-            cnt[c] = cnt[c] + 1;
+            W.mask[A] = W.mask[A] | (1u << c);
+            W.mask[B] = W.mask[B] | (1u << c);
+            cmax = max(cmax, c);
         }
-        int acc = 0;
-        for (int c = 0; c < ncol; c++) {
-            const int k = cnt[c];
-            W.cstart[c] = (uint16_t)acc;
-            cnt[c] = (uint16_t)acc;
-            acc += k;
-        }
-        W.cstart[ncol] = (uint16_t)acc;
-        for (int m = 0; m < M; m++) {
-            const int c = W.mcol[m];
-            if (c == 255) continue;
-            const int f = cnt[c];
-            cnt[c] = (uint16_t)(f + 1);
-            W.order[f] = (uint16_t)m;
-        }
-        W.scal[5] = ncol;
-        W.scal[6] = acc;
     }
     __syncwarp();
-    return __shfl_sync(0xffffffffu, (int)overflow, 0) != 0;
+    // plane manifolds (body B is the box), then pusher manifolds (body A is the box)
+    for (int grp = 0; grp < 2; grp++) {
+        const int lo = grp == 0 ? Mbb : Mbb + Mpl, hi = grp == 0 ? Mbb + Mpl : M;
+        for (int m = lo + g.gl; m < hi; m += g.G) {
+            const int ab = W.mAB[m];
+            const int box = grp == 0 ? (ab >> 8) : (ab & 255);
+            const uint32_t u = W.mask[box];
+            if (u == 0xffffffffu) {
+                W.mcol[m] = 255;
+                overflow = true;
+                continue;
+            }
+            const int c = __ffs(~u) - 1;
+            W.mcol[m] = (uint8_t)c;
+            W.mask[box] = u | (1u << c);
+            cmax = max(cmax, c);
+        }
+        __syncwarp();
+    }
+    const int ncol = g.vmax(cmax + 1);
+    const int cw = wmax(ncol), mw = wmax(M);
+    int pos = 0;
+    for (int c = 0; c < cw; c++) {
+        if (g.gl == 0 && c < ncol) W.cstart[c] = (uint16_t)pos;
+        for (int base = 0; base < mw; base += g.G) {
+            const int m = base + g.gl;
+            const bool is = c < ncol && m < M && W.mcol[m] == c;
+            const unsigned bal = g.ballot(is);
+            if (is) W.order[pos + __popc(bal & g.lt())] = (uint16_t)m;
+            pos += __popc(bal);
+        }
+    }
+    if (g.gl == 0 && on) {
+        W.cstart[ncol] = (uint16_t)pos;
+        W.scal[5] = ncol;
+        W.scal[6] = pos;
+    }
+    __syncwarp();
+    return g.any(overflow);
 }
 
 // ------------------------------------------------------------------ PGS
-// Returns the number of points; bb_pts gets them too when both bodies are dynamic.
+// One manifold's Gauss-Seidel update: all normal rows, then all friction pairs.  Returns
+// the number of points; bb_pts gets them too when both bodies are dynamic.
 __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pusherV, int& bb_pts) {
-    const float4* mh = man_ptr(W, m);
-    const float4 h0 = mh[0], h1 = mh[1], h2 = mh[2];
+    const CRef r = cref(W, m);
+    const float4 h0 = r.f(0), h1 = r.f(1), h2 = r.f(2);
     const float3 n = f3(h0.x, h0.y, h0.z), t1 = f3(h1.x, h1.y, h1.z), t2 = f3(h2.x, h2.y, h2.z);
     const float mu = h0.w;
     const int ids = __float_as_int(h1.w);
     const int A = ids & 255, B = (ids >> 8) & 255, np = (ids >> 16) & 255;
-    const int p0 = __float_as_int(h2.w);
     const bool dA = A < kPusher, dB = B < kPusher;
     float3 vA = f3(0.f, 0.f, 0.f), wA = vA, vB = vA, wB = vA;
     float imA = 0.f, imB = 0.f, muA = 0.f, muB = 0.f;
@@ -544,9 +657,8 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
         vB = pusherV;
     }
     for (int p = 0; p < np; p++) {
-        float4* pp = pt_ptr(W, p0 + p);
-        const float4 q0 = pp[0], q1 = pp[1];
-        float4 q2 = pp[2];
+        const float4 q0 = r.pt(p, 0), q1 = r.pt(p, 1);
+        float4 q2 = r.pt(p, 2);
         const float3 rA = f3(q0.x, q0.y, q0.z), rB = f3(q1.x, q1.y, q1.z);
         const float3 vr = (vB + cross3(wB, rB)) - (vA + cross3(wA, rA));
         const float vn = dot3(n, vr);
@@ -554,7 +666,7 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
         const float l = fmaxf(q2.x + delta, 0.f);
         const float dl = l - q2.x;
         q2.x = l;
-        pp[2] = q2;
+        r.pt(p, 2) = q2;
         const float3 P = n * dl;
         vA = vA - P * imA;
         wA = wA - sym_mul(IA0, IA1, cross3(rA, P));
@@ -562,9 +674,8 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
         wB = wB + sym_mul(IB0, IB1, cross3(rB, P));
     }
     for (int p = 0; p < np; p++) {
-        float4* pp = pt_ptr(W, p0 + p);
-        const float4 q0 = pp[0], q1 = pp[1], q3 = pp[3];
-        float4 q2 = pp[2];
+        const float4 q0 = r.pt(p, 0), q1 = r.pt(p, 1), q3 = r.pt(p, 3);
+        float4 q2 = r.pt(p, 2);
         const float3 rA = f3(q0.x, q0.y, q0.z), rB = f3(q1.x, q1.y, q1.z);
         const float3 vr = (vB + cross3(wB, rB)) - (vA + cross3(wA, rA));
         const float vt1 = dot3(t1, vr), vt2 = dot3(t2, vr);
@@ -573,14 +684,14 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
         const float lim = mu * q2.x;
         const float l2 = c1 * c1 + c2 * c2;
         if (l2 > lim * lim) {
-            const float s = lim / sqrtf(l2);
-            c1 *= s;
-            c2 *= s;
+            const float sc = lim / sqrtf(l2);
+            c1 *= sc;
+            c2 *= sc;
         }
         const float d1 = c1 - q2.y, d2 = c2 - q2.z;
         q2.y = c1;
         q2.z = c2;
-        pp[2] = q2;
+        r.pt(p, 2) = q2;
         const float3 P = t1 * d1 + t2 * d2;
         vA = vA - P * imA;
         wA = wA - sym_mul(IA0, IA1, cross3(rA, P));
@@ -601,13 +712,15 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
 
 // Returns the number of point visits (normal + friction row pairs) of this lane, and
 // in bb_visits those of manifolds between two dynamic bodies.
-__device__ __forceinline__ int pgs(const WarpMem& W, int lane, int iters, float3 pusherV, int& bb_visits) {
-    const int ncol = W.scal[5];
+__device__ __forceinline__ int pgs(const WarpMem& W, const Grp& g, bool on, int iters, float3 pusherV,
+                                   int& bb_visits) {
+    const int ncol = on ? W.scal[5] : 0;
+    const int cw = wmax(ncol);
     int visits = 0;
     for (int it = 0; it < iters; it++) {
-        for (int c = 0; c < ncol; c++) {
-            const int a = W.cstart[c], b = W.cstart[c + 1];
-            for (int k = a + lane; k < b; k += 32) visits += solve_manifold(W, W.order[k], pusherV, bb_visits);
+        for (int c = 0; c < cw; c++) {
+            const int a = c < ncol ? (int)W.cstart[c] : 0, b = c < ncol ? (int)W.cstart[c + 1] : 0;
+            for (int k = a + g.gl; k < b; k += g.G) visits += solve_manifold(W, W.order[k], pusherV, bb_visits);
             __syncwarp();
         }
     }
@@ -615,9 +728,9 @@ __device__ __forceinline__ int pgs(const WarpMem& W, int lane, int iters, float3
 }
 
 // ------------------------------------------------------------------ integration
-__device__ __forceinline__ void integrate(const WarpMem& W, int n, int lane, float dt) {
+__device__ __forceinline__ void integrate(const WarpMem& W, int n, const Grp& g, float dt) {
     const int NB = W.NB;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = g.gl; i < n; i += g.G) {
         const float4 v = W.bv[i], w = W.bw[i];
         W.x[i] += v.x * dt;
         W.x[NB + i] += v.y * dt;
@@ -639,9 +752,9 @@ __device__ __forceinline__ void integrate(const WarpMem& W, int n, int lane, flo
 
 // ------------------------------------------------------------------ footprints & tests
 // Footprints of every box at the current state into the R area (8 floats per box).
-__device__ __forceinline__ void compute_footprints(const WarpMem& W, int n, int lane) {
+__device__ __forceinline__ void compute_footprints(const WarpMem& W, int n, const Grp& g) {
     const int NB = W.NB;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = g.gl; i < n; i += g.G) {
         float R[9];
         quat_to_R_exact(W.q[i], W.q[NB + i], W.q[2 * NB + i], W.q[3 * NB + i], R);
         const Foot f = footprint_exact(W.x[i], W.x[NB + i], R, W.h[i], W.h[NB + i], W.h[2 * NB + i]);
@@ -675,15 +788,18 @@ __device__ __forceinline__ Foot load_foot(const WarpMem& W, int i) {
 
 // Grasp-clearance decision on the footprints (Sec. IV-B grasp evaluation stand-in):
 // lane pairs (angle k, finger side) test the finger sweep against every other footprint.
-__device__ __forceinline__ bool grasp_check(const WarpMem& W, int n, int t, int lane, const SimConst& C) {
-    const Foot ft = load_foot(W, t);
+// on = false: the group takes no part (result false).
+__device__ __forceinline__ bool grasp_check(const WarpMem& W, int n, int t, const Grp& g, bool on,
+                                            const SimConst& C) {
+    const Foot ft = on ? load_foot(W, t) : Foot{0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 0.f};
     const float halfW = xm(C.grasp_W, 0.5f), hfw = xm(C.grasp_fw, 0.5f);
     bool any = false;
-    for (int kb = 0; kb < C.grasp_K; kb += 16) {
-        const int k = kb + (lane >> 1);
-        const float s = (lane & 1) ? -1.f : 1.f;
+    for (int sb = 0; sb < 2 * C.grasp_K; sb += g.G) {
+        const int slot = sb + g.gl;
+        const int k = slot >> 1;
+        const float s = (slot & 1) ? -1.f : 1.f;
         bool ok = false;
-        if (k < C.grasp_K) {
+        if (on && k < C.grasp_K) {
             const float ax = C.gcos[k], ay = C.gsin[k];
             const float bx = -ay, by = ax;
             const float wa = xa(xm(fabsf(xdot2(ft.ux, ft.uy, ax, ay)), ft.su), xm(fabsf(xdot2(ft.vx, ft.vy, ax, ay)), ft.sv));
@@ -702,9 +818,9 @@ __device__ __forceinline__ bool grasp_check(const WarpMem& W, int n, int t, int 
                 }
             }
         }
-        // every lane must execute the collectives (no short-circuit around them)
-        const bool partner = __shfl_xor_sync(0xffffffffu, ok, 1) != 0;
-        const bool found = __any_sync(0xffffffffu, ok && partner) != 0;
+        // every lane executes the collectives (no short-circuit around them)
+        const bool partner = __shfl_xor_sync(kFull, ok, 1, g.G) != 0;
+        const bool found = g.any(ok && partner);
         any = any || found;
     }
     return any;
@@ -712,22 +828,23 @@ __device__ __forceinline__ bool grasp_check(const WarpMem& W, int n, int t, int 
 
 // Start-pose check of a push starting at (px, py): any footprint within the pusher
 // radius (Sec. IV-B: only the start pose is collision-checked).
-__device__ __forceinline__ bool start_blocked(const WarpMem& W, int n, int lane, float px, float py, float r) {
+__device__ __forceinline__ bool start_blocked(const WarpMem& W, int n, const Grp& g, float px, float py, float r) {
     bool hit = false;
-    for (int i = lane; i < n; i += 32) hit = hit || disc_hits_foot_exact(load_foot(W, i), px, py, r);
-    return __any_sync(0xffffffffu, hit);
+    for (int i = g.gl; i < n; i += g.G) hit = hit || disc_hits_foot_exact(load_foot(W, i), px, py, r);
+    return g.any(hit);
 }
 
 // Contour sampler for push k >= 2 (Sec. IV-B): lane a evaluates attempt a; the lowest
-// unblocked attempt wins.  Returns the attempt (or -1) and the push in out[4].
-__device__ __forceinline__ int sample_push(const WarpMem& W, int n, int lane, uint64_t seed, int k,
+// unblocked attempt wins.  Returns the attempt (or -1) and the push in out[4].  on =
+// false: the group takes no part.
+__device__ __forceinline__ int sample_push(const WarpMem& W, int n, const Grp& g, bool on, uint64_t seed, int k,
                                            const SimConst& C, float* out) {
     int best = -1;
-    for (int ab = 0; ab < C.attempts && best < 0; ab += 32) {
-        const int a = ab + lane;
+    for (int ab = 0; ab < C.attempts; ab += g.G) {
+        const int a = ab + g.gl;
         float push[4] = {0.f, 0.f, 0.f, 0.f};
         bool good = false;
-        if (a < C.attempts) {
+        if (on && best < 0 && a < C.attempts) {
             int j, p;
             sampler_draws(seed, k, a, n, C.npts, j, p);
             contour_push_exact(load_foot(W, j), p, C.npts, C.pr, C.sample_clear, C.plen, push);
@@ -738,11 +855,13 @@ __device__ __forceinline__ int sample_push(const WarpMem& W, int n, int lane, ui
                     break;
                 }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, good);
-        if (m) {
-            const int src = __ffs(m) - 1;
+        const unsigned m = g.ballot(good);
+        const int src = m ? __ffs(m) - 1 : 0;
+        float moved[4];
+        for (int i = 0; i < 4; i++) moved[i] = g.bcast(push[i], src);
+        if (m && best < 0) {
             best = ab + src;
-            for (int i = 0; i < 4; i++) out[i] = __shfl_sync(0xffffffffu, push[i], src);
+            for (int i = 0; i < 4; i++) out[i] = moved[i];
         }
     }
     return best;

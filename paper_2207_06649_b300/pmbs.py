@@ -42,7 +42,8 @@ class pmbs_config(C.Structure):
                 ("grasp_angles", C.c_int), ("margin", C.c_float), ("slop", C.c_float),
                 ("baumgarte", C.c_float), ("sample_clearance", C.c_float), ("sample_attempts", C.c_int),
                 ("contour_points", C.c_int), ("contact_cap", C.c_int), ("manifold_cap", C.c_int),
-                ("pair_cap", C.c_int), ("warps_per_block", C.c_int), ("smem_points", C.c_int),
+                ("pair_cap", C.c_int), ("lanes_per_env", C.c_int), ("warps_per_block", C.c_int),
+                ("smem_points", C.c_int),
                 ("smem_manifolds", C.c_int)]
 
 
@@ -87,8 +88,8 @@ def load(build_if_missing: bool = True):
         "pmbs_eval_grasp": ([vp, i32] + [vp] * 5, i32),
         "pmbs_eval_sample": ([vp, i32, vp, vp, vp, vp, i32, vp, vp], i32),
         "pmbs_eval_start_blocked": ([vp, i32] + [vp] * 5, i32),
-        "pmbs_launch_shape": ([vp, i32, vp, vp, vp, vp], i32),
-        "pmbs_set_launch_shape": ([vp, i32, i32, i32], i32),
+        "pmbs_launch_shape": ([vp, i32, vp, vp, vp, vp, vp], i32),
+        "pmbs_set_launch_shape": ([vp, i32, i32, i32, i32], i32),
         "pmbs_fp32_peak": ([vp, P(C.c_double)], i32),
         "pmbs_rollout_noalloc": ([P(pmbs_config), vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
     }
@@ -304,14 +305,15 @@ class Engine:
 
     # ---- launch shape and probes
     def launch_shape(self, max_boxes):
-        w, ps, ms, sm = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-        self._check(self.lib.pmbs_launch_shape(self.ctx, max_boxes, C.byref(w), C.byref(ps), C.byref(ms),
-                                               C.byref(sm)), "pmbs_launch_shape")
-        return dict(warps_per_block=w.value, smem_points=ps.value, smem_manifolds=ms.value, smem_bytes=sm.value)
+        g, w, ps, ms, sm = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(self.lib.pmbs_launch_shape(self.ctx, max_boxes, C.byref(g), C.byref(w), C.byref(ps),
+                                               C.byref(ms), C.byref(sm)), "pmbs_launch_shape")
+        return dict(lanes_per_env=g.value, warps_per_block=w.value, smem_points=ps.value,
+                    smem_manifolds=ms.value, smem_bytes=sm.value)
 
-    def set_launch_shape(self, warps_per_block=0, smem_points=-1, smem_manifolds=-1):
-        self._check(self.lib.pmbs_set_launch_shape(self.ctx, warps_per_block, smem_points, smem_manifolds),
-                    "pmbs_set_launch_shape")
+    def set_launch_shape(self, lanes_per_env=0, warps_per_block=0, smem_points=-1, smem_manifolds=-1):
+        self._check(self.lib.pmbs_set_launch_shape(self.ctx, lanes_per_env, warps_per_block, smem_points,
+                                                   smem_manifolds), "pmbs_set_launch_shape")
 
     def fp32_peak(self) -> float:
         t = C.c_double()

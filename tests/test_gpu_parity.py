@@ -234,10 +234,11 @@ def test_results_identical_across_launch_shapes(eng):
     scenes, pushes, seeds = _config3_small()
     ids = eng.load(scenes)
     outs = []
-    for shape in [(0, -1, -1), (1, 0, 0), (2, 32, 8), (8, 0, 0), (4, 200, 60)]:
+    for shape in [(0, 0, -1, -1), (32, 1, 0, 0), (32, 2, 32, 8), (32, 4, 0, 0), (32, 4, 200, 60), (16, 4, -1, -1),
+                  (8, 4, -1, -1), (8, 1, 16, 4), (16, 2, 0, 0)]:
         eng.set_launch_shape(*shape)
         outs.append(eng.rollout(ids, pushes, depth=2, seeds=seeds))
-    eng.set_launch_shape(0, -1, -1)
+    eng.set_launch_shape(0, 0, -1, -1)
     eng.free_scenes(ids)
     for o in outs[1:]:
         assert np.array_equal(o["cost"], outs[0]["cost"])
