@@ -3,9 +3,9 @@
  * Carlo tree search with batched simulation, arXiv 2207.06649).
  *
  * The engine executes the paper's batch expansion and batch simulation (Sec. IV-C):
- * many environments, each loaded with a selected state (Sec. IV-C "Batch Expansion":
- * environments are loaded with the selected states, then the transition is carried
- * out in parallel), execute a first push action and then further random pushes drawn
+ * many environments, each set to one selected tree state (Sec. IV-C, batch expansion
+ * sets the simulator's environments to the chosen states and applies all transitions
+ * at once), execute a first push action and then further random pushes drawn
  * by the contour action sampler (Sec. IV-B "Speeding up Action Sampling"), with a
  * terminal test after every push (Sec. IV-C "Batch Simulation").  A scene is a set of
  * rigid boxes on a table plane with a designated target (Sec. III-A, state space); an

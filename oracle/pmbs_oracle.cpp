@@ -16,8 +16,9 @@
 // After each push: workspace bounds, grasp-clearance test standing in for the grasp
 // classifier (Sec. IV-B), cost and discounted reward gamma^(k-1) (Sec. III-A, Sec. V-A
 // gamma = 0.8).  Pushes after the first are drawn by the contour sampler of Sec. IV-B
-// ("N_a actions evenly around the contour of each object, from edge to center", start
-// pose collision-checked) with SplitMix64 (Steele, Lea, Flood 2014) as the generator.
+// (a fixed number of start points spaced evenly around each object's outline, each push
+// aimed inward at the object, only the start pose checked for collision) with SplitMix64
+// (Steele, Lea, Flood 2014) as the generator.
 //
 // Precision: the trajectory runs in double.  The pair-list, grasp and sampler
 // predicates are also instantiated in IEEE binary32 (templates below, each operation
@@ -246,10 +247,10 @@ uint64_t splitmix64_next(uint64_t& s) {
 // Unbiased multiply-shift draw of an index in [0, count) from the top 32 bits.
 int draw_index(uint64_t r, int count) { return (int)(((r >> 32) * (uint64_t)count) >> 32); }
 
-// Contour push sampler (Sec. IV-B, Fig. "Sampled push actions"): for attempt a of push
+// Contour push sampler (Sec. IV-B and its figure of sampled pushes): for attempt a of push
 // k the keyed SplitMix64 stream picks object j and contour point p of N_a points spaced
 // evenly by arc length around j's footprint grown by (pusher radius + clearance); the
-// push runs from p toward j's centre ("from edge to center") for length L.  Returns the
+// push runs from p inward to j's centre for length L.  Returns the
 // accepted attempt, or -1 for a no-op push when every attempt's start is blocked.
 template <typename T>
 int sample_push(int n, const T* x, const T* q, const T* h, uint64_t seed, int k, T r, T clear,

@@ -1,11 +1,11 @@
 // Batched push-rollout engine for PMBS on one B300 (sm_103a): kernels and the C ABI.
 //
-// One warp runs one environment (a scene copy, Sec. IV-C: "the number of parallel
-// environments in the simulator is fixed to some number N_e"); a persistent grid pulls
-// environments from a device work queue ordered by box count, largest first, so that
-// scenes of uneven size share one launch and a warp that finishes an environment early
-// (target graspable, Sec. IV-C: early-terminated environments are re-purposed) takes the
-// next one.  See pmbs.h for the contract of every entry point.
+// A warp runs one environment (a scene copy; Sec. IV-C keeps a fixed pool of N_e parallel
+// environments); a persistent grid pulls environments from a device work queue ordered by
+// box count, largest first, so that scenes of uneven size share one launch and a warp
+// whose environment ends early (target graspable; Sec. IV-C reuses such environments for
+// further simulations) takes the next one.  See pmbs.h for the contract of every entry
+// point.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -186,7 +186,7 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
 
 // The environment slots of one warp: each group pulls environments from the work queue
 // (largest first) and runs them push by push; a group whose environment finishes early
-// (target graspable, Sec. IV-C: early-terminated environments are re-purposed) takes the
+// (target graspable; Sec. IV-C hands such environments other work) takes the
 // next one while the other groups continue.  Push set-up and end-of-push phases run when
 // any group needs them; groups without work take part in the collectives only.
 __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W, const Grp& g) {
