@@ -164,6 +164,23 @@ pmbs_status pmbs_rollout_pushes_device(pmbs_ctx* ctx, int n_envs, const int32_t*
  * max_substeps <= 0 it returns PMBS_OK immediately after enqueueing. */
 pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps);
 
+/* Run the batch to completion as a CUDA graph of launches that each advance every
+ * unfinished environment by substeps_per_launch substeps (the substep loop captured in a
+ * graph; e.g. 240 = one launch per push).  The graph is captured on the first call for a
+ * given substeps_per_launch and replayed afterwards; results are bit-identical to
+ * pmbs_step.  Enqueues and returns PMBS_OK. */
+pmbs_status pmbs_step_graph(pmbs_ctx* ctx, int64_t batch, int substeps_per_launch);
+
+/* Autotuner of the launch shape (batching knobs only, never the arithmetic): builds the
+ * given batch once per candidate shape (lanes per environment 32/16/8, warps per block
+ * 4/2, shared-memory contact capacity default/none), times its first `substeps` substeps
+ * with CUDA events, and records the fastest shape for the batch's box-count bucket; later
+ * batches in that bucket use it unless a shape is fixed.  Outputs may be NULL.  Blocks
+ * until the timings finish. */
+pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push,
+                          int depth, const uint64_t* seeds, int substeps, int32_t* out_lanes_per_env,
+                          int32_t* out_warps_per_block, int32_t* out_smem_manifolds, float* out_ms);
+
 /* Results of a finished batch, copied to host arrays of n_envs entries: cost (pushes
  * until graspable, depth+1 if never), reward (gamma^(cost-1) or 0), flags (PMBS_FLAG_*).
  * out_child_states (NULL to skip): [sum of boxes][13] state after push 1, the new tree
@@ -245,6 +262,35 @@ pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int lanes_per_env, int warps_pe
  * denominator for the contact solve). */
 pmbs_status pmbs_fp32_peak(pmbs_ctx* ctx, double* out_tflops);
 
+
+/* Serving loop (continuous batching of rollout requests from many concurrent planners;
+ * the paper's planners submit one batch per MCTS iteration, Alg. 1, here many planners
+ * share one GPU).  pmbs_server_create starts a dispatcher thread on the context with
+ * n_streams non-blocking CUDA streams and at most max_inflight batches on the device.
+ * Requests are admitted in arrival order whenever the context's arena can hold their
+ * batch (memory-based admission: the arena size is the budget); admitted batches run
+ * concurrently, each on its own stream with its own scratch.  A request's results are
+ * bit-identical to the same request run alone.  The context must not be destroyed
+ * before the server.  pmbs_server_destroy waits for batches on the device. */
+typedef struct pmbs_server pmbs_server;
+pmbs_status pmbs_server_create(pmbs_ctx* ctx, int n_streams, int max_inflight, pmbs_server** out);
+/* Thread-safe: copies the request (same arguments as pmbs_rollout_pushes) and returns a
+ * ticket at once. */
+pmbs_status pmbs_server_submit(pmbs_server* server, int n_envs, const int32_t* scene_ids,
+                               const float* first_push, int depth, const uint64_t* seeds,
+                               int64_t* out_ticket);
+/* Thread-safe: wait up to timeout_ms (< 0: forever; 0: poll) for a ticket; on success the
+ * results (n_envs entries each; any pointer may be NULL) and the latency from submission
+ * to completion are written and the ticket is released.  PMBS_E_NOT_READY (poll) or
+ * PMBS_E_TIMEOUT while the request is still pending; the request's own error otherwise. */
+pmbs_status pmbs_server_wait(pmbs_server* server, int64_t ticket, int timeout_ms, int32_t* out_cost,
+                             float* out_reward, uint8_t* out_flags, int32_t* out_steps,
+                             double* out_latency_ms);
+/* out[8]: completed requests, simulated env-steps, seconds from the first submission to
+ * the last completion, p50 and p99 latency (ms), mean latency (ms), peak arena bytes in
+ * use, requests pending or on the device. */
+pmbs_status pmbs_server_stats(pmbs_server* server, double* out);
+void pmbs_server_destroy(pmbs_server* server);
 
 /* Allocation-free rollout.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory.  Two kinds of caller need it: a planning

@@ -13,8 +13,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -605,7 +610,11 @@ struct Batch {
     unsigned long long* events = nullptr;
     bool finished = false;
     int G = 32, wpb = 4, Ms = 0;
+    cudaStream_t stream = nullptr;  // stream of this batch's launches (the context's by default)
+    bool own_scratch = false;       // contact spill scratch of its own (batches that may overlap)
+    size_t scr_off = 0, scr_bytes = 0;
     cudaGraphExec_t graph = nullptr;
+    int graph_k = 0;
 };
 
 }  // namespace
@@ -628,6 +637,7 @@ struct pmbs_ctx {
     float4* gscratch = nullptr;
     size_t gscratch_off = 0, gscratch_bytes = 0;
     int fixed_wpb = 0, fixed_Ps = -1, fixed_Ms = -1, fixed_G = 0;
+    std::map<int, std::array<int, 3>> tuned;  // box-count bucket -> {G, wpb, Ms} from pmbs_autotune
     SimConst C;
 };
 
@@ -694,8 +704,23 @@ void* arena_ptr(pmbs_ctx* ctx, size_t off) { return ctx->arena.base + off; }
 // packing stretches the largest colour over more passes), about 18 KB of shared memory
 // per environment slot.  smem_points (if set) counts
 // point slots, four per manifold; smem_manifolds takes precedence.
+int shape_bucket(int nb) { return nb <= 8 ? 8 : nb <= 16 ? 16 : nb <= 24 ? 24 : nb <= 32 ? 32 : nb <= 40 ? 40 : 64; }
+
 void choose_shape(pmbs_ctx* ctx, int nb, int& G, int& wpb, int& Ms) {
     const pmbs_config& c = ctx->cfg;
+    const auto tuned = ctx->tuned.find(shape_bucket(nb));
+    if (tuned != ctx->tuned.end() && ctx->fixed_G == 0 && ctx->fixed_wpb == 0 && ctx->fixed_Ms < 0 &&
+        ctx->fixed_Ps < 0 && c.lanes_per_env == 0 && c.warps_per_block == 0 && c.smem_points < 0 &&
+        c.smem_manifolds < 0) {
+        const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
+        G = tuned->second[0];
+        wpb = tuned->second[1];
+        Ms = tuned->second[2];
+        const int K = 32 / G;
+        while (Ms > 0 && (size_t)K * make_layout(nb, pairS, Ms, c.manifold_cap).bytes > 227 * 1024) Ms /= 2;
+        while (wpb > 1 && (size_t)wpb * K * make_layout(nb, pairS, Ms, c.manifold_cap).bytes > 227 * 1024) wpb >>= 1;
+        return;
+    }
     const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
     G = ctx->fixed_G > 0 ? ctx->fixed_G : (c.lanes_per_env > 0 ? c.lanes_per_env : 32);
     wpb = ctx->fixed_wpb > 0 ? ctx->fixed_wpb : (c.warps_per_block > 0 ? c.warps_per_block : 4);
@@ -791,6 +816,8 @@ pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, s
 void release_batch_mem(pmbs_ctx* ctx, Batch& b) {
     if (b.graph) cudaGraphExecDestroy(b.graph);
     b.graph = nullptr;
+    if (b.scr_bytes) ctx->arena.release(b.scr_off, b.scr_bytes);
+    b.scr_bytes = 0;
     if (b.bytes) ctx->arena.release(b.off, b.bytes);
     b.bytes = 0;
     for (int s : b.scene_ids)
@@ -889,6 +916,7 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
         for (int s : b.scene_ids) ctx->scenes[s].uses++;
     }
     b.finished = n_envs == 0;
+    b.stream = ctx->stream;
     choose_shape(ctx, nb, b.G, b.wpb, b.Ms);
     const int64_t id = ctx->next_batch++;
     ctx->batches[id] = b;
@@ -896,7 +924,7 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
     return PMBS_OK;
 }
 
-pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps) {
+pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaStream_t stream) {
     const pmbs_config& c = ctx->cfg;
     const int nb = b.nb;
     const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
@@ -910,8 +938,24 @@ pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps) {
     per_sm = std::min(per_sm, kMaxWarpsPerSM / b.wpb);
     const int per_block = b.wpb * K;
     const int blocks = std::max(1, std::min((b.n_envs + per_block - 1) / per_block, per_sm * ctx->num_sms));
-    const pmbs_status st = ensure_scratch(ctx, (size_t)blocks * per_block);
-    if (st != PMBS_OK) return st;
+    const size_t slot_bytes = (size_t)scratch_f4_per_warp(c.manifold_cap) * sizeof(float4);
+    float4* scratch = nullptr;
+    if (b.own_scratch) {
+        const size_t need = (size_t)blocks * per_block * slot_bytes;
+        if (need > b.scr_bytes) {
+            if (b.scr_bytes) ctx->arena.release(b.scr_off, b.scr_bytes);
+            b.scr_bytes = 0;
+            const size_t off = ctx->arena.alloc(need);
+            if (off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "batch scratch does not fit in the arena");
+            b.scr_off = off;
+            b.scr_bytes = need;
+        }
+        scratch = (float4*)arena_ptr(ctx, b.scr_off);
+    } else {
+        const pmbs_status st = ensure_scratch(ctx, (size_t)blocks * per_block);
+        if (st != PMBS_OK) return st;
+        scratch = ctx->gscratch;
+    }
     RolloutArgs a;
     a.C = ctx->C;
     a.L = L;
@@ -934,12 +978,12 @@ pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps) {
     a.flags = b.flags;
     a.steps = b.steps;
     a.events = b.events;
-    a.gscratch = ctx->gscratch;
+    a.gscratch = scratch;
     a.scratch_f4_per_warp = scratch_f4_per_warp(c.manifold_cap);
     a.watchdog_cycles = 20LL * 1000 * 1000 * 1000;  // about 10 s of SM clock per env and launch
     a.watchdog_flag = b.counters + 4;
-    CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), ctx->stream));
-    rollout_kernel<<<blocks, threads, smem, ctx->stream>>>(a);
+    CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), stream));
+    rollout_kernel<<<blocks, threads, smem, stream>>>(a);
     CU(cudaGetLastError());
     return PMBS_OK;
 }
@@ -1292,15 +1336,15 @@ pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps) {
     if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
     if (b->finished) return PMBS_OK;
     CU(cudaSetDevice(ctx->device));
-    const pmbs_status st = launch_rollout(ctx, *b, max_substeps);
+    const pmbs_status st = launch_rollout(ctx, *b, max_substeps, b->stream);
     if (st != PMBS_OK) return st;
     if (max_substeps <= 0) {
         b->finished = true;
         return PMBS_OK;
     }
     int cnt[5] = {0, 0, 0, 0, 0};
-    CU(cudaMemcpyAsync(cnt, b->counters, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(cnt, b->counters, sizeof(cnt), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
     if (cnt[4]) return fail(ctx, PMBS_E_TIMEOUT, "an environment exceeded the per-launch time limit");
     const int done = cnt[3];
     if (done >= b->n_envs) {
@@ -1308,6 +1352,107 @@ pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps) {
         return PMBS_OK;
     }
     return PMBS_E_NOT_READY;
+}
+
+pmbs_status pmbs_step_graph(pmbs_ctx* ctx, int64_t batch, int substeps_per_launch) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    if (substeps_per_launch < 1) return fail(ctx, PMBS_E_INVALID, "substeps_per_launch must be >= 1");
+    if (b->finished) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    if (!b->graph || b->graph_k != substeps_per_launch) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        // capture on a private stream (the legacy default stream cannot be captured)
+        cudaStream_t cs;
+        CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const long total = (long)b->depth * ctx->cfg.substeps_per_push;
+        const long launches = (total + substeps_per_launch - 1) / substeps_per_launch;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        pmbs_status st = PMBS_OK;
+        for (long i = 0; i < launches && e == cudaSuccess && st == PMBS_OK; i++)
+            st = launch_rollout(ctx, *b, substeps_per_launch, cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && st == PMBS_OK) e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (st != PMBS_OK) return st;
+        if (e != cudaSuccess) return fail(ctx, PMBS_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        b->graph_k = substeps_per_launch;
+    }
+    CU(cudaGraphLaunch(b->graph, b->stream));
+    b->finished = true;
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push, int depth,
+                          const uint64_t* seeds, int substeps, int32_t* out_lanes_per_env, int32_t* out_warps_per_block,
+                          int32_t* out_smem_manifolds, float* out_ms) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n_envs < 1 || substeps < 1) return fail(ctx, PMBS_E_INVALID, "need environments and substeps to time");
+    CU(cudaSetDevice(ctx->device));
+    int nb = 1;
+    for (int e = 0; e < n_envs; e++) {
+        const int sid = scene_ids[e];
+        if (sid < 0 || sid >= (int)ctx->scenes.size() || !ctx->scenes[sid].live)
+            return fail(ctx, PMBS_E_INVALID, "unknown scene id");
+        nb = std::max(nb, ctx->scenes[sid].n);
+    }
+    const int saved[4] = {ctx->fixed_G, ctx->fixed_wpb, ctx->fixed_Ps, ctx->fixed_Ms};
+    ctx->tuned.erase(shape_bucket(nb));
+    const int Gs[3] = {32, 16, 8}, Ws[2] = {4, 2}, Mss[2] = {-1, 0};
+    float best_ms = 1e30f;
+    std::array<int, 3> best = {32, 4, -1};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    pmbs_status result = PMBS_OK;
+    for (int gi = 0; gi < 3 && result == PMBS_OK; gi++)
+        for (int wi = 0; wi < 2 && result == PMBS_OK; wi++)
+            for (int mi = 0; mi < 2 && result == PMBS_OK; mi++) {
+                ctx->fixed_G = Gs[gi];
+                ctx->fixed_wpb = Ws[wi];
+                ctx->fixed_Ps = -1;
+                ctx->fixed_Ms = Mss[mi];
+                int64_t id = 0;
+                result = rollout_common(ctx, n_envs, scene_ids, first_push, depth, seeds, false, &id);
+                if (result != PMBS_OK) break;
+                Batch& b = ctx->batches[id];
+                float ms = 0.f;
+                cudaError_t e = cudaEventRecord(e0, b.stream);
+                if (e == cudaSuccess) result = launch_rollout(ctx, b, substeps, b.stream);
+                if (e == cudaSuccess && result == PMBS_OK) e = cudaEventRecord(e1, b.stream);
+                if (e == cudaSuccess && result == PMBS_OK) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess && result == PMBS_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+                const int used_Ms = b.Ms;
+                release_batch_mem(ctx, b);
+                ctx->batches.erase(id);
+                if (e != cudaSuccess) result = fail(ctx, PMBS_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                if (result == PMBS_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = {Gs[gi], Ws[wi], used_Ms};
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->fixed_G = saved[0];
+    ctx->fixed_wpb = saved[1];
+    ctx->fixed_Ps = saved[2];
+    ctx->fixed_Ms = saved[3];
+    if (result != PMBS_OK) return result;
+    ctx->tuned[shape_bucket(nb)] = best;
+    if (out_lanes_per_env) *out_lanes_per_env = best[0];
+    if (out_warps_per_block) *out_warps_per_block = best[1];
+    if (out_smem_manifolds) *out_smem_manifolds = best[2];
+    if (out_ms) *out_ms = best_ms;
+    return PMBS_OK;
 }
 
 pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, float* out_reward, uint8_t* out_flags,
@@ -1563,6 +1708,303 @@ pmbs_status pmbs_fp32_peak(pmbs_ctx* ctx, double* out_tflops) {
     const double flops = (double)blocks * threads * iters * 16.0 * 8.0 * 2.0;
     *out_tflops = flops / (ms * 1e-3) / 1e12;
     return PMBS_OK;
+}
+
+}  // extern "C"
+
+
+// ====================================================================== serving loop
+// Continuous batching of rollout requests from many concurrent planners: submit() copies
+// a request and returns a ticket; a dispatcher thread admits pending requests in arrival
+// order whenever the device arena can hold them (memory-based admission), launches each
+// on one of several non-blocking streams with its own contact scratch so that admitted
+// batches overlap on the device, and retires them as their completion events fire.  A
+// request's result does not depend on what else is running: every environment's
+// arithmetic is independent of scheduling.
+namespace {
+
+struct Request {
+    int64_t ticket = 0;
+    int n_envs = 0, depth = 1;
+    std::vector<int32_t> scene_ids;
+    std::vector<float> first_push;
+    std::vector<uint64_t> seeds;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    int64_t batch = 0;
+    int stream = -1;
+    cudaEvent_t done_ev = nullptr;
+    bool finished = false;
+    pmbs_status status = PMBS_OK;
+    std::vector<int32_t> cost, steps;
+    std::vector<float> reward;
+    std::vector<uint8_t> flags;
+};
+
+}  // namespace
+
+struct pmbs_server {
+    pmbs_ctx* ctx = nullptr;
+    std::vector<cudaStream_t> streams;
+    int max_inflight = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<int64_t> pending;
+    std::vector<int64_t> inflight;
+    std::map<int64_t, Request> reqs;
+    int64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    int next_stream = 0;
+    // statistics
+    std::vector<double> latencies_ms;
+    double env_steps = 0.0;
+    int64_t completed = 0;
+    size_t peak_used = 0;
+    std::chrono::steady_clock::time_point t_first, t_last;
+    bool any = false;
+};
+
+namespace {
+
+// Admit one pending request: create its batch (host ids: copies and set-up finish before
+// return), give it its own stream and scratch, launch it.  Returns PMBS_E_OOM when the
+// arena cannot hold it now.
+pmbs_status server_admit(pmbs_server* sv, Request& r) {
+    pmbs_ctx* ctx = sv->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int64_t id = 0;
+    pmbs_status st = rollout_common(ctx, r.n_envs, r.scene_ids.data(), r.first_push.data(), r.depth,
+                                    r.seeds.data(), false, &id);
+    if (st != PMBS_OK) return st;
+    Batch& b = ctx->batches[id];
+    r.stream = sv->next_stream;
+    sv->next_stream = (sv->next_stream + 1) % (int)sv->streams.size();
+    b.stream = sv->streams[r.stream];
+    b.own_scratch = true;
+    if (b.n_envs > 0) {
+        st = launch_rollout(ctx, b, 0, b.stream);
+        if (st != PMBS_OK) {
+            release_batch_mem(ctx, b);
+            ctx->batches.erase(id);
+            return st;
+        }
+    }
+    b.finished = true;
+    r.batch = id;
+    if (cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(r.done_ev, b.stream) != cudaSuccess) {
+        // leave the batch to be retired by a synchronous wait
+        r.done_ev = nullptr;
+    }
+    sv->peak_used = std::max(sv->peak_used, ctx->arena.used);
+    return PMBS_OK;
+}
+
+// Copy a finished request's results back and free its batch.
+void server_retire(pmbs_server* sv, Request& r) {
+    pmbs_ctx* ctx = sv->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Batch* b = find_batch(ctx, r.batch);
+    const int n = r.n_envs;
+    r.cost.assign(n, 0);
+    r.reward.assign(n, 0.f);
+    r.flags.assign(n, 0);
+    r.steps.assign(n, 0);
+    cudaError_t e = cudaSuccess;
+    int wd = 0;
+    if (b && n > 0) {
+        e = cudaMemcpyAsync(r.cost.data(), b->cost, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r.reward.data(), b->reward, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r.flags.data(), b->flags, n, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r.steps.data(), b->steps, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&wd, b->counters + 4, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    if (b) {
+        release_batch_mem(ctx, *b);
+        ctx->batches.erase(r.batch);
+    }
+    if (r.done_ev) cudaEventDestroy(r.done_ev);
+    r.done_ev = nullptr;
+    r.status = e != cudaSuccess ? PMBS_E_CUDA : (wd ? PMBS_E_TIMEOUT : PMBS_OK);
+    r.t_done = std::chrono::steady_clock::now();
+    // r.finished is set by the caller under the server lock
+}
+
+void server_loop(pmbs_server* sv) {
+    cudaSetDevice(sv->ctx->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (!sv->stop) {
+        bool progressed = false;
+        // admit in arrival order while memory and the in-flight limit allow
+        while (!sv->pending.empty() && (int)sv->inflight.size() < sv->max_inflight) {
+            Request& r = sv->reqs[sv->pending.front()];
+            lk.unlock();
+            const pmbs_status st = server_admit(sv, r);
+            lk.lock();
+            if (st == PMBS_E_OOM && !sv->inflight.empty()) break;  // wait for memory to free up
+            sv->pending.pop_front();
+            progressed = true;
+            if (st != PMBS_OK) {
+                r.status = st;
+                r.finished = true;
+                r.t_done = std::chrono::steady_clock::now();
+                sv->cv_done.notify_all();
+                continue;
+            }
+            sv->inflight.push_back(r.ticket);
+        }
+        // retire finished batches
+        for (size_t i = 0; i < sv->inflight.size();) {
+            Request& r = sv->reqs[sv->inflight[i]];
+            const bool ready = !r.done_ev || cudaEventQuery(r.done_ev) != cudaErrorNotReady;
+            if (!ready) {
+                i++;
+                continue;
+            }
+            lk.unlock();
+            server_retire(sv, r);
+            lk.lock();
+            const double ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+            sv->latencies_ms.push_back(ms);
+            for (int32_t s : r.steps) sv->env_steps += s;
+            sv->completed++;
+            sv->t_last = r.t_done;
+            r.finished = true;
+            sv->inflight.erase(sv->inflight.begin() + (long)i);
+            progressed = true;
+            sv->cv_done.notify_all();
+        }
+        if (!progressed) {
+            if (sv->inflight.empty() && sv->pending.empty())
+                sv->cv_work.wait(lk, [sv] { return sv->stop || !sv->pending.empty(); });
+            else
+                sv->cv_work.wait_for(lk, std::chrono::microseconds(50));
+        }
+    }
+}
+
+double percentile(std::vector<double> v, double p) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = p * (double)(v.size() - 1);
+    const size_t i = (size_t)pos;
+    const double f = pos - (double)i;
+    return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+pmbs_status pmbs_server_create(pmbs_ctx* ctx, int n_streams, int max_inflight, pmbs_server** out) {
+    if (!ctx || !out || n_streams < 1 || n_streams > 64 || max_inflight < 1) return PMBS_E_INVALID;
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PMBS_E_CUDA;
+    pmbs_server* sv = new pmbs_server();
+    sv->ctx = ctx;
+    sv->max_inflight = max_inflight;
+    for (int i = 0; i < n_streams; i++) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
+            delete sv;
+            return PMBS_E_CUDA;
+        }
+        sv->streams.push_back(st);
+    }
+    sv->worker = std::thread(server_loop, sv);
+    *out = sv;
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_server_submit(pmbs_server* sv, int n_envs, const int32_t* scene_ids, const float* first_push, int depth,
+                               const uint64_t* seeds, int64_t* out_ticket) {
+    if (!sv || !out_ticket || n_envs < 0 || depth < 1 || depth > 64) return PMBS_E_INVALID;
+    if (n_envs > 0 && (!scene_ids || !first_push || (!seeds && depth > 1))) return PMBS_E_INVALID;
+    Request r;
+    r.n_envs = n_envs;
+    r.depth = depth;
+    r.scene_ids.assign(scene_ids, scene_ids + n_envs);
+    r.first_push.assign(first_push, first_push + 4 * (size_t)n_envs);
+    r.seeds.assign((size_t)n_envs, 0ull);
+    if (seeds) r.seeds.assign(seeds, seeds + n_envs);
+    r.t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r.ticket = sv->next_ticket++;
+        if (!sv->any) {
+            sv->any = true;
+            sv->t_first = r.t_submit;
+        }
+        *out_ticket = r.ticket;
+        sv->pending.push_back(r.ticket);
+        sv->reqs[r.ticket] = std::move(r);
+    }
+    sv->cv_work.notify_one();
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_server_wait(pmbs_server* sv, int64_t ticket, int timeout_ms, int32_t* out_cost, float* out_reward,
+                             uint8_t* out_flags, int32_t* out_steps, double* out_latency_ms) {
+    if (!sv) return PMBS_E_INVALID;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return PMBS_E_INVALID;
+    const auto pred = [&] { return it->second.finished; };
+    if (timeout_ms < 0) sv->cv_done.wait(lk, pred);
+    else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+        return timeout_ms == 0 ? PMBS_E_NOT_READY : PMBS_E_TIMEOUT;
+    Request& r = it->second;
+    const pmbs_status st = r.status;
+    const int n = r.n_envs;
+    if (st == PMBS_OK) {
+        if (out_cost) std::memcpy(out_cost, r.cost.data(), sizeof(int32_t) * n);
+        if (out_reward) std::memcpy(out_reward, r.reward.data(), sizeof(float) * n);
+        if (out_flags) std::memcpy(out_flags, r.flags.data(), n);
+        if (out_steps) std::memcpy(out_steps, r.steps.data(), sizeof(int32_t) * n);
+    }
+    if (out_latency_ms) *out_latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+    sv->reqs.erase(it);
+    return st;
+}
+
+pmbs_status pmbs_server_stats(pmbs_server* sv, double* out) {
+    if (!sv || !out) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const double span = sv->completed ? std::chrono::duration<double>(sv->t_last - sv->t_first).count() : 0.0;
+    out[0] = (double)sv->completed;
+    out[1] = sv->env_steps;
+    out[2] = span;
+    out[3] = percentile(sv->latencies_ms, 0.50);
+    out[4] = percentile(sv->latencies_ms, 0.99);
+    double mean = 0.0;
+    for (double x : sv->latencies_ms) mean += x;
+    out[5] = sv->latencies_ms.empty() ? 0.0 : mean / (double)sv->latencies_ms.size();
+    out[6] = (double)sv->peak_used;
+    out[7] = (double)(sv->pending.size() + sv->inflight.size());
+    return PMBS_OK;
+}
+
+void pmbs_server_destroy(pmbs_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->ctx->device);
+    for (auto& kv : sv->reqs) {
+        Request& r = kv.second;
+        if (r.batch && !r.finished) {
+            if (r.stream >= 0) cudaStreamSynchronize(sv->streams[r.stream]);
+            server_retire(sv, r);
+            r.finished = true;
+        }
+    }
+    for (cudaStream_t st : sv->streams) cudaStreamDestroy(st);
+    delete sv;
 }
 
 }  // extern "C"

@@ -28,7 +28,9 @@ EXPORTED = ["pmbs_default_config", "pmbs_create", "pmbs_create_with_arena", "pmb
             "pmbs_rollout_pushes_device", "pmbs_step", "pmbs_query_cost", "pmbs_query_cost_device",
             "pmbs_query_states", "pmbs_query_events", "pmbs_batch_info", "pmbs_release_batch",
             "pmbs_eval_pairs", "pmbs_eval_grasp", "pmbs_eval_sample", "pmbs_eval_start_blocked",
-            "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_rollout_noalloc"]
+            "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_rollout_noalloc",
+            "pmbs_step_graph", "pmbs_autotune", "pmbs_server_create", "pmbs_server_submit",
+            "pmbs_server_wait", "pmbs_server_stats", "pmbs_server_destroy"]
 
 
 class pmbs_config(C.Structure):
@@ -78,6 +80,8 @@ def load(build_if_missing: bool = True):
         "pmbs_rollout_pushes": ([vp, i32, vp, vp, i32, vp, vp], i32),
         "pmbs_rollout_pushes_device": ([vp, i32, vp, vp, i32, vp, vp], i32),
         "pmbs_step": ([vp, i64, i32], i32),
+        "pmbs_step_graph": ([vp, i64, i32], i32),
+        "pmbs_autotune": ([vp, i32, vp, vp, i32, vp, i32, vp, vp, vp, vp], i32),
         "pmbs_query_cost": ([vp, i64, vp, vp, vp, vp, vp], i32),
         "pmbs_query_cost_device": ([vp, i64, vp, vp, vp], i32),
         "pmbs_query_states": ([vp, i64, vp, vp], i32),
@@ -92,6 +96,11 @@ def load(build_if_missing: bool = True):
         "pmbs_set_launch_shape": ([vp, i32, i32, i32, i32], i32),
         "pmbs_fp32_peak": ([vp, P(C.c_double)], i32),
         "pmbs_rollout_noalloc": ([P(pmbs_config), vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
+        "pmbs_server_create": ([vp, i32, i32, P(vp)], i32),
+        "pmbs_server_submit": ([vp, i32, vp, vp, i32, vp, P(C.c_int64)], i32),
+        "pmbs_server_wait": ([vp, C.c_int64, i32, vp, vp, vp, vp, P(C.c_double)], i32),
+        "pmbs_server_stats": ([vp, vp], i32),
+        "pmbs_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -207,6 +216,19 @@ class Engine:
             return False
         self._check(st, "pmbs_step")
         return True
+
+    def step_graph(self, batch, substeps_per_launch=240):
+        self._check(self.lib.pmbs_step_graph(self.ctx, batch, substeps_per_launch), "pmbs_step_graph")
+
+    def autotune(self, scene_ids, first_push, depth, seeds=None, substeps=240):
+        scene_ids = np.ascontiguousarray(scene_ids, np.int32)
+        first_push = np.ascontiguousarray(first_push, np.float32)
+        n = scene_ids.shape[0]
+        seeds = np.ascontiguousarray(np.zeros(n, np.uint64) if seeds is None else seeds, np.uint64)
+        g, w, m, t = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
+        self._check(self.lib.pmbs_autotune(self.ctx, n, _p(scene_ids), _p(first_push), depth, _p(seeds), substeps,
+                                           C.byref(g), C.byref(w), C.byref(m), C.byref(t)), "pmbs_autotune")
+        return dict(lanes_per_env=g.value, warps_per_block=w.value, smem_manifolds=m.value, ms=t.value)
 
     def batch_info(self, batch):
         ne, nb = C.c_int32(), C.c_int32()
@@ -330,6 +352,64 @@ class Engine:
         out["events"] = self.query_events(b)
         self.release_batch(b)
         return out
+
+
+class Server:
+    """Continuous-batching request server on an Engine (pmbs_server_* calls)."""
+
+    def __init__(self, engine: Engine, n_streams: int = 8, max_inflight: int = 64):
+        self.engine = engine
+        self.lib = engine.lib
+        self.sv = C.c_void_p()
+        st = self.lib.pmbs_server_create(engine.ctx, n_streams, max_inflight, C.byref(self.sv))
+        if st != PMBS_OK:
+            raise PmbsError(st, "pmbs_server_create failed")
+        self._n = {}
+
+    def submit(self, scene_ids, first_push, depth, seeds=None) -> int:
+        scene_ids = np.ascontiguousarray(scene_ids, np.int32)
+        first_push = np.ascontiguousarray(first_push, np.float32)
+        n = scene_ids.shape[0]
+        seeds = np.ascontiguousarray(np.zeros(n, np.uint64) if seeds is None else seeds, np.uint64)
+        t = C.c_int64()
+        st = self.lib.pmbs_server_submit(self.sv, n, _p(scene_ids), _p(first_push), depth, _p(seeds), C.byref(t))
+        if st != PMBS_OK:
+            raise PmbsError(st, "pmbs_server_submit")
+        self._n[t.value] = n
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        n = self._n[ticket]
+        cost = np.zeros(max(n, 1), np.int32)
+        reward = np.zeros(max(n, 1), np.float32)
+        flags = np.zeros(max(n, 1), np.uint8)
+        steps = np.zeros(max(n, 1), np.int32)
+        lat = C.c_double()
+        st = self.lib.pmbs_server_wait(self.sv, ticket, timeout_ms, _p(cost), _p(reward), _p(flags), _p(steps),
+                                       C.byref(lat))
+        if st in (PMBS_E_NOT_READY, PMBS_E_TIMEOUT):
+            return None
+        self._n.pop(ticket, None)
+        if st != PMBS_OK:
+            raise PmbsError(st, "pmbs_server_wait")
+        return dict(cost=cost[:n], reward=reward[:n], flags=flags[:n], steps=steps[:n], latency_ms=lat.value)
+
+    def stats(self):
+        out = np.zeros(8, np.float64)
+        self.lib.pmbs_server_stats(self.sv, _p(out))
+        keys = ["completed", "env_steps", "span_s", "p50_ms", "p99_ms", "mean_ms", "peak_bytes", "outstanding"]
+        return dict(zip(keys, out.tolist()))
+
+    def close(self):
+        if self.sv:
+            self.lib.pmbs_server_destroy(self.sv)
+            self.sv = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # Module-level names matching the C ABI, for callers that manage handles themselves.
