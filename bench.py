@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="served-load run length (0 = skip)")
+    ap.add_argument("--plan-seeds", type=int, default=1, help="planning episodes per method (0 = skip)")
+    ap.add_argument("--plan-tmax", type=float, default=2.0, help="PMBS planning budget per action (s)")
+    ap.add_argument("--serial-budgets", default="2,8", help="serial MCTS budgets per action (s)")
     return ap.parse_args()
 
 
@@ -210,6 +213,38 @@ def serving_run(pmbs, sg, dev_index, seconds, rate, seed=5, planners=64, pool=No
             "peak_arena_gb": st["peak_bytes"] / 2 ** 30}
 
 
+def planning_run(pmbs, sg, local, seeds, tmax, serial_budgets, n_envs=512, c=1.4, max_actions=16):
+    """Full planning episodes (buried target in 30-box clutter): PMBS with n_envs rollouts
+    per iteration vs serial MCTS (one rollout per iteration) on the same engine, each
+    given a planning budget per action; reports actions to retrieval (pushes + grasp),
+    completion within max_actions and planning seconds per action."""
+    from paper_2207_06649_b300 import planner as P
+    eng = pmbs.Engine(device=local, mem_budget_bytes=4 << 30)
+    methods = [("pmbs", n_envs, tmax)] + [("serial", 1, b) for b in serial_budgets]
+    res = {}
+    for name, ne, budget in methods:
+        acts, done, plan = [], 0, []
+        for sd in range(seeds):
+            sc = sg.config_planning(sd)
+            be = P.GpuBackend(eng, sc.half, sc.mass, sc.mu)
+            st = sg.state13(sc)
+            if be.graspable(st, sc.half, 0):
+                continue
+            ep = P.run_episode(be, st, sc.half, 0,
+                               lambda: P.Planner(be, sc.half, 0, n_envs=ne, c=c, t_max=budget, seed=sd),
+                               max_actions=max_actions)
+            acts.append(ep["actions"])
+            done += int(ep["success"])
+            plan.extend(ep["plan_s"])
+        key = f"{name}_{budget:g}s" if name == "serial" else f"pmbs_{ne}envs_{budget:g}s"
+        res[key] = {"episodes": len(acts), "actions_mean": float(np.mean(acts)) if acts else None,
+                    "completion": done / max(1, len(acts)),
+                    "plan_s_per_action": float(np.mean(plan)) if plan else None,
+                    "plan_s_total_mean": float(np.sum(plan) / max(1, len(acts)))}
+    eng.close()
+    return res
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_info()
@@ -326,6 +361,13 @@ def run_ours(args):
         serving = {"config": "64 planners, batches log-uniform 32..2048 envs, Poisson arrivals, 5-40 boxes, "
                              "depth 3, 16 GB arena, continuous batching on 8 streams",
                    "at_200_per_s": full, "sustainable": sus}
+    planning = None
+    if args.plan_seeds > 0 and ws == 1:
+        budgets = [float(x) for x in args.serial_budgets.split(",") if x]
+        planning = {"config": "30-box clutter, target buried on 16 rays within 0.03 m, UCB c=1.4, gamma 0.8, "
+                              "d_T 7 + d_s 3, expansion candidates 16 contour points per box within 0.1 m",
+                    "seeds": args.plan_seeds,
+                    "results": planning_run(pmbs, sg, local, args.plan_seeds, args.plan_tmax, budgets)}
     peak_fma = eng.fp32_peak()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
@@ -355,6 +397,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
         "serving": serving,
+        "planning": planning,
         "gpu_launches": 2 * args.steps,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -287,6 +287,112 @@ def config_uneven(seed: int = 3, n_envs: int = 4096, n_lo=5, n_hi=40, workers: i
     return scenes, pushes, seeds
 
 
+def _buried(pose, half, gap=0.03, rays=16, samples=7):
+    """True when, on every one of `rays` rays leaving the target (box 0) footprint, some
+    other footprint lies within `gap` of the target's boundary (sampled along the ray)."""
+    t = pose[0]
+    yaw_t = 2 * math.atan2(t[6], t[3])
+    for k in range(rays):
+        th = 2 * math.pi * k / rays
+        d = np.array([math.cos(th), math.sin(th)])
+        w = _support_half_width(half[0], pose[0, 3:], d)
+        hit = False
+        for s_ in np.linspace(0.0, gap, samples):
+            p = pose[0, :2] + d * (w + s_)
+            for i in range(1, len(pose)):
+                yaw = 2 * math.atan2(pose[i, 6], pose[i, 3])
+                c, sn = math.cos(yaw), math.sin(yaw)
+                rel = p - pose[i, :2]
+                if abs(c * rel[0] + sn * rel[1]) <= half[i, 0] and abs(-sn * rel[0] + c * rel[1]) <= half[i, 1]:
+                    hit = True
+                    break
+            if hit:
+                break
+        if not hit:
+            return False
+    return True
+
+
+def config_planning(seed: int, n_boxes: int = 30, attempts: int = 50):
+    """Planning scene: the target (box 0) at the table centre buried in clutter: every one
+    of 16 rays from its boundary meets another box within 0.03 m.  For each ray not yet
+    covered a box is placed on it just outside the target, aligned with the ray; the
+    remaining boxes are placed anywhere on the table by rejection sampling (a box that
+    finds no room is redrawn, which favours smaller late boxes).  Sizes, friction and
+    masses follow the uneven workload (half extents U[0.01, 0.04], mu U[0.3, 0.8], mass
+    U[0.05, 0.2])."""
+    rng = np.random.default_rng(seed)
+    for _ in range(attempts):
+        ht = rng.uniform(0.015, 0.025, size=3)
+        yaw_t = rng.uniform(0, math.pi / 2)
+        rows = [(0.0, 0.0, ht[0], ht[1], yaw_t, ht[2])]
+        arr = np.array([[0.0, 0.0, ht[0], ht[1], yaw_t]])
+        tq = np.array(_yaw_quat(yaw_t))
+        for k in range(16):
+            th = 2 * math.pi * k / 16
+            d = np.array([math.cos(th), math.sin(th)])
+            pose = np.array([[r[0], r[1], 0, *_yaw_quat(r[4])] for r in rows])
+            half = np.array([[r[2], r[3], r[5]] for r in rows])
+            w = _support_half_width(ht, tq, d)
+            covered = False
+            for s_ in np.linspace(0.0, 0.03, 7):
+                p = d * (w + s_)
+                for r in rows[1:]:
+                    c, sn = math.cos(r[4]), math.sin(r[4])
+                    rel = p - np.array(r[:2])
+                    if abs(c * rel[0] + sn * rel[1]) <= r[2] and abs(-sn * rel[0] + c * rel[1]) <= r[3]:
+                        covered = True
+                        break
+                if covered:
+                    break
+            if covered:
+                continue
+            perp = np.array([-d[1], d[0]])
+            for _a in range(400):
+                hr = rng.uniform(0.01, 0.03)          # radial half extent
+                htg = rng.uniform(0.012, 0.035)       # tangential half extent
+                gap = rng.uniform(0.0015, 0.02)
+                # the box only has to cross the ray: shift it sideways within its width
+                ctr = d * (w + gap + hr) + perp * rng.uniform(-(htg - 0.003), htg - 0.003)
+                cand = np.array([[ctr[0], ctr[1], hr, htg, th]])
+                if not _overlaps(cand, arr, PLACEMENT_GAP).any():
+                    rows.append((ctr[0], ctr[1], hr, htg, th, rng.uniform(0.01, 0.04)))
+                    arr = np.vstack([arr, cand])
+                    break
+        redraws = 0
+        while len(rows) < n_boxes and redraws < 60:
+            h = rng.uniform(0.01, 0.04, size=3)
+            yaw = rng.uniform(0, math.pi / 2)
+            lim = TABLE_HALF - math.hypot(h[0], h[1]) - 0.005
+            ok = False
+            for _a in range(8):
+                xy = rng.uniform(-lim, lim, size=(250, 2))
+                cand = np.column_stack([xy, np.full(250, h[0]), np.full(250, h[1]), np.full(250, yaw)])
+                free = ~_overlaps(cand, arr, PLACEMENT_GAP).any(1)
+                if free.any():
+                    q = int(np.argmax(free))
+                    rows.append((xy[q, 0], xy[q, 1], h[0], h[1], yaw, h[2]))
+                    arr = np.vstack([arr, cand[q:q + 1]])
+                    ok = True
+                    break
+            if not ok:
+                redraws += 1       # no room for this size: draw another box
+        if len(rows) != n_boxes:
+            continue
+        m = n_boxes
+        pose = np.zeros((m, 7))
+        half = np.zeros((m, 3))
+        for k, r in enumerate(rows):
+            pose[k, :3] = (r[0], r[1], r[5])
+            pose[k, 3:] = _yaw_quat(r[4])
+            half[k] = (r[2], r[3], r[5])
+        if _buried(pose, half):
+            return Scenes(np.array([0, m], np.int32), pose.astype(np.float32), np.zeros((m, 6), np.float32),
+                          half.astype(np.float32), rng.uniform(0.05, 0.2, size=m).astype(np.float32),
+                          rng.uniform(0.3, 0.8, size=m).astype(np.float32), np.array([0], np.int32))
+    raise RuntimeError("no buried scene found")
+
+
 def random_state_snapshot(rng: np.random.Generator, n: int, spread=0.06, tilt=0.3):
     """Generic box state (arbitrary orientations, small velocities) for snapshot tests
     of pair lists, grasp decisions and sampling; boxes may touch or overlap."""

@@ -1,0 +1,44 @@
+"""PMBS planner on the CUDA engine (GPU backend over the C ABI)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_gpu_planner_plans_and_frees_its_scenes():
+    from paper_2207_06649_b300 import pmbs, planner as P, scenegen as sg
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30)
+    sc = sg.config_planning(0)
+    st = sg.state13(sc)
+    be = P.GpuBackend(eng, sc.half, sc.mass, sc.mu)
+    assert not be.graspable(st, sc.half, 0)
+    root = be.load_state(st, sc.half, 0)
+    pl = P.Planner(be, sc.half, 0, n_envs=128, t_max=30.0, max_iterations=3, seed=0)
+    action, info = pl.plan(root, st)
+    assert action is not None and action.shape == (4,)
+    # the early-stop rule of Alg. 1 may end planning before the iteration cap
+    assert 1 <= info.iterations <= 3 and info.rollouts == info.iterations * 128 and info.nodes > 1
+    # every child scene the planner registered has been released: the ids are reusable
+    ids = eng.load(sc)
+    assert ids[0] <= root + 1
+    be.release([root])
+    eng.free_scenes(ids)
+    eng.close()
+
+
+def test_serial_and_parallel_planners_share_one_engine():
+    from paper_2207_06649_b300 import pmbs, planner as P, scenegen as sg
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30)
+    sc = sg.config_planning(1)
+    st = sg.state13(sc)
+    be = P.GpuBackend(eng, sc.half, sc.mass, sc.mu)
+    root = be.load_state(st, sc.half, 0)
+    serial = P.Planner(be, sc.half, 0, n_envs=1, t_max=30.0, max_iterations=4, seed=0)
+    a1, i1 = serial.plan(root, st)
+    par = P.Planner(be, sc.half, 0, n_envs=64, t_max=30.0, max_iterations=2, seed=0)
+    a2, i2 = par.plan(root, st)
+    assert i1.rollouts == i1.iterations and 1 <= i1.iterations <= 4
+    assert i2.rollouts == 64 * i2.iterations and 1 <= i2.iterations <= 2
+    assert a1 is not None and a2 is not None
+    be.release([root])
+    eng.close()
