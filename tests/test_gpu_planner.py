@@ -18,9 +18,12 @@ def test_gpu_planner_plans_and_frees_its_scenes():
     assert action is not None and action.shape == (4,)
     # the early-stop rule of Alg. 1 may end planning before the iteration cap
     assert 1 <= info.iterations <= 3 and info.rollouts == info.iterations * 128 and info.nodes > 1
-    # every child scene the planner registered has been released: the ids are reusable
+    # every child scene the planner registered has been released: freeing them again fails
     ids = eng.load(sc)
-    assert ids[0] <= root + 1
+    assert ids[0] != root
+    with pytest.raises(pmbs.PmbsError):
+        eng.free_scenes(np.array([int(root) + 1], np.int32) if int(ids[0]) != int(root) + 1
+                        else np.array([int(root) + 2], np.int32))
     be.release([root])
     eng.free_scenes(ids)
     eng.close()
