@@ -254,9 +254,9 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2207_06649_b300 import flops, pmbs, scenegen as sg
+    from paper_2207_06649_b300 import flops, multigpu, pmbs, scenegen as sg
 
-    scenes, pushes, seeds = sg.config_uneven(seed=args.seed + 1000 * rank, n_envs=args.envs)
+    scenes, pushes, seeds = sg.config_uneven(seed=multigpu.rank_seed(args.seed, rank), n_envs=args.envs)
     stream = torch.cuda.current_stream()
     eng = pmbs.Engine(device=local, mem_budget_bytes=8 << 30, max_envs=max(args.envs, 1),
                       stream=pmbs.C.c_void_p(stream.cuda_stream))
@@ -308,15 +308,7 @@ def run_ours(args):
     kernel_s = float(np.mean([a.elapsed_time(b) for a, b in zip(k0, k1)])) / 1e3
     for b in batches:
         eng.release_batch(b)
-    total_env_steps = env_steps * args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        s = torch.tensor([total_env_steps], device=dev, dtype=torch.float64)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        total_env_steps = int(s.item())
+    elapsed, total_env_steps = multigpu.reduce_job(elapsed, env_steps * args.steps, device=dev)
     value = total_env_steps / elapsed
 
     # end to end through the C ABI with host buffers
