@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": None, "bytes_per_launch": None, "note": None}
+TRAFFIC = {"source_sha": "b966a75c22c64006", "bytes_per_launch": 43674602,
+           "note": "ncu dram bytes of a 1024-env launch scaled by env-steps to the 4096-env launch"}
 
 
 def kernel_source_sha():
@@ -60,6 +61,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="served-load run length (0 = skip)")
     ap.add_argument("--plan-seeds", type=int, default=1, help="planning episodes per method (0 = skip)")
+    ap.add_argument("--arena-gb", type=float, default=8.0, help="device arena of the timed engine")
     ap.add_argument("--plan-tmax", type=float, default=2.0, help="PMBS planning budget per action (s)")
     ap.add_argument("--serial-budgets", default="2,8", help="serial MCTS budgets per action (s)")
     return ap.parse_args()
@@ -258,7 +260,7 @@ def run_ours(args):
 
     scenes, pushes, seeds = sg.config_uneven(seed=multigpu.rank_seed(args.seed, rank), n_envs=args.envs)
     stream = torch.cuda.current_stream()
-    eng = pmbs.Engine(device=local, mem_budget_bytes=8 << 30, max_envs=max(args.envs, 1),
+    eng = pmbs.Engine(device=local, mem_budget_bytes=int(args.arena_gb * 2 ** 30), max_envs=max(args.envs, 1),
                       stream=pmbs.C.c_void_p(stream.cuda_stream))
     ids = eng.load(scenes)
     d_ids = torch.from_numpy(ids.astype(np.int32)).to(dev)
