@@ -102,6 +102,12 @@ typedef struct {
     int warps_per_block;        /* launch shape (1, 2 or 4); 0 = autotune */
     int smem_points;            /* contact point slots (4 per manifold) in shared memory; -1 = auto */
     int smem_manifolds;         /* manifolds kept in shared memory per env (wins); -1 = auto */
+    float watchdog_ms;          /* per environment and launch run-time limit (10000 ms, read
+                                   as SM clock cycles at 2 GHz); an environment over it
+                                   stops after its current substep, keeps its progress,
+                                   and pmbs_step / pmbs_query_cost report PMBS_E_TIMEOUT;
+                                   the next pmbs_step resumes it */
+    float max_initial_penetration; /* 1e-3 m: scenes with deeper box-box overlap are refused */
 } pmbs_config;
 
 /* Fill *cfg with the defaults listed above.  Never fails. */
@@ -130,8 +136,9 @@ const char* pmbs_last_error(const pmbs_ctx* ctx);
  * qz), vel [B][6] (linear, angular; NULL = at rest), half_ext [B][3], mass [B], mu [B];
  * target[s] is the local index of its target box.  Writes one id per scene to
  * out_scene_ids.  Validation: finite values, | |q| - 1 | <= 1e-3, 1 <= n <= max boxes,
- * positive half extents and mass, target in range -> else PMBS_E_INVALID; no room in the
- * arena -> PMBS_E_OOM.  Copies synchronously. */
+ * positive half extents and mass, target in range, no box-box penetration deeper than
+ * cfg->max_initial_penetration (separating-axis test on the device) -> else
+ * PMBS_E_INVALID; no room in the arena -> PMBS_E_OOM.  Copies synchronously. */
 pmbs_status pmbs_load_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offset,
                              const float* pose, const float* vel, const float* half_ext,
                              const float* mass, const float* mu, const int32_t* target,
@@ -161,7 +168,10 @@ pmbs_status pmbs_rollout_pushes_device(pmbs_ctx* ctx, int n_envs, const int32_t*
  * (<= 0: to completion) in one persistent launch on the context's stream.  Returns
  * PMBS_OK when the batch is finished, PMBS_E_NOT_READY when substeps remain.  The call
  * synchronises the stream only when max_substeps > 0 (to report readiness); with
- * max_substeps <= 0 it returns PMBS_OK immediately after enqueueing. */
+ * max_substeps <= 0 it returns PMBS_OK immediately after enqueueing.  With
+ * max_substeps > 0: PMBS_E_TIMEOUT when an environment hit cfg->watchdog_ms in this
+ * launch (its progress is kept; call again to resume), PMBS_E_INVALID when the batch names
+ * an unknown scene id (device-side ids). */
 pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps);
 
 /* Run the batch to completion as a CUDA graph of launches that each advance every
@@ -186,12 +196,15 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
  * out_child_states (NULL to skip): [sum of boxes][13] state after push 1, the new tree
  * node of the expansion (Sec. IV-C); out_child_scene_ids (NULL to skip): registers each
  * child state as a new scene and writes its id.  Synchronises the stream.  Any output
- * pointer may be NULL. */
+ * pointer may be NULL.  PMBS_E_TIMEOUT when environments were stopped by the watchdog
+ * (the batch then counts as unfinished again and pmbs_step resumes it); PMBS_E_INVALID
+ * when the batch names an unknown scene id. */
 pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, float* out_reward,
                             uint8_t* out_flags, float* out_child_states,
                             int32_t* out_child_scene_ids);
 
-/* As pmbs_query_cost but copies into device buffers asynchronously on the stream. */
+/* As pmbs_query_cost but copies into device buffers asynchronously on the stream (no
+ * status check: entries of environments stopped by the watchdog are undefined). */
 pmbs_status pmbs_query_cost_device(pmbs_ctx* ctx, int64_t batch, int32_t* d_cost,
                                    float* d_reward, uint8_t* d_flags);
 
@@ -282,14 +295,22 @@ pmbs_status pmbs_server_submit(pmbs_server* server, int n_envs, const int32_t* s
 /* Thread-safe: wait up to timeout_ms (< 0: forever; 0: poll) for a ticket; on success the
  * results (n_envs entries each; any pointer may be NULL) and the latency from submission
  * to completion are written and the ticket is released.  PMBS_E_NOT_READY (poll) or
- * PMBS_E_TIMEOUT while the request is still pending; the request's own error otherwise. */
+ * PMBS_E_TIMEOUT while the request is still pending; PMBS_E_INVALID for an unknown or
+ * cancelled ticket; the request's own error otherwise. */
 pmbs_status pmbs_server_wait(pmbs_server* server, int64_t ticket, int timeout_ms, int32_t* out_cost,
                              float* out_reward, uint8_t* out_flags, int32_t* out_steps,
                              double* out_latency_ms);
-/* out[8]: completed requests, simulated env-steps, seconds from the first submission to
+/* out[11]: completed requests, simulated env-steps, seconds from the first submission to
  * the last completion, p50 and p99 latency (ms), mean latency (ms), peak arena bytes in
- * use, requests pending or on the device. */
+ * use, requests pending or on the device, finished results not yet claimed by a wait,
+ * relaunches after the watchdog stopped environments (each resumes them where they
+ * stopped, so results do not change), arena bytes in use now. */
 pmbs_status pmbs_server_stats(pmbs_server* server, double* out);
+
+/* Drop a ticket whose caller will never wait for it (e.g. a planner that gave up): a
+ * pending request is removed, one on the device is discarded when it completes, a finished
+ * one releases its held results.  Unknown ticket -> PMBS_E_INVALID. */
+pmbs_status pmbs_server_cancel(pmbs_server* server, int64_t ticket);
 void pmbs_server_destroy(pmbs_server* server);
 
 /* Allocation-free rollout.  The paper has no counterpart: this entry point exists for

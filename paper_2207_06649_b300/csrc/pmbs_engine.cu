@@ -424,6 +424,39 @@ __global__ void __launch_bounds__(1024) prepare_batch_kernel(int n_envs, const i
     }
 }
 
+// Deepest box-box penetration of each scene (one warp per scene, one lane per pair, the
+// rollout engine's separating-axis test); out[s] = max(0, -separation).
+__global__ void __launch_bounds__(128) penetration_kernel(int n_scenes, const int32_t* box_offset,
+                                                          const float* rec, float* out) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= n_scenes) return;
+    const int b0 = box_offset[s] - box_offset[0], n = box_offset[s + 1] - box_offset[s];
+    const int T = n * (n - 1) / 2;
+    float worst = 0.f;
+    for (int t = lane; t < T; t += 32) {
+        int i, j;
+        pair_of_index(t, n, i, j);
+        CBox A, B;
+        const float* ra = rec + (size_t)kRecFloats * (b0 + i);
+        const float* rb = rec + (size_t)kRecFloats * (b0 + j);
+        A.c = f3(ra[0], ra[1], ra[2]);
+        B.c = f3(rb[0], rb[1], rb[2]);
+        quat_to_R_exact(ra[3], ra[4], ra[5], ra[6], A.R);
+        quat_to_R_exact(rb[3], rb[4], rb[5], rb[6], B.R);
+        for (int k = 0; k < 3; k++) {
+            A.h[k] = ra[13 + k];
+            B.h[k] = rb[13 + k];
+        }
+        CManifold cm;
+        int clip = 0;
+        if (collide_box_box(A, B, 0.f, cm, clip))
+            for (int p = 0; p < cm.np; p++) worst = fmaxf(worst, -cm.d[p]);
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if (lane == 0) out[s] = worst;
+}
+
 // Scene table update: table[ids[i]] = desc[i].
 __global__ void scatter_desc_kernel(int n, const int32_t* ids, const SceneDesc* desc, SceneDesc* table) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -763,7 +796,8 @@ pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, s
         c.pgs_iters < 0 || !(c.dt > 0) || c.grasp_angles < 1 || c.grasp_angles > 32 || c.sample_attempts < 1 ||
         c.sample_attempts > 32 || c.contour_points < 1 || c.contact_cap < 4 || c.manifold_cap < 1 ||
         c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096 || !(c.pusher_speed > 0) ||
-        !(c.pusher_radius > 0) || !(c.lanes_per_env == 0 || c.lanes_per_env == 8 || c.lanes_per_env == 16 ||
+        !(c.pusher_radius > 0) || !(c.watchdog_ms > 0) || !(c.max_initial_penetration >= 0) ||
+        !(c.lanes_per_env == 0 || c.lanes_per_env == 8 || c.lanes_per_env == 16 ||
                                     c.lanes_per_env == 32))
         return PMBS_E_INVALID;
     pmbs_ctx* ctx = new pmbs_ctx();
@@ -980,7 +1014,7 @@ pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaStream
     a.events = b.events;
     a.gscratch = scratch;
     a.scratch_f4_per_warp = scratch_f4_per_warp(c.manifold_cap);
-    a.watchdog_cycles = 20LL * 1000 * 1000 * 1000;  // about 10 s of SM clock per env and launch
+    a.watchdog_cycles = (long long)((double)c.watchdog_ms * 2.0e6);  // SM cycles at up to 2 GHz
     a.watchdog_flag = b.counters + 4;
     CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), stream));
     rollout_kernel<<<blocks, threads, smem, stream>>>(a);
@@ -993,19 +1027,53 @@ Batch* find_batch(pmbs_ctx* ctx, int64_t id) {
     return it == ctx->batches.end() ? nullptr : &it->second;
 }
 
-// Copy the records of n_scenes scenes into one arena block, assign ids and publish the
+// Copy the records of n_scenes scenes into one arena block, validate them (deepest initial
+// box-box penetration, on the device) when asked, then assign ids and publish the
 // descriptors to the device scene table (one copy of the records, one scatter).
 pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offset, const float* rec_host,
-                            const int32_t* target, int32_t* out_ids) {
+                            const int32_t* target, int32_t* out_ids, bool check_penetration) {
     const int total = box_offset[n_scenes] - box_offset[0];
     const size_t rec_bytes = sizeof(float) * kRecFloats * (size_t)std::max(total, 1);
     const size_t meta = sizeof(int32_t) * n_scenes, meta_al = (meta + 255) & ~(size_t)255;
     const size_t desc_bytes = sizeof(SceneDesc) * n_scenes;
+    const size_t pen_bytes = sizeof(float) * n_scenes, pen_al = (pen_bytes + 255) & ~(size_t)255;
     const size_t rec_al = (rec_bytes + 255) & ~(size_t)255;
-    // block layout: records | staging ids | staging descriptors (staging reused per call)
-    const size_t bytes = rec_al + meta_al + desc_bytes;
+    // block layout: records | staging ids (also the CSR offsets for validation) | staging
+    // descriptors | penetration per scene (staging is reused per call)
+    const size_t off_bytes = sizeof(int32_t) * (n_scenes + 1), off_al = (off_bytes + 255) & ~(size_t)255;
+    const size_t stage = std::max(meta_al, off_al);
+    const size_t bytes = rec_al + stage + ((desc_bytes + 255) & ~(size_t)255) + pen_al;
     const size_t off = ctx->arena.alloc(bytes);
     if (off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "scene store is full");
+    char* base = (char*)arena_ptr(ctx, off);
+    char* stage_p = base + rec_al;
+    char* desc_p = stage_p + stage;
+    float* pen_p = (float*)(desc_p + ((desc_bytes + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemcpyAsync(base, rec_host, sizeof(float) * kRecFloats * (size_t)total,
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && check_penetration && n_scenes > 0) {
+        std::vector<float> pen(n_scenes, 0.f);
+        e = cudaMemcpyAsync(stage_p, box_offset, off_bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) {
+            penetration_kernel<<<(n_scenes + 3) / 4, 128, 0, ctx->stream>>>(n_scenes, (const int32_t*)stage_p,
+                                                                           (const float*)base, pen_p);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pen.data(), pen_p, pen_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess)
+            for (int s = 0; s < n_scenes; s++)
+                if (pen[s] > ctx->cfg.max_initial_penetration) {
+                    ctx->arena.release(off, bytes);
+                    return fail(ctx, PMBS_E_INVALID, "scene " + std::to_string(s) + " starts with box-box penetration " +
+                                                         std::to_string(pen[s]) + " m");
+                }
+    }
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(ctx->stream);
+        ctx->arena.release(off, bytes);
+        return fail(ctx, PMBS_E_CUDA, std::string("scene upload: ") + cudaGetErrorString(e));
+    }
     std::vector<int> ids(n_scenes);
     for (int s = 0; s < n_scenes; s++) {
         int id;
@@ -1016,6 +1084,7 @@ pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offs
             id = (int)ctx->scenes.size();
             if (id >= kSceneTableCap) {
                 for (int t = 0; t < s; t++) ctx->free_ids.push_back(ids[t]);
+                cudaStreamSynchronize(ctx->stream);
                 ctx->arena.release(off, bytes);
                 return fail(ctx, PMBS_E_OOM, "scene table full");
             }
@@ -1023,7 +1092,6 @@ pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offs
         }
         ids[s] = id;
     }
-    char* base = (char*)arena_ptr(ctx, off);
     std::vector<SceneDesc> desc(n_scenes);
     for (int s = 0; s < n_scenes; s++) {
         SceneRec& r = ctx->scenes[ids[s]];
@@ -1041,11 +1109,10 @@ pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offs
     blk.bytes = bytes;
     blk.live = n_scenes;
     ctx->blocks[off] = blk;
-    CU(cudaMemcpyAsync(base, rec_host, sizeof(float) * kRecFloats * (size_t)total, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(base + rec_al, ids.data(), meta, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(base + rec_al + meta_al, desc.data(), desc_bytes, cudaMemcpyHostToDevice, ctx->stream));
-    scatter_desc_kernel<<<(n_scenes + 255) / 256, 256, 0, ctx->stream>>>(
-        n_scenes, (const int32_t*)(base + rec_al), (const SceneDesc*)(base + rec_al + meta_al), ctx->d_table);
+    CU(cudaMemcpyAsync(stage_p, ids.data(), meta, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(desc_p, desc.data(), desc_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    scatter_desc_kernel<<<(n_scenes + 255) / 256, 256, 0, ctx->stream>>>(n_scenes, (const int32_t*)stage_p,
+                                                                         (const SceneDesc*)desc_p, ctx->d_table);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(ctx->stream));
     for (int s = 0; s < n_scenes; s++) out_ids[s] = ids[s];
@@ -1194,6 +1261,8 @@ void pmbs_default_config(pmbs_config* c) {
     c->warps_per_block = 0;
     c->smem_points = -1;
     c->smem_manifolds = -1;
+    c->watchdog_ms = 10000.f;
+    c->max_initial_penetration = 1e-3f;
 }
 
 pmbs_status pmbs_create(const pmbs_config* cfg, void* cuda_stream, pmbs_ctx** out) {
@@ -1255,7 +1324,7 @@ pmbs_status pmbs_load_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_off
         if (!(h[0] > 0 && h[1] > 0 && h[2] > 0) || !(r[16] > 0) || !(r[17] >= 0))
             return fail(ctx, PMBS_E_INVALID, "non-positive half extent or mass, or negative friction");
     }
-    return register_scenes(ctx, n_scenes, box_offset, rec.data(), target, out_scene_ids);
+    return register_scenes(ctx, n_scenes, box_offset, rec.data(), target, out_scene_ids, true);
 }
 
 pmbs_status pmbs_free_scenes(pmbs_ctx* ctx, int n, const int32_t* scene_ids) {
@@ -1345,7 +1414,13 @@ pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps) {
     int cnt[5] = {0, 0, 0, 0, 0};
     CU(cudaMemcpyAsync(cnt, b->counters, sizeof(cnt), cudaMemcpyDeviceToHost, b->stream));
     CU(cudaStreamSynchronize(b->stream));
-    if (cnt[4]) return fail(ctx, PMBS_E_TIMEOUT, "an environment exceeded the per-launch time limit");
+    if (cnt[1]) return fail(ctx, PMBS_E_INVALID, "the batch names an unknown scene id");
+    if (cnt[4]) {
+        // the stopped environments kept their progress: clear the flag so that the next
+        // call resumes them
+        CU(cudaMemsetAsync(b->counters + 4, 0, sizeof(int), b->stream));
+        return fail(ctx, PMBS_E_TIMEOUT, "an environment exceeded the per-launch time limit");
+    }
     const int done = cnt[3];
     if (done >= b->n_envs) {
         b->finished = true;
@@ -1467,9 +1542,16 @@ pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, flo
     if (!b->finished) return fail(ctx, PMBS_E_NOT_READY, "batch not finished");
     const int n = b->n_envs;
     if (n == 0) return PMBS_OK;
-    int wd = 0;
-    CU(cudaMemcpy(&wd, b->counters + 4, sizeof(int), cudaMemcpyDeviceToHost));
-    if (wd) return fail(ctx, PMBS_E_TIMEOUT, "an environment exceeded the per-launch time limit");
+    int cnt[5] = {0, 0, 0, 0, 0};
+    CU(cudaMemcpyAsync(cnt, b->counters, sizeof(cnt), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    if (cnt[1]) return fail(ctx, PMBS_E_INVALID, "the batch names an unknown scene id");
+    if (cnt[3] < n) {
+        // environments stopped by the watchdog kept their progress; pmbs_step resumes them
+        b->finished = false;
+        CU(cudaMemsetAsync(b->counters + 4, 0, sizeof(int), b->stream));
+        return fail(ctx, PMBS_E_TIMEOUT, std::to_string(n - cnt[3]) + " environments exceeded the per-launch time limit");
+    }
     if (out_cost) CU(cudaMemcpyAsync(out_cost, b->cost, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
     if (out_reward) CU(cudaMemcpyAsync(out_reward, b->reward, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
     if (out_flags) CU(cudaMemcpyAsync(out_flags, b->flags, n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1505,7 +1587,8 @@ pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, flo
                     r[k] = (parent && parent->live) ? parent->host[(size_t)kRecFloats * i + k] : 1.f;
             }
         }
-        const pmbs_status st = register_scenes(ctx, n, off.data(), rec.data(), tgt.data(), out_child_scene_ids);
+        // child states come out of the solver and may rest within the contact slop
+        const pmbs_status st = register_scenes(ctx, n, off.data(), rec.data(), tgt.data(), out_child_scene_ids, false);
         if (st != PMBS_OK) return st;
     }
     return PMBS_OK;
@@ -1734,6 +1817,8 @@ struct Request {
     int stream = -1;
     cudaEvent_t done_ev = nullptr;
     bool finished = false;
+    bool abandoned = false;  // cancelled while on the device: dropped when it retires
+    int resumes = 0;         // relaunches after the watchdog stopped environments
     pmbs_status status = PMBS_OK;
     std::vector<int32_t> cost, steps;
     std::vector<float> reward;
@@ -1760,6 +1845,8 @@ struct pmbs_server {
     double env_steps = 0.0;
     int64_t completed = 0;
     size_t peak_used = 0;
+    int64_t resumes = 0;
+    int64_t admitting = 0;  // ticket being admitted with the server lock released
     std::chrono::steady_clock::time_point t_first, t_last;
     bool any = false;
 };
@@ -1800,25 +1887,42 @@ pmbs_status server_admit(pmbs_server* sv, Request& r) {
     return PMBS_OK;
 }
 
-// Copy a finished request's results back and free its batch.
-void server_retire(pmbs_server* sv, Request& r) {
+// A request's launch has completed.  When the watchdog stopped some of its environments
+// (they keep their progress), clear the flag and relaunch the batch on its stream, which
+// resumes them, and return false.  Otherwise copy the results back, free the batch and
+// return true.
+bool server_retire(pmbs_server* sv, Request& r) {
     pmbs_ctx* ctx = sv->ctx;
     std::lock_guard<std::mutex> lk(ctx->mu);
     Batch* b = find_batch(ctx, r.batch);
     const int n = r.n_envs;
+    cudaError_t e = cudaSuccess;
+    int cnt[5] = {0, 0, 0, 0, 0};
+    if (b && n > 0) {
+        e = cudaMemcpyAsync(cnt, b->counters, sizeof(cnt), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e == cudaSuccess && cnt[4] && !cnt[1]) {
+            e = cudaMemsetAsync(b->counters + 4, 0, sizeof(int), b->stream);
+            if (e == cudaSuccess && launch_rollout(ctx, *b, 0, b->stream) == PMBS_OK &&
+                (!r.done_ev || cudaEventRecord(r.done_ev, b->stream) == cudaSuccess)) {
+                r.resumes++;
+                return false;
+            }
+            if (e == cudaSuccess) e = cudaErrorLaunchFailure;
+        }
+    }
     r.cost.assign(n, 0);
     r.reward.assign(n, 0.f);
     r.flags.assign(n, 0);
     r.steps.assign(n, 0);
-    cudaError_t e = cudaSuccess;
-    int wd = 0;
-    if (b && n > 0) {
+    if (b && n > 0 && e == cudaSuccess) {
         e = cudaMemcpyAsync(r.cost.data(), b->cost, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(r.reward.data(), b->reward, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(r.flags.data(), b->flags, n, cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(r.steps.data(), b->steps, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&wd, b->counters + 4, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    } else if (b) {
+        cudaStreamSynchronize(b->stream);
     }
     if (b) {
         release_batch_mem(ctx, *b);
@@ -1826,9 +1930,10 @@ void server_retire(pmbs_server* sv, Request& r) {
     }
     if (r.done_ev) cudaEventDestroy(r.done_ev);
     r.done_ev = nullptr;
-    r.status = e != cudaSuccess ? PMBS_E_CUDA : (wd ? PMBS_E_TIMEOUT : PMBS_OK);
+    r.status = e != cudaSuccess ? PMBS_E_CUDA : (cnt[1] ? PMBS_E_INVALID : PMBS_OK);
     r.t_done = std::chrono::steady_clock::now();
     // r.finished is set by the caller under the server lock
+    return true;
 }
 
 void server_loop(pmbs_server* sv) {
@@ -1838,13 +1943,20 @@ void server_loop(pmbs_server* sv) {
         bool progressed = false;
         // admit in arrival order while memory and the in-flight limit allow
         while (!sv->pending.empty() && (int)sv->inflight.size() < sv->max_inflight) {
-            Request& r = sv->reqs[sv->pending.front()];
+            const int64_t t = sv->pending.front();
+            Request& r = sv->reqs[t];
+            sv->admitting = t;  // a cancel now only marks the request
             lk.unlock();
             const pmbs_status st = server_admit(sv, r);
             lk.lock();
-            if (st == PMBS_E_OOM && !sv->inflight.empty()) break;  // wait for memory to free up
+            sv->admitting = 0;
+            if (st == PMBS_E_OOM && !sv->inflight.empty() && !r.abandoned) break;  // wait for memory to free up
             sv->pending.pop_front();
             progressed = true;
+            if (r.abandoned && st != PMBS_OK) {
+                sv->reqs.erase(t);
+                continue;
+            }
             if (st != PMBS_OK) {
                 r.status = st;
                 r.finished = true;
@@ -1863,16 +1975,23 @@ void server_loop(pmbs_server* sv) {
                 continue;
             }
             lk.unlock();
-            server_retire(sv, r);
+            const bool retired = server_retire(sv, r);
             lk.lock();
+            progressed = true;
+            if (!retired) {
+                i++;
+                continue;
+            }
             const double ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
             sv->latencies_ms.push_back(ms);
             for (int32_t s : r.steps) sv->env_steps += s;
             sv->completed++;
+            sv->resumes += r.resumes;
             sv->t_last = r.t_done;
             r.finished = true;
+            const int64_t t = sv->inflight[i];
             sv->inflight.erase(sv->inflight.begin() + (long)i);
-            progressed = true;
+            if (r.abandoned) sv->reqs.erase(t);
             sv->cv_done.notify_all();
         }
         if (!progressed) {
@@ -1949,12 +2068,17 @@ pmbs_status pmbs_server_wait(pmbs_server* sv, int64_t ticket, int timeout_ms, in
                              uint8_t* out_flags, int32_t* out_steps, double* out_latency_ms) {
     if (!sv) return PMBS_E_INVALID;
     std::unique_lock<std::mutex> lk(sv->mu);
-    auto it = sv->reqs.find(ticket);
-    if (it == sv->reqs.end()) return PMBS_E_INVALID;
-    const auto pred = [&] { return it->second.finished; };
+    if (sv->reqs.find(ticket) == sv->reqs.end()) return PMBS_E_INVALID;
+    // look the ticket up afresh after every wake-up: a cancel may have dropped it
+    const auto pred = [&] {
+        auto j = sv->reqs.find(ticket);
+        return j == sv->reqs.end() || j->second.finished || j->second.abandoned;
+    };
     if (timeout_ms < 0) sv->cv_done.wait(lk, pred);
     else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
         return timeout_ms == 0 ? PMBS_E_NOT_READY : PMBS_E_TIMEOUT;
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end() || it->second.abandoned) return PMBS_E_INVALID;
     Request& r = it->second;
     const pmbs_status st = r.status;
     const int n = r.n_envs;
@@ -1983,6 +2107,35 @@ pmbs_status pmbs_server_stats(pmbs_server* sv, double* out) {
     out[5] = sv->latencies_ms.empty() ? 0.0 : mean / (double)sv->latencies_ms.size();
     out[6] = (double)sv->peak_used;
     out[7] = (double)(sv->pending.size() + sv->inflight.size());
+    size_t held = 0;
+    for (const auto& kv : sv->reqs) held += kv.second.finished ? 1 : 0;
+    out[8] = (double)held;
+    out[9] = (double)sv->resumes;
+    {
+        std::lock_guard<std::mutex> lk2(sv->ctx->mu);
+        out[10] = (double)sv->ctx->arena.used;
+    }
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_server_cancel(pmbs_server* sv, int64_t ticket) {
+    if (!sv) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return PMBS_E_INVALID;
+    Request& r = it->second;
+    auto p = std::find(sv->pending.begin(), sv->pending.end(), ticket);
+    if (ticket == sv->admitting) {
+        r.abandoned = true;
+    } else if (p != sv->pending.end()) {
+        sv->pending.erase(p);
+        sv->reqs.erase(it);
+    } else if (r.finished) {
+        sv->reqs.erase(it);
+    } else {
+        r.abandoned = true;
+    }
+    sv->cv_done.notify_all();
     return PMBS_OK;
 }
 
@@ -1998,8 +2151,9 @@ void pmbs_server_destroy(pmbs_server* sv) {
     for (auto& kv : sv->reqs) {
         Request& r = kv.second;
         if (r.batch && !r.finished) {
-            if (r.stream >= 0) cudaStreamSynchronize(sv->streams[r.stream]);
-            server_retire(sv, r);
+            do {
+                if (r.stream >= 0) cudaStreamSynchronize(sv->streams[r.stream]);
+            } while (!server_retire(sv, r));
             r.finished = true;
         }
     }
@@ -2180,7 +2334,7 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     a.events = events;
     a.gscratch = spill;
     a.scratch_f4_per_warp = f4_per_warp;
-    a.watchdog_cycles = 20LL * 1000 * 1000 * 1000;
+    a.watchdog_cycles = (long long)((double)c.watchdog_ms * 2.0e6);
     a.watchdog_flag = counters + 4;
     rollout_kernel<<<blocks, 32 * wpb, smem, stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;

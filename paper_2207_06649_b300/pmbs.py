@@ -30,7 +30,7 @@ EXPORTED = ["pmbs_default_config", "pmbs_create", "pmbs_create_with_arena", "pmb
             "pmbs_eval_pairs", "pmbs_eval_grasp", "pmbs_eval_sample", "pmbs_eval_start_blocked",
             "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_rollout_noalloc",
             "pmbs_step_graph", "pmbs_autotune", "pmbs_server_create", "pmbs_server_submit",
-            "pmbs_server_wait", "pmbs_server_stats", "pmbs_server_destroy"]
+            "pmbs_server_wait", "pmbs_server_stats", "pmbs_server_cancel", "pmbs_server_destroy"]
 
 
 class pmbs_config(C.Structure):
@@ -46,7 +46,8 @@ class pmbs_config(C.Structure):
                 ("contour_points", C.c_int), ("contact_cap", C.c_int), ("manifold_cap", C.c_int),
                 ("pair_cap", C.c_int), ("lanes_per_env", C.c_int), ("warps_per_block", C.c_int),
                 ("smem_points", C.c_int),
-                ("smem_manifolds", C.c_int)]
+                ("smem_manifolds", C.c_int), ("watchdog_ms", C.c_float),
+                ("max_initial_penetration", C.c_float)]
 
 
 class PmbsError(RuntimeError):
@@ -100,6 +101,7 @@ def load(build_if_missing: bool = True):
         "pmbs_server_submit": ([vp, i32, vp, vp, i32, vp, P(C.c_int64)], i32),
         "pmbs_server_wait": ([vp, C.c_int64, i32, vp, vp, vp, vp, P(C.c_double)], i32),
         "pmbs_server_stats": ([vp, vp], i32),
+        "pmbs_server_cancel": ([vp, C.c_int64], i32),
         "pmbs_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -394,10 +396,18 @@ class Server:
             raise PmbsError(st, "pmbs_server_wait")
         return dict(cost=cost[:n], reward=reward[:n], flags=flags[:n], steps=steps[:n], latency_ms=lat.value)
 
+    def cancel(self, ticket: int):
+        """Drop a ticket that will never be waited for."""
+        st = self.lib.pmbs_server_cancel(self.sv, ticket)
+        self._n.pop(ticket, None)
+        if st != PMBS_OK:
+            raise PmbsError(st, "pmbs_server_cancel")
+
     def stats(self):
-        out = np.zeros(8, np.float64)
+        out = np.zeros(11, np.float64)
         self.lib.pmbs_server_stats(self.sv, _p(out))
-        keys = ["completed", "env_steps", "span_s", "p50_ms", "p99_ms", "mean_ms", "peak_bytes", "outstanding"]
+        keys = ["completed", "env_steps", "span_s", "p50_ms", "p99_ms", "mean_ms", "peak_bytes", "outstanding",
+                "held_results", "resumes", "arena_used_bytes"]
         return dict(zip(keys, out.tolist()))
 
     def close(self):
