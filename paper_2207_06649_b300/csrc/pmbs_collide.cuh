@@ -28,6 +28,9 @@ struct CBox {
     float R[9];
     float h[3];
     __device__ __forceinline__ float3 ax(int k) const { return f3(R[k], R[3 + k], R[6 + k]); }
+    // runtime index through selects (keeps the box in registers)
+    __device__ __forceinline__ float3 axs(int k) const { return k == 0 ? ax(0) : (k == 1 ? ax(1) : ax(2)); }
+    __device__ __forceinline__ float hs(int k) const { return k == 0 ? h[0] : (k == 1 ? h[1] : h[2]); }
     __device__ __forceinline__ float3 rot(float3 l) const {
         return f3(R[0] * l.x + R[1] * l.y + R[2] * l.z, R[3] * l.x + R[4] * l.y + R[5] * l.z,
                   R[6] * l.x + R[7] * l.y + R[8] * l.z);
@@ -49,22 +52,33 @@ struct CManifold {
 __device__ __forceinline__ void collide_box_plane(const CBox& b, float margin, CManifold& M) {
     M.np = 0;
     M.n = f3(0.f, 0.f, 1.f);
+#pragma unroll
     for (int v = 0; v < 8; v++) {
         const float3 l = f3((v & 1) ? b.h[0] : -b.h[0], (v & 2) ? b.h[1] : -b.h[1], (v & 4) ? b.h[2] : -b.h[2]);
-        const float3 r = b.rot(l);
-        const float d = b.c.z + r.z;
+        float3 r = b.rot(l);
+        float d = b.c.z + r.z;
         if (!(d < margin)) continue;
-        // insertion into the depth-sorted list (stable: equal depths keep vertex order)
-        int pos = M.np < 4 ? M.np : 4;
-        while (pos > 0 && d < M.d[pos - 1]) pos--;
-        if (pos >= 4) continue;
-        const int last = M.np < 4 ? M.np : 3;
-        for (int k = last; k > pos; k--) {
-            M.d[k] = M.d[k - 1];
-            M.p[k] = M.p[k - 1];
+        // insertion into the depth-sorted list (stable: equal depths keep vertex order):
+        // the new entry goes before the first strictly shallower one, every later entry
+        // moves down one slot, and an entry pushed past the fourth slot is dropped
+        bool shift = false;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (k < M.np) {
+                if (shift || d < M.d[k]) {
+                    shift = true;
+                    const float td = M.d[k];
+                    const float3 tp = M.p[k];
+                    M.d[k] = d;
+                    M.p[k] = r;
+                    d = td;
+                    r = tp;
+                }
+            } else if (k == M.np) {
+                M.d[k] = d;
+                M.p[k] = r;
+            }
         }
-        M.d[pos] = d;
-        M.p[pos] = r;
         if (M.np < 4) M.np++;
     }
 }
@@ -79,10 +93,10 @@ __device__ __forceinline__ int clip_side(const float3* in, int n, float3* out, f
         const float3 prev = in[(i + n - 1) % n];
         const float dc = dot3(cur - o, a) - h, dp = dot3(prev - o, a) - h;
         if (dc <= 0.f) {
-            if (dp > 0.f && m < 8) out[m++] = prev + (cur - prev) * (dp / (dp - dc));
+            if (dp > 0.f && m < 8) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
             if (m < 8) out[m++] = cur;
         } else if (dp <= 0.f) {
-            if (m < 8) out[m++] = prev + (cur - prev) * (dp / (dp - dc));
+            if (m < 8) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
         }
     }
     return m;
@@ -91,14 +105,17 @@ __device__ __forceinline__ int clip_side(const float3* in, int n, float3* out, f
 // Clip the incident face of `inc` against the side planes of face k (outward normal
 // nref) of `ref`; keep points within the margin; reduce to four points.  Returns the
 // number of points in M (p = world point, d = separation from the reference face).
+// Box axes and extents are picked by selects so that both boxes stay in registers; only
+// the clip polygons live in per-thread memory.
 __device__ __forceinline__ int face_contact(const CBox& ref, int k, float3 nref, const CBox& inc, float margin,
                                             CManifold& M, int& clip_verts) {
-    const float3 fc = ref.c + nref * ref.h[k];
+    const float3 fc = ref.c + nref * ref.hs(k);
     const int k1 = (k == 0) ? 1 : 0, k2 = (k == 2) ? 1 : 2;
-    const float3 u = ref.ax(k1), v = ref.ax(k2);
-    const float hu = ref.h[k1], hv = ref.h[k2];
+    const float3 u = ref.axs(k1), v = ref.axs(k2);
+    const float hu = ref.hs(k1), hv = ref.hs(k2);
     int best_f = 0;
     float best = 0.f;
+#pragma unroll
     for (int m = 0; m < 3; m++) {
         const float dm = dot3(inc.ax(m), nref);
         if (m == 0 || dm < best) {
@@ -113,34 +130,39 @@ __device__ __forceinline__ int face_contact(const CBox& ref, int k, float3 nref,
     const int mi = best_f >> 1;
     const float si = (best_f & 1) ? -1.f : 1.f;
     const int m1 = (mi == 0) ? 1 : 0, m2 = (mi == 2) ? 1 : 2;
-    const float3 fi = inc.c + inc.ax(mi) * (si * inc.h[mi]);
-    const float3 e1 = inc.ax(m1) * inc.h[m1], e2 = inc.ax(m2) * inc.h[m2];
-    float3 A[8], B[8];
-    A[0] = fi + e1 + e2;
-    A[1] = fi - e1 + e2;
-    A[2] = fi - e1 - e2;
-    A[3] = fi + e1 - e2;
+    const float3 fi = inc.c + inc.axs(mi) * (si * inc.hs(mi));
+    const float3 e1 = inc.axs(m1) * inc.hs(m1), e2 = inc.axs(m2) * inc.hs(m2);
+    float3 P[2][8];
+    P[0][0] = fi + e1 + e2;
+    P[0][1] = fi - e1 + e2;
+    P[0][2] = fi - e1 - e2;
+    P[0][3] = fi + e1 - e2;
     int n = 4;
-    n = clip_side(A, n, B, fc, u, hu);
-    n = clip_side(B, n, A, fc, -u, hu);
-    n = clip_side(A, n, B, fc, v, hv);
-    n = clip_side(B, n, A, fc, -v, hv);
+    // sides +u, -u, +v, -v; the polygon alternates between the two buffers and ends in P[0]
+#pragma unroll 1
+    for (int side = 0; side < 4; side++) {
+        const float3 a = side < 2 ? u : v;
+        n = clip_side(P[side & 1], n, P[(side & 1) ^ 1], fc, (side & 1) ? -a : a, side < 2 ? hu : hv);
+    }
     clip_verts += n;
+    float3* B = P[1];
     float kd[8];
     int nk = 0;
     for (int i = 0; i < n; i++) {
-        const float d = dot3(A[i] - fc, nref);
+        const float d = dot3(P[0][i] - fc, nref);
         if (d < margin) {
-            B[nk] = A[i];
+            B[nk] = P[0][i];
             kd[nk] = d;
             nk++;
         }
     }
     if (nk <= 4) {
-        for (int i = 0; i < nk; i++) {
-            M.p[i] = B[i];
-            M.d[i] = kd[i];
-        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            if (i < nk) {
+                M.p[i] = B[i];
+                M.d[i] = kd[i];
+            }
         return nk;
     }
     // deepest; farthest from it; largest triangle; largest area added outside an edge
@@ -185,11 +207,14 @@ __device__ __forceinline__ int face_contact(const CBox& ref, int k, float3 nref,
             i4 = i;
         }
     }
-    const int sel[4] = {i1, i2, i3, i4};
-    for (int i = 0; i < 4; i++) {
-        M.p[i] = B[sel[i]];
-        M.d[i] = kd[sel[i]];
-    }
+    M.p[0] = B[i1];
+    M.d[0] = kd[i1];
+    M.p[1] = B[i2];
+    M.d[1] = kd[i2];
+    M.p[2] = B[i3];
+    M.d[2] = kd[i3];
+    M.p[3] = B[i4];
+    M.d[3] = kd[i4];
     return 4;
 }
 
@@ -234,29 +259,31 @@ __device__ __forceinline__ int collide_box_box(const CBox& A, const CBox& B, flo
     int fe = -1;
     float se = 0.f;
     float3 le = f3(0.f, 0.f, 0.f);
+#pragma unroll
     for (int i = 0; i < 3; i++)
+#pragma unroll
         for (int j = 0; j < 3; j++) {
             const float3 L = cross3(a[i], b[j]);
             const float l2 = dot3(L, L);
             if (l2 < 1e-12f) continue;
-            const float len = sqrtf(l2);
+            const float inv = rsqrtf(l2);
             const float rA = (A.h[0] * fabsf(dot3(a[0], L)) + A.h[1] * fabsf(dot3(a[1], L))) + A.h[2] * fabsf(dot3(a[2], L));
             const float rB = (B.h[0] * fabsf(dot3(b[0], L)) + B.h[1] * fabsf(dot3(b[1], L))) + B.h[2] * fabsf(dot3(b[2], L));
-            const float s = (fabsf(dot3(D, L)) - (rA + rB)) / len;
+            const float s = (fabsf(dot3(D, L)) - (rA + rB)) * inv;
             if (s >= margin) return 0;
             if (fe < 0 || s > se) {
                 fe = 6 + 3 * i + j;
                 se = s;
-                le = L * (1.f / len);
+                le = L * inv;
             }
         }
     int axis = fa;
     float s = sa;
-    float3 L = a[fa];
+    float3 L = A.axs(fa);
     if (sb > sa + 1e-5f) {
         axis = 3 + fb;
         s = sb;
-        L = b[fb];
+        L = B.axs(fb);
     }
     if (fe >= 0 && se > s + 1e-4f + 0.05f * fabsf(s)) {
         axis = fe;
@@ -265,27 +292,28 @@ __device__ __forceinline__ int collide_box_box(const CBox& A, const CBox& B, flo
     }
     if (dot3(L, D) < 0.f) L = -L;
     M.n = L;
-    if (axis < 3) {
-        M.np = face_contact(A, axis, L, B, margin, M, clip_verts);
-        return M.np ? 1 : 0;
-    }
     if (axis < 6) {
-        M.np = face_contact(B, axis - 3, -L, A, margin, M, clip_verts);
+        // one clipping routine for both reference boxes
+        const bool ar = axis < 3;
+        const CBox ref = ar ? A : B, inc = ar ? B : A;
+        M.np = face_contact(ref, ar ? axis : axis - 3, ar ? L : -L, inc, margin, M, clip_verts);
         return M.np ? 1 : 0;
     }
     const int ea = (axis - 6) / 3, eb = (axis - 6) % 3;
     float3 pA = A.c, pB = B.c;
+#pragma unroll
     for (int k = 0; k < 3; k++) {
         if (k == ea) continue;
         const float sg = dot3(a[k], L) < 0.f ? -1.f : 1.f;
         pA = pA + a[k] * (sg * A.h[k]);
     }
+#pragma unroll
     for (int m = 0; m < 3; m++) {
         if (m == eb) continue;
         const float sg = dot3(b[m], L) > 0.f ? -1.f : 1.f;
         pB = pB + b[m] * (sg * B.h[m]);
     }
-    const float3 dA = a[ea], dB = b[eb];
+    const float3 dA = A.axs(ea), dB = B.axs(eb);
     const float3 r = pA - pB;
     const float bb = dot3(dA, dB), c = dot3(dA, r), f = dot3(dB, r);
     const float den = 1.f - bb * bb;
@@ -296,8 +324,9 @@ __device__ __forceinline__ int collide_box_box(const CBox& A, const CBox& B, flo
     } else {
         tb = f;
     }
-    ta = fminf(fmaxf(ta, -A.h[ea]), A.h[ea]);
-    tb = fminf(fmaxf(tb, -B.h[eb]), B.h[eb]);
+    const float ha = A.hs(ea), hb = B.hs(eb);
+    ta = fminf(fmaxf(ta, -ha), ha);
+    tb = fminf(fmaxf(tb, -hb), hb);
     const float3 qa = pA + dA * ta, qb = pB + dB * tb;
     M.p[0] = (qa + qb) * 0.5f;
     M.d[0] = s;
@@ -316,25 +345,28 @@ __device__ __forceinline__ void collide_capsule_box(const CBox& b, float px, flo
     const float ez = (fabsf(b.R[6]) * b.h[0] + fabsf(b.R[7]) * b.h[1]) + fabsf(b.R[8]) * b.h[2];
     const float zlo = b.c.z - ez, zhi = b.c.z + ez;
     const float za = fmaxf(z0, zlo), zb = fminf(z1, zhi);
-    float zc[2];
+    float zc0, zc1 = 0.f;
     int nc;
     if (za > zb) {
-        zc[0] = (zhi < z0) ? z0 : z1;
+        zc0 = (zhi < z0) ? z0 : z1;
         nc = 1;
     } else if (zb - za < 1e-3f) {
-        zc[0] = (za + zb) * 0.5f;
+        zc0 = (za + zb) * 0.5f;
         nc = 1;
     } else {
-        zc[0] = za;
-        zc[1] = zb;
+        zc0 = za;
+        zc1 = zb;
         nc = 2;
     }
     float best_d = 0.f;
     float3 best_n = f3(1.f, 0.f, 0.f);
-    for (int i = 0; i < nc; i++) {
-        const float3 S = f3(px, py, zc[i]);
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        if (i >= nc) break;
+        const float3 S = f3(px, py, i == 0 ? zc0 : zc1);
         const float3 rel = S - b.c;
         float loc[3], ql[3];
+#pragma unroll
         for (int k = 0; k < 3; k++) {
             loc[k] = dot3(b.ax(k), rel);
             ql[k] = fminf(fmaxf(loc[k], -b.h[k]), b.h[k]);
@@ -357,8 +389,13 @@ __device__ __forceinline__ void collide_capsule_box(const CBox& b, float px, flo
             nrm = lw > 1e-9f ? w * (1.f / lw) : f3(1.f, 0.f, 0.f);
         }
         if (!(d < margin)) continue;
-        M.p[M.np] = Q;
-        M.d[M.np] = d;
+        if (M.np == 0) {
+            M.p[0] = Q;
+            M.d[0] = d;
+        } else {
+            M.p[1] = Q;
+            M.d[1] = d;
+        }
         if (M.np == 0 || d < best_d) {
             best_d = d;
             best_n = nrm;

@@ -135,14 +135,10 @@ __device__ __forceinline__ void store_state(const WarpMem& W, int n, float* dst,
     }
 }
 
-struct Counters {
-    unsigned long long ev[kNumEvents];
-};
-
 // One substep of the group's environment (on = false: the group only takes part in the
 // warp's collectives).  Returns true on a cap overflow.
 __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, int n_env, bool on, const Pusher& pu,
-                                        int s, const Grp& g, Counters& cnt) {
+                                        int s, const Grp& g) {
     const SimConst& C = a.C;
     const int n = on ? n_env : 0;
     const int done = s < pu.moving ? s : pu.moving;
@@ -167,23 +163,24 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
     const int visits = pgs(W, g, on, C.iters, V, bb_visits);
     integrate(W, n, g, C.dt);
     const int v_all = g.sum(visits), v_bb = g.sum(bb_visits);
-    if (on) {
-        cnt.ev[EV_SUBSTEPS] += 1;
-        cnt.ev[EV_BOX_STEPS] += n;
-        cnt.ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
-        cnt.ev[EV_SAT] += st.sat;
-        cnt.ev[EV_FACE] += st.face;
-        cnt.ev[EV_EDGE] += st.edge;
-        cnt.ev[EV_PLANE] += st.plane;
-        cnt.ev[EV_PUSHER] += st.pusher;
-        cnt.ev[EV_POINTS] += W.scal[4];
-        cnt.ev[EV_MANIFOLDS] += W.scal[3];
-        cnt.ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal[6];
-        cnt.ev[EV_PGS_PTS] += v_all;
-        cnt.ev[EV_CLIP_VERTS] += st.clip_verts;
-        cnt.ev[EV_COLOURS] += W.scal[5];
-        cnt.ev[EV_BB_POINTS] += st.bb_points;
-        cnt.ev[EV_PGS_BB_POINTS] += v_bb;
+    if (on && g.gl == 0) {
+        unsigned long long* ev = W.ev;
+        ev[EV_SUBSTEPS] += 1;
+        ev[EV_BOX_STEPS] += n;
+        ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
+        ev[EV_SAT] += st.sat;
+        ev[EV_FACE] += st.face;
+        ev[EV_EDGE] += st.edge;
+        ev[EV_PLANE] += st.plane;
+        ev[EV_PUSHER] += st.pusher;
+        ev[EV_POINTS] += W.scal[4];
+        ev[EV_MANIFOLDS] += W.scal[3];
+        ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal[6];
+        ev[EV_PGS_PTS] += v_all;
+        ev[EV_CLIP_VERTS] += st.clip_verts;
+        ev[EV_COLOURS] += W.scal[5];
+        ev[EV_BB_POINTS] += st.bb_points;
+        ev[EV_PGS_BB_POINTS] += v_bb;
     }
     __syncwarp();
     return ovf && on;
@@ -204,8 +201,6 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
     int budget = 0;
     long long t_start = 0;
     bool ovf = false, timed_out = false;
-    Counters cnt;
-    for (int k = 0; k < kNumEvents; k++) cnt.ev[k] = 0;
     for (;;) {
         // 1. fetch
         const bool need = e < 0 && !exhausted;
@@ -235,7 +230,8 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
             ovf = false;
             timed_out = false;
             t_start = clock64();
-            for (int k = 0; k < kNumEvents; k++) cnt.ev[k] = 0;
+            if (g.gl == 0)
+                for (int k = 0; k < kNumEvents; k++) W.ev[k] = 0ull;
         }
         const bool active = e >= 0;
         if (!__any_sync(kFull, active || !exhausted)) break;
@@ -260,7 +256,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
                 }
             }
             if (samp) {
-                cnt.ev[EV_SAMPLE_ATTEMPTS] += at < 0 ? C.attempts : at + 1;
+                if (g.gl == 0) W.ev[EV_SAMPLE_ATTEMPTS] += at < 0 ? C.attempts : at + 1;
                 if (at < 0) {
                     pg.noop = 1;
                     pg.flags |= FLAG_NOOP;
@@ -277,7 +273,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
         // 3. one substep
         const bool run = active && !pg.done && pg.s < C.substeps && budget > 0;
         const Pusher pu = make_pusher(C, pg.push, pg.noop != 0);
-        ovf |= substep(a, W, ei.n, run, pu, pg.s, g, cnt);
+        ovf |= substep(a, W, ei.n, run, pu, pg.s, g);
         // bounded run time per environment and launch (the shuffle runs in every lane)
         const bool late = g.bcast((int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
         if (run) {
@@ -298,7 +294,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
             compute_footprints(W, test ? ei.n : 0, g);
             const bool graspable = grasp_check(W, ei.n, ei.target, g, test, C);
             if (endp) {
-                cnt.ev[EV_PUSH_EVALS] += 1;
+                if (g.gl == 0) W.ev[EV_PUSH_EVALS] += 1;
                 if (out) {
                     pg.flags |= FLAG_OUT_OF_WS;
                     pg.done = 1;
@@ -328,7 +324,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
             if (g.gl == 0) {
                 a.prog[e] = pg;
                 unsigned long long* ev = a.events + (size_t)e * kNumEvents;
-                for (int k = 0; k < kNumEvents; k++) ev[k] += cnt.ev[k];
+                for (int k = 0; k < kNumEvents; k++) ev[k] += W.ev[k];
                 a.steps[e] = pg.steps;
                 if (pg.done) {
                     a.cost[e] = pg.cost;

@@ -59,7 +59,7 @@ struct Layout {
     int Mcap;      // manifold capacity (lists, global scratch stride)
     int bytes;     // total bytes per warp
     int o_bv, o_bw, o_bI0, o_bI1, o_con, o_x, o_q, o_h, o_ib, o_R, o_lo, o_hi, o_mask, o_plane, o_pusher,
-        o_pairs, o_mAB, o_mcol, o_order, o_cstart, o_scal;
+        o_pairs, o_mAB, o_mcol, o_order, o_cstart, o_scal, o_ev;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -85,6 +85,8 @@ __host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Mca
     L.o_hi = o; o += 12 * NB;
     L.o_mask = o; o += 4 * NB;
     L.o_scal = o; o += 4 * 16;
+    o = align_up(o, 8);
+    L.o_ev = o; o += 8 * kNumEvents;  // event counters of the running environment (8-byte aligned)
     L.o_mAB = o; o += 2 * Mcap;
     L.o_order = o; o += 2 * Mcap;
     L.o_cstart = o; o += 2 * (kMaxColours + 2);
@@ -106,6 +108,7 @@ struct WarpMem {
     float *x, *q, *h, *ib, *R, *lo, *hi;  // SoA with stride NB (q: 4 rows, R: 9 rows)
     uint32_t* mask;
     int* scal;
+    unsigned long long* ev;  // written by the group's first lane only
     uint16_t *mAB, *order, *cstart, *pairs;
     uint8_t *mcol, *plane, *pusher;
     float4 *con_s, *con_g;
@@ -127,6 +130,7 @@ __device__ __forceinline__ WarpMem bind_mem(const Layout& L, char* base, float4*
     W.hi = (float*)(base + L.o_hi);
     W.mask = (uint32_t*)(base + L.o_mask);
     W.scal = (int*)(base + L.o_scal);
+    W.ev = (unsigned long long*)(base + L.o_ev);
     W.mAB = (uint16_t*)(base + L.o_mAB);
     W.order = (uint16_t*)(base + L.o_order);
     W.cstart = (uint16_t*)(base + L.o_cstart);
@@ -375,7 +379,9 @@ __device__ __forceinline__ int emit_chunk(const WarpMem& W, const Grp& g, const 
         r.f(1) = make_float4(0.f, 0.f, 0.f, __int_as_float(A | (B << 8) | (cm.np << 16)));
         r.f(2) = make_float4(0.f, 0.f, 0.f, 0.f);
         W.mAB[mi] = (uint16_t)(A | (B << 8));
-        for (int k = 0; k < cm.np; k++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (k >= cm.np) break;
             float3 rA, rB;
             if (kind == 1) {
                 rA = f3(0.f, 0.f, 0.f);
@@ -510,7 +516,7 @@ __device__ __forceinline__ void prepare(const WarpMem& W, const Grp& g, bool on,
         if (an2 < amin) k = 2;
         const float3 e = f3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f);
         float3 t1 = cross3(n, e);
-        t1 = t1 * (1.f / norm3(t1));
+        t1 = t1 * rsqrtf(dot3(t1, t1));
         const float3 t2 = cross3(n, t1);
         r.f(1) = make_float4(t1.x, t1.y, t1.z, h1.w);
         r.f(2) = make_float4(t2.x, t2.y, t2.z, 0.f);
@@ -536,9 +542,9 @@ __device__ __forceinline__ void prepare(const WarpMem& W, const Grp& g, bool on,
                     const float3 rn = cross3(rB, dirs[j]);
                     s += imB + dot3(rn, sym_mul(IB0, IB1, rn));
                 }
-                kk[j] = 1.f / s;
+                kk[j] = __fdividef(1.f, s);
             }
-            const float bias = d > 0.f ? -d / C.dt : (C.baumgarte / C.dt) * fmaxf(-d - C.slop, 0.f);
+            const float bias = d > 0.f ? __fdividef(-d, C.dt) : __fdividef(C.baumgarte, C.dt) * fmaxf(-d - C.slop, 0.f);
             r.pt(p, 0) = make_float4(rA.x, rA.y, rA.z, kk[0]);
             r.pt(p, 1) = make_float4(rB.x, rB.y, rB.z, bias);
             r.pt(p, 2) = make_float4(0.f, 0.f, 0.f, kk[1]);
@@ -684,7 +690,7 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
         const float lim = mu * q2.x;
         const float l2 = c1 * c1 + c2 * c2;
         if (l2 > lim * lim) {
-            const float sc = lim / sqrtf(l2);
+            const float sc = lim * rsqrtf(l2);
             c1 *= sc;
             c2 *= sc;
         }
@@ -741,11 +747,11 @@ __device__ __forceinline__ void integrate(const WarpMem& W, int n, const Grp& g,
         const float3 dv = om * q0 + cross3(om, qv);
         const float hd = 0.5f * dt;
         const float a0 = q0 + hd * dw, a1 = q1 + hd * dv.x, a2 = q2 + hd * dv.y, a3 = q3 + hd * dv.z;
-        const float l = sqrtf(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
-        W.q[i] = a0 / l;
-        W.q[NB + i] = a1 / l;
-        W.q[2 * NB + i] = a2 / l;
-        W.q[3 * NB + i] = a3 / l;
+        const float il = rsqrtf(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
+        W.q[i] = a0 * il;
+        W.q[NB + i] = a1 * il;
+        W.q[2 * NB + i] = a2 * il;
+        W.q[3 * NB + i] = a3 * il;
     }
     __syncwarp();
 }
