@@ -87,45 +87,45 @@ struct RolloutArgs {
 // on = false load nothing.
 __device__ __forceinline__ void load_env(const RolloutArgs& a, const WarpMem& W, const EnvIn& ei, bool on,
                                          bool from_scene, const Grp& g) {
-    const int NB = W.NB;
+    const int NB = W.NB();
     const int n = on ? ei.n : 0;
     for (int i = g.gl; i < n; i += g.G) {
         const float* r = ei.rec + kRecFloats * i;
         const float* s = from_scene ? r : a.state + (size_t)(ei.box_off + i) * 13;
-        W.x[i] = s[0];
-        W.x[NB + i] = s[1];
-        W.x[2 * NB + i] = s[2];
-        W.q[i] = s[3];
-        W.q[NB + i] = s[4];
-        W.q[2 * NB + i] = s[5];
-        W.q[3 * NB + i] = s[6];
+        W.x()[i] = s[0];
+        W.x()[NB + i] = s[1];
+        W.x()[2 * NB + i] = s[2];
+        W.q()[i] = s[3];
+        W.q()[NB + i] = s[4];
+        W.q()[2 * NB + i] = s[5];
+        W.q()[3 * NB + i] = s[6];
         const float h0 = r[13], h1 = r[14], h2 = r[15], m = r[16], mu = r[17];
-        W.h[i] = h0;
-        W.h[NB + i] = h1;
-        W.h[2 * NB + i] = h2;
-        W.bv[i] = make_float4(s[7], s[8], s[9], 1.f / m);
-        W.bw[i] = make_float4(s[10], s[11], s[12], mu);
+        W.h()[i] = h0;
+        W.h()[NB + i] = h1;
+        W.h()[2 * NB + i] = h2;
+        W.bv()[i] = make_float4(s[7], s[8], s[9], 1.f / m);
+        W.bw()[i] = make_float4(s[10], s[11], s[12], mu);
         const float hx2 = h0 * h0, hy2 = h1 * h1, hz2 = h2 * h2;
-        W.ib[i] = 1.f / (m / 3.f * (hy2 + hz2));
-        W.ib[NB + i] = 1.f / (m / 3.f * (hx2 + hz2));
-        W.ib[2 * NB + i] = 1.f / (m / 3.f * (hx2 + hy2));
+        W.ib()[i] = 1.f / (m / 3.f * (hy2 + hz2));
+        W.ib()[NB + i] = 1.f / (m / 3.f * (hx2 + hz2));
+        W.ib()[2 * NB + i] = 1.f / (m / 3.f * (hx2 + hy2));
     }
     __syncwarp();
 }
 
 // Copy an environment's state rows to dst (no collective).
 __device__ __forceinline__ void store_state(const WarpMem& W, int n, float* dst, const Grp& g) {
-    const int NB = W.NB;
+    const int NB = W.NB();
     for (int i = g.gl; i < n; i += g.G) {
         float* s = dst + (size_t)i * 13;
-        const float4 v = W.bv[i], w = W.bw[i];
-        s[0] = W.x[i];
-        s[1] = W.x[NB + i];
-        s[2] = W.x[2 * NB + i];
-        s[3] = W.q[i];
-        s[4] = W.q[NB + i];
-        s[5] = W.q[2 * NB + i];
-        s[6] = W.q[3 * NB + i];
+        const float4 v = W.bv()[i], w = W.bw()[i];
+        s[0] = W.x()[i];
+        s[1] = W.x()[NB + i];
+        s[2] = W.x()[2 * NB + i];
+        s[3] = W.q()[i];
+        s[4] = W.q()[NB + i];
+        s[5] = W.q()[2 * NB + i];
+        s[6] = W.q()[3 * NB + i];
         s[7] = v.x;
         s[8] = v.y;
         s[9] = v.z;
@@ -146,17 +146,35 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
     const float Px = pu.sx + pu.dx * travel, Py = pu.sy + pu.dy * travel;
     const float3 V = (pu.active && s < pu.moving) ? f3(pu.dx * C.pspeed, pu.dy * C.pspeed, 0.f) : f3(0.f, 0.f, 0.f);
     for (int i = g.gl; i < n; i += g.G) {
-        float4 v = W.bv[i];
+        float4 v = W.bv()[i];
         v.x += C.gx * C.dt;
         v.y += C.gy * C.dt;
         v.z += C.gz * C.dt;
-        W.bv[i] = v;
+        W.bv()[i] = v;
     }
     frames_and_aabb(W, n, g, C.margin);
     __syncwarp();
     bool ovf = broadphase(W, n, g, C.pair_cap, on && pu.active, Px, Py, C);
-    NarrowStats st{0, 0, 0, 0, 0, 0, 0};
-    ovf |= narrowphase(W, g, on, C, Px, Py, st);
+    {
+        NarrowStats st{0, 0, 0, 0, 0, 0, 0};
+        ovf |= narrowphase(W, g, on, C, Px, Py, st);
+        // count now, so that nothing of the narrowphase stays live through the solve
+        if (on && g.gl == 0) {
+            unsigned long long* ev = W.ev().ptr();
+            ev[EV_SUBSTEPS] += 1;
+            ev[EV_BOX_STEPS] += n;
+            ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
+            ev[EV_SAT] += st.sat;
+            ev[EV_FACE] += st.face;
+            ev[EV_EDGE] += st.edge;
+            ev[EV_PLANE] += st.plane;
+            ev[EV_PUSHER] += st.pusher;
+            ev[EV_POINTS] += W.scal()[4];
+            ev[EV_MANIFOLDS] += W.scal()[3];
+            ev[EV_CLIP_VERTS] += st.clip_verts;
+            ev[EV_BB_POINTS] += st.bb_points;
+        }
+    }
     prepare(W, g, on, C);
     ovf |= colour_manifolds(W, n, g, on);
     int bb_visits = 0;
@@ -164,22 +182,10 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
     integrate(W, n, g, C.dt);
     const int v_all = g.sum(visits), v_bb = g.sum(bb_visits);
     if (on && g.gl == 0) {
-        unsigned long long* ev = W.ev;
-        ev[EV_SUBSTEPS] += 1;
-        ev[EV_BOX_STEPS] += n;
-        ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
-        ev[EV_SAT] += st.sat;
-        ev[EV_FACE] += st.face;
-        ev[EV_EDGE] += st.edge;
-        ev[EV_PLANE] += st.plane;
-        ev[EV_PUSHER] += st.pusher;
-        ev[EV_POINTS] += W.scal[4];
-        ev[EV_MANIFOLDS] += W.scal[3];
-        ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal[6];
+        unsigned long long* ev = W.ev().ptr();
+        ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal()[6];
         ev[EV_PGS_PTS] += v_all;
-        ev[EV_CLIP_VERTS] += st.clip_verts;
-        ev[EV_COLOURS] += W.scal[5];
-        ev[EV_BB_POINTS] += st.bb_points;
+        ev[EV_COLOURS] += W.scal()[5];
         ev[EV_PGS_BB_POINTS] += v_bb;
     }
     __syncwarp();
@@ -231,7 +237,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
             timed_out = false;
             t_start = clock64();
             if (g.gl == 0)
-                for (int k = 0; k < kNumEvents; k++) W.ev[k] = 0ull;
+                for (int k = 0; k < kNumEvents; k++) W.ev()[k] = 0ull;
         }
         const bool active = e >= 0;
         if (!__any_sync(kFull, active || !exhausted)) break;
@@ -256,7 +262,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
                 }
             }
             if (samp) {
-                if (g.gl == 0) W.ev[EV_SAMPLE_ATTEMPTS] += at < 0 ? C.attempts : at + 1;
+                if (g.gl == 0) W.ev()[EV_SAMPLE_ATTEMPTS] += at < 0 ? C.attempts : at + 1;
                 if (at < 0) {
                     pg.noop = 1;
                     pg.flags |= FLAG_NOOP;
@@ -288,13 +294,13 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
             if (endp && pg.k == 1 && a.child_on) store_state(W, ei.n, a.child + (size_t)ei.box_off * 13, g);
             bool out = false;
             for (int i = g.gl; endp && i < ei.n; i += g.G)
-                out = out || fabsf(W.x[i]) > C.table_hx || fabsf(W.x[W.NB + i]) > C.table_hy;
+                out = out || fabsf(W.x()[i]) > C.table_hx || fabsf(W.x()[W.NB() + i]) > C.table_hy;
             out = g.any(out);
             const bool test = endp && !out;
             compute_footprints(W, test ? ei.n : 0, g);
             const bool graspable = grasp_check(W, ei.n, ei.target, g, test, C);
             if (endp) {
-                if (g.gl == 0) W.ev[EV_PUSH_EVALS] += 1;
+                if (g.gl == 0) W.ev()[EV_PUSH_EVALS] += 1;
                 if (out) {
                     pg.flags |= FLAG_OUT_OF_WS;
                     pg.done = 1;
@@ -324,7 +330,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
             if (g.gl == 0) {
                 a.prog[e] = pg;
                 unsigned long long* ev = a.events + (size_t)e * kNumEvents;
-                for (int k = 0; k < kNumEvents; k++) ev[k] += W.ev[k];
+                for (int k = 0; k < kNumEvents; k++) ev[k] += W.ev()[k];
                 a.steps[e] = pg.steps;
                 if (pg.done) {
                     a.cost[e] = pg.cost;
@@ -342,14 +348,13 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
 
 // 128 threads (up to four warps) per block and a register budget for two blocks per SM:
 // the solver keeps its working set in registers without spilling.
-__global__ void __launch_bounds__(128, 2) rollout_kernel(const __grid_constant__ RolloutArgs a) {
-    extern __shared__ __align__(16) char smem[];
+__global__ void __launch_bounds__(128, 3) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const Grp g(a.G, lane);
     const int per_warp = 32 / a.G;
     const int slot = wib * per_warp + (lane / a.G);
     const size_t gslot = (size_t)blockIdx.x * (blockDim.x >> 5) * per_warp + slot;
-    const WarpMem W = bind_mem(a.L, smem + (size_t)slot * a.L.bytes, a.gscratch + gslot * a.scratch_f4_per_warp);
+    const WarpMem W = bind_mem(a.L, (uint32_t)slot * (uint32_t)a.L.bytes, a.gscratch + gslot * a.scratch_f4_per_warp);
     run_slots(a, W, g);
 }
 
@@ -483,21 +488,20 @@ struct EvalArgs {
 };
 
 __global__ void __launch_bounds__(128) eval_kernel(const __grid_constant__ EvalArgs a) {
-    extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * (blockDim.x >> 5);
-    const WarpMem W = bind_mem(a.L, smem + (size_t)wib * a.L.bytes, nullptr);
+    const WarpMem W = bind_mem(a.L, (uint32_t)wib * (uint32_t)a.L.bytes, nullptr);
     const Grp g(32, lane);
-    const int NB = W.NB;
+    const int NB = W.NB();
     for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < a.n_envs; e += nw) {
         const int b0 = a.box_offset[e], n = a.box_offset[e + 1] - b0;
         for (int i = lane; i < n; i += 32) {
             const float* s = a.states + (size_t)(b0 + i) * 13;
             const float* h = a.half + (size_t)(b0 + i) * 3;
-            W.x[i] = s[0]; W.x[NB + i] = s[1]; W.x[2 * NB + i] = s[2];
-            W.q[i] = s[3]; W.q[NB + i] = s[4]; W.q[2 * NB + i] = s[5]; W.q[3 * NB + i] = s[6];
-            W.h[i] = h[0]; W.h[NB + i] = h[1]; W.h[2 * NB + i] = h[2];
-            W.ib[i] = 1.f; W.ib[NB + i] = 1.f; W.ib[2 * NB + i] = 1.f;
+            W.x()[i] = s[0]; W.x()[NB + i] = s[1]; W.x()[2 * NB + i] = s[2];
+            W.q()[i] = s[3]; W.q()[NB + i] = s[4]; W.q()[2 * NB + i] = s[5]; W.q()[3 * NB + i] = s[6];
+            W.h()[i] = h[0]; W.h()[NB + i] = h[1]; W.h()[2 * NB + i] = h[2];
+            W.ib()[i] = 1.f; W.ib()[NB + i] = 1.f; W.ib()[2 * NB + i] = 1.f;
         }
         __syncwarp();
         if (a.mode == 0) {
@@ -506,13 +510,13 @@ __global__ void __launch_bounds__(128) eval_kernel(const __grid_constant__ EvalA
             const bool on = a.pusher_xy != nullptr;
             const float px = on ? a.pusher_xy[2 * e] : 0.f, py = on ? a.pusher_xy[2 * e + 1] : 0.f;
             broadphase(W, n, g, a.C.pair_cap, on, px, py, a.C);
-            const int np = W.scal[0], npl = W.scal[1], npu = W.scal[2];
+            const int np = W.scal()[0], npl = W.scal()[1], npu = W.scal()[2];
             for (int k = lane; k < np; k += 32) {
-                a.out_pairs[((size_t)e * a.C.pair_cap + k) * 2] = W.pairs[k] & 255;
-                a.out_pairs[((size_t)e * a.C.pair_cap + k) * 2 + 1] = W.pairs[k] >> 8;
+                a.out_pairs[((size_t)e * a.C.pair_cap + k) * 2] = W.pairs()[k] & 255;
+                a.out_pairs[((size_t)e * a.C.pair_cap + k) * 2 + 1] = W.pairs()[k] >> 8;
             }
-            for (int k = lane; k < npl; k += 32) a.out_plane[b0 + k] = W.plane[k];
-            for (int k = lane; k < npu; k += 32) a.out_pusher[b0 + k] = W.pusher[k];
+            for (int k = lane; k < npl; k += 32) a.out_plane[b0 + k] = W.plane()[k];
+            for (int k = lane; k < npu; k += 32) a.out_pusher[b0 + k] = W.pusher()[k];
             if (lane == 0) {
                 a.out_n_pairs[e] = np;
                 a.out_n_plane[e] = npl;

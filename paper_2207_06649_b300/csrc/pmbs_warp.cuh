@@ -103,47 +103,62 @@ __host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Mca
 __host__ __device__ inline int scratch_f4_per_warp(int Mcap) { return kConFields * Mcap; }
 
 // Pointers into one warp's shared region and its global scratch.
-struct WarpMem {
-    float4 *bv, *bw, *bI0, *bI1;  // v+invm, w+mu, inv inertia (00 01 02 11), (12 22 . .)
-    float *x, *q, *h, *ib, *R, *lo, *hi;  // SoA with stride NB (q: 4 rows, R: 9 rows)
-    uint32_t* mask;
-    int* scal;
-    unsigned long long* ev;  // written by the group's first lane only
-    uint16_t *mAB, *order, *cstart, *pairs;
-    uint8_t *mcol, *plane, *pusher;
-    float4 *con_s, *con_g;
-    int NB, Ms, Mcap, pairS;
+// The block's dynamic shared memory; every kernel that binds warp regions uses it.
+extern __shared__ __align__(16) unsigned char pmbs_smem[];
+
+// An array in the block's dynamic shared memory held as a 32-bit byte offset: one
+// register per array, and accesses compile to shared-memory loads and stores.
+template <class T>
+struct SArr {
+    uint32_t off;
+    __device__ __forceinline__ T& operator[](int i) const { return reinterpret_cast<T*>(pmbs_smem + off)[i]; }
+    __device__ __forceinline__ T* ptr() const { return reinterpret_cast<T*>(pmbs_smem + off); }
 };
 
-__device__ __forceinline__ WarpMem bind_mem(const Layout& L, char* base, float4* gscratch) {
+// One warp's region: its byte offset in the block's dynamic shared memory, the launch's
+// layout (a kernel parameter, so field offsets are read from the parameter bank instead
+// of being held in registers) and the warp's global contact scratch.
+struct WarpMem {
+    uint32_t base;
+    const Layout* L;
+    float4* con_g;
+    __device__ __forceinline__ SArr<float4> bv() const { return {base + (uint32_t)L->o_bv}; }    // v, 1/m
+    __device__ __forceinline__ SArr<float4> bw() const { return {base + (uint32_t)L->o_bw}; }    // w, mu
+    __device__ __forceinline__ SArr<float4> bI0() const { return {base + (uint32_t)L->o_bI0}; }  // I^-1 00 01 02 11
+    __device__ __forceinline__ SArr<float4> bI1() const { return {base + (uint32_t)L->o_bI1}; }  // I^-1 12 22
+    __device__ __forceinline__ SArr<float> x() const { return {base + (uint32_t)L->o_x}; }  // SoA, stride NB
+    __device__ __forceinline__ SArr<float> q() const { return {base + (uint32_t)L->o_q}; }  // 4 rows
+    __device__ __forceinline__ SArr<float> h() const { return {base + (uint32_t)L->o_h}; }
+    __device__ __forceinline__ SArr<float> ib() const { return {base + (uint32_t)L->o_ib}; }
+    __device__ __forceinline__ SArr<float> R() const { return {base + (uint32_t)L->o_R}; }  // 9 rows
+    __device__ __forceinline__ SArr<float> lo() const { return {base + (uint32_t)L->o_lo}; }
+    __device__ __forceinline__ SArr<float> hi() const { return {base + (uint32_t)L->o_hi}; }
+    __device__ __forceinline__ SArr<uint32_t> mask() const { return {base + (uint32_t)L->o_mask}; }
+    __device__ __forceinline__ SArr<int> scal() const { return {base + (uint32_t)L->o_scal}; }
+    // event counters, written by the group's first lane only
+    __device__ __forceinline__ SArr<unsigned long long> ev() const { return {base + (uint32_t)L->o_ev}; }
+    __device__ __forceinline__ SArr<uint16_t> mAB() const { return {base + (uint32_t)L->o_mAB}; }
+    __device__ __forceinline__ SArr<uint16_t> order() const { return {base + (uint32_t)L->o_order}; }
+    __device__ __forceinline__ SArr<uint16_t> cstart() const { return {base + (uint32_t)L->o_cstart}; }
+    __device__ __forceinline__ SArr<uint16_t> pairs() const { return {base + (uint32_t)L->o_pairs}; }
+    __device__ __forceinline__ SArr<uint8_t> mcol() const { return {base + (uint32_t)L->o_mcol}; }
+    __device__ __forceinline__ SArr<uint8_t> plane() const { return {base + (uint32_t)L->o_plane}; }
+    __device__ __forceinline__ SArr<uint8_t> pusher() const { return {base + (uint32_t)L->o_pusher}; }
+    // contacts: shared memory below Ms, global scratch above
+    __device__ __forceinline__ float4* con_s() const { return reinterpret_cast<float4*>(pmbs_smem + base + L->o_con); }
+    __device__ __forceinline__ int NB() const { return L->NB; }
+    __device__ __forceinline__ int Ms() const { return L->Ms; }
+    __device__ __forceinline__ int Mcap() const { return L->Mcap; }
+    __device__ __forceinline__ int pairS() const { return L->pairS; }
+};
+
+// base: the warp region's byte offset in the block's dynamic shared memory; L must be a
+// kernel parameter.
+__device__ __forceinline__ WarpMem bind_mem(const Layout& L, uint32_t base, float4* gscratch) {
     WarpMem W;
-    W.bv = (float4*)(base + L.o_bv);
-    W.bw = (float4*)(base + L.o_bw);
-    W.bI0 = (float4*)(base + L.o_bI0);
-    W.bI1 = (float4*)(base + L.o_bI1);
-    W.x = (float*)(base + L.o_x);
-    W.q = (float*)(base + L.o_q);
-    W.h = (float*)(base + L.o_h);
-    W.ib = (float*)(base + L.o_ib);
-    W.R = (float*)(base + L.o_R);
-    W.lo = (float*)(base + L.o_lo);
-    W.hi = (float*)(base + L.o_hi);
-    W.mask = (uint32_t*)(base + L.o_mask);
-    W.scal = (int*)(base + L.o_scal);
-    W.ev = (unsigned long long*)(base + L.o_ev);
-    W.mAB = (uint16_t*)(base + L.o_mAB);
-    W.order = (uint16_t*)(base + L.o_order);
-    W.cstart = (uint16_t*)(base + L.o_cstart);
-    W.pairs = (uint16_t*)(base + L.o_pairs);
-    W.mcol = (uint8_t*)(base + L.o_mcol);
-    W.plane = (uint8_t*)(base + L.o_plane);
-    W.pusher = (uint8_t*)(base + L.o_pusher);
-    W.con_s = (float4*)(base + L.o_con);
+    W.base = base;
+    W.L = &L;
     W.con_g = gscratch;
-    W.NB = L.NB;
-    W.Ms = L.Ms;
-    W.Mcap = L.Mcap;
-    W.pairS = L.pairS;
     return W;
 }
 
@@ -157,12 +172,12 @@ struct CRef {
 
 __device__ __forceinline__ CRef cref(const WarpMem& W, int m) {
     CRef r;
-    if (m < W.Ms) {
-        r.p = W.con_s + m;
-        r.stride = W.Ms;
+    if (m < W.Ms()) {
+        r.p = W.con_s() + m;
+        r.stride = W.Ms();
     } else {
         r.p = W.con_g + m;
-        r.stride = W.Mcap;
+        r.stride = W.Mcap();
     }
     return r;
 }
@@ -209,14 +224,14 @@ struct Grp {
 __device__ __forceinline__ int wmax(int v) { return __reduce_max_sync(kFull, v); }
 
 __device__ __forceinline__ CBox load_cbox(const WarpMem& W, int i) {
-    const int NB = W.NB;
+    const int NB = W.NB();
     CBox b;
-    b.c = f3(W.x[i], W.x[NB + i], W.x[2 * NB + i]);
+    b.c = f3(W.x()[i], W.x()[NB + i], W.x()[2 * NB + i]);
 #pragma unroll
-    for (int k = 0; k < 9; k++) b.R[k] = W.R[k * NB + i];
-    b.h[0] = W.h[i];
-    b.h[1] = W.h[NB + i];
-    b.h[2] = W.h[2 * NB + i];
+    for (int k = 0; k < 9; k++) b.R[k] = W.R()[k * NB + i];
+    b.h[0] = W.h()[i];
+    b.h[1] = W.h()[NB + i];
+    b.h[2] = W.h()[2 * NB + i];
     return b;
 }
 
@@ -247,13 +262,13 @@ __device__ __forceinline__ Pusher make_pusher(const SimConst& C, const float* pu
 // Per box: rotation (exact), world inverse inertia, AABB (exact).  n = 0 for a group
 // without work in this phase (every function below accepts that).
 __device__ __forceinline__ void frames_and_aabb(const WarpMem& W, int n, const Grp& g, float margin) {
-    const int NB = W.NB;
+    const int NB = W.NB();
     for (int i = g.gl; i < n; i += g.G) {
         float R[9];
-        quat_to_R_exact(W.q[i], W.q[NB + i], W.q[2 * NB + i], W.q[3 * NB + i], R);
+        quat_to_R_exact(W.q()[i], W.q()[NB + i], W.q()[2 * NB + i], W.q()[3 * NB + i], R);
 #pragma unroll
-        for (int k = 0; k < 9; k++) W.R[k * NB + i] = R[k];
-        const float i0 = W.ib[i], i1 = W.ib[NB + i], i2 = W.ib[2 * NB + i];
+        for (int k = 0; k < 9; k++) W.R()[k * NB + i] = R[k];
+        const float i0 = W.ib()[i], i1 = W.ib()[NB + i], i2 = W.ib()[2 * NB + i];
         // R diag(ib) R^T
         const float I00 = R[0] * i0 * R[0] + R[1] * i1 * R[1] + R[2] * i2 * R[2];
         const float I01 = R[0] * i0 * R[3] + R[1] * i1 * R[4] + R[2] * i2 * R[5];
@@ -261,15 +276,15 @@ __device__ __forceinline__ void frames_and_aabb(const WarpMem& W, int n, const G
         const float I11 = R[3] * i0 * R[3] + R[4] * i1 * R[4] + R[5] * i2 * R[5];
         const float I12 = R[3] * i0 * R[6] + R[4] * i1 * R[7] + R[5] * i2 * R[8];
         const float I22 = R[6] * i0 * R[6] + R[7] * i1 * R[7] + R[8] * i2 * R[8];
-        W.bI0[i] = make_float4(I00, I01, I02, I11);
-        W.bI1[i] = make_float4(I12, I22, 0.f, 0.f);
-        const float h0 = W.h[i], h1 = W.h[NB + i], h2 = W.h[2 * NB + i];
+        W.bI0()[i] = make_float4(I00, I01, I02, I11);
+        W.bI1()[i] = make_float4(I12, I22, 0.f, 0.f);
+        const float h0 = W.h()[i], h1 = W.h()[NB + i], h2 = W.h()[2 * NB + i];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const float e = aabb_half_exact(R + 3 * k, h0, h1, h2);
-            const float c = W.x[k * NB + i];
-            W.lo[k * NB + i] = xs(xs(c, e), margin);
-            W.hi[k * NB + i] = xa(xa(c, e), margin);
+            const float c = W.x()[k * NB + i];
+            W.lo()[k * NB + i] = xs(xs(c, e), margin);
+            W.hi()[k * NB + i] = xa(xa(c, e), margin);
         }
     }
 }
@@ -291,8 +306,8 @@ __device__ __forceinline__ void pair_of_index(int t, int n, int& i, int& j) {
 // and returns true if the pair cap dropped pairs.
 __device__ __forceinline__ bool broadphase(const WarpMem& W, int n, const Grp& g, int pair_cap, bool pusher_on,
                                            float Px, float Py, const SimConst& C) {
-    const int NB = W.NB;
-    const int cap = min(pair_cap, W.pairS);
+    const int NB = W.NB();
+    const int cap = min(pair_cap, W.pairS());
     const int T = n * (n - 1) / 2;
     const int Tw = wmax(T);
     int np = 0;
@@ -303,14 +318,14 @@ __device__ __forceinline__ bool broadphase(const WarpMem& W, int n, const Grp& g
         int i = 0, j = 0;
         if (t < T) {
             pair_of_index(t, n, i, j);
-            ov = W.lo[i] <= W.hi[j] && W.lo[j] <= W.hi[i] && W.lo[NB + i] <= W.hi[NB + j] &&
-                 W.lo[NB + j] <= W.hi[NB + i] && W.lo[2 * NB + i] <= W.hi[2 * NB + j] &&
-                 W.lo[2 * NB + j] <= W.hi[2 * NB + i];
+            ov = W.lo()[i] <= W.hi()[j] && W.lo()[j] <= W.hi()[i] && W.lo()[NB + i] <= W.hi()[NB + j] &&
+                 W.lo()[NB + j] <= W.hi()[NB + i] && W.lo()[2 * NB + i] <= W.hi()[2 * NB + j] &&
+                 W.lo()[2 * NB + j] <= W.hi()[2 * NB + i];
         }
         const unsigned m = g.ballot(ov);
         const int pos = np + __popc(m & g.lt());
         if (ov) {
-            if (pos < cap) W.pairs[pos] = (uint16_t)(i | (j << 8));
+            if (pos < cap) W.pairs()[pos] = (uint16_t)(i | (j << 8));
             else overflow = true;
         }
         np += __popc(m);
@@ -323,22 +338,22 @@ __device__ __forceinline__ bool broadphase(const WarpMem& W, int n, const Grp& g
     const int nw = wmax(n);
     for (int b = 0; b < nw; b += g.G) {
         const int i = b + g.gl;
-        const bool pl = i < n && W.lo[2 * NB + i] < 0.f;
+        const bool pl = i < n && W.lo()[2 * NB + i] < 0.f;
         bool pu = false;
         if (pusher_on && i < n)
-            pu = W.lo[i] <= phi0 && plo0 <= W.hi[i] && W.lo[NB + i] <= phi1 && plo1 <= W.hi[NB + i] &&
-                 W.lo[2 * NB + i] <= phi2 && plo2 <= W.hi[2 * NB + i];
+            pu = W.lo()[i] <= phi0 && plo0 <= W.hi()[i] && W.lo()[NB + i] <= phi1 && plo1 <= W.hi()[NB + i] &&
+                 W.lo()[2 * NB + i] <= phi2 && plo2 <= W.hi()[2 * NB + i];
         const unsigned mp = g.ballot(pl);
         const unsigned mu = g.ballot(pu);
-        if (pl) W.plane[npl + __popc(mp & g.lt())] = (uint8_t)i;
-        if (pu) W.pusher[npu + __popc(mu & g.lt())] = (uint8_t)i;
+        if (pl) W.plane()[npl + __popc(mp & g.lt())] = (uint8_t)i;
+        if (pu) W.pusher()[npu + __popc(mu & g.lt())] = (uint8_t)i;
         npl += __popc(mp);
         npu += __popc(mu);
     }
     if (g.gl == 0) {
-        W.scal[0] = min(np, cap);
-        W.scal[1] = npl;
-        W.scal[2] = npu;
+        W.scal()[0] = min(np, cap);
+        W.scal()[1] = npl;
+        W.scal()[2] = npu;
     }
     __syncwarp();
     return overflow;
@@ -378,7 +393,7 @@ __device__ __forceinline__ int emit_chunk(const WarpMem& W, const Grp& g, const 
         r.f(0) = make_float4(cm.n.x, cm.n.y, cm.n.z, mu);
         r.f(1) = make_float4(0.f, 0.f, 0.f, __int_as_float(A | (B << 8) | (cm.np << 16)));
         r.f(2) = make_float4(0.f, 0.f, 0.f, 0.f);
-        W.mAB[mi] = (uint16_t)(A | (B << 8));
+        W.mAB()[mi] = (uint16_t)(A | (B << 8));
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (k >= cm.np) break;
@@ -414,7 +429,7 @@ __device__ __forceinline__ int emit_chunk(const WarpMem& W, const Grp& g, const 
 // plane manifolds to scal[8]; returns true on overflow.
 __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool on, const SimConst& C, float Px,
                                             float Py, NarrowStats& st) {
-    const int npairs = on ? W.scal[0] : 0, nplane = on ? W.scal[1] : 0, npush = on ? W.scal[2] : 0;
+    const int npairs = on ? W.scal()[0] : 0, nplane = on ? W.scal()[1] : 0, npush = on ? W.scal()[2] : 0;
     Emit E{0, 0, false};
     int sat = 0, face = 0, edge = 0, clipv = 0;
     const int pw = wmax(npairs);
@@ -426,7 +441,7 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
         float mu = 0.f;
         float3 cA = f3(0.f, 0.f, 0.f), cB = cA;
         if (c < npairs && !E.stop) {
-            const int pr = W.pairs[c];
+            const int pr = W.pairs()[c];
             A = pr & 255;
             B = pr >> 8;
             const CBox a = load_cbox(W, A), b = load_cbox(W, B);
@@ -434,7 +449,7 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
             const int kd = collide_box_box(a, b, C.margin, cm, clipv);
             if (kd == 1) face++;
             if (kd == 2) edge++;
-            mu = sqrtf(W.bw[A].w * W.bw[B].w);
+            mu = sqrtf(W.bw()[A].w * W.bw()[B].w);
             cA = a.c;
             cB = b.c;
         }
@@ -450,10 +465,10 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
         float mu = 0.f;
         float3 cB = f3(0.f, 0.f, 0.f);
         if (c < nplane && !E.stop) {
-            B = W.plane[c];
+            B = W.plane()[c];
             const CBox b = load_cbox(W, B);
             collide_box_plane(b, C.margin, cm);
-            mu = sqrtf(W.bw[B].w * C.table_mu);
+            mu = sqrtf(W.bw()[B].w * C.table_mu);
             cB = b.c;
         }
         emit_chunk(W, g, C, E, cm, kPlane, B, mu, 1, f3(0.f, 0.f, 0.f), cB);
@@ -468,10 +483,10 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
         float mu = 0.f;
         float3 cA = f3(0.f, 0.f, 0.f);
         if (c < npush && !E.stop) {
-            A = W.pusher[c];
+            A = W.pusher()[c];
             const CBox a = load_cbox(W, A);
             collide_capsule_box(a, Px, Py, C.pz0, C.pz1, C.pr, C.margin, cm);
-            mu = sqrtf(W.bw[A].w * C.pusher_mu);
+            mu = sqrtf(W.bw()[A].w * C.pusher_mu);
             cA = a.c;
         }
         emit_chunk(W, g, C, E, cm, A, kPusher, mu, 2, cA, f3(0.f, 0.f, 0.f));
@@ -483,10 +498,10 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
     st.plane += nplane;
     st.pusher += npush;
     if (g.gl == 0 && on) {
-        W.scal[3] = E.M;
-        W.scal[4] = E.P;
-        W.scal[7] = Mbb;
-        W.scal[8] = Mpl;
+        W.scal()[3] = E.M;
+        W.scal()[4] = E.P;
+        W.scal()[7] = Mbb;
+        W.scal()[8] = Mpl;
     }
     __syncwarp();
     return E.stop;
@@ -502,7 +517,7 @@ __device__ __forceinline__ float3 sym_mul(float4 I0, float4 I1, float3 v) {
 // n, t1, t2; target normal velocity (speculative -d/dt when separated, Baumgarte
 // beta/dt * max(-d - slop, 0) when penetrating); impulses start at zero.
 __device__ __forceinline__ void prepare(const WarpMem& W, const Grp& g, bool on, const SimConst& C) {
-    const int M = on ? W.scal[3] : 0;
+    const int M = on ? W.scal()[3] : 0;
     for (int m = g.gl; m < M; m += g.G) {
         const CRef r = cref(W, m);
         const float4 h0 = r.f(0), h1 = r.f(1);
@@ -523,8 +538,8 @@ __device__ __forceinline__ void prepare(const WarpMem& W, const Grp& g, bool on,
         const bool dA = A < kPusher, dB = B < kPusher;
         float4 IA0 = make_float4(0.f, 0.f, 0.f, 0.f), IA1 = IA0, IB0 = IA0, IB1 = IA0;
         float imA = 0.f, imB = 0.f;
-        if (dA) { IA0 = W.bI0[A]; IA1 = W.bI1[A]; imA = W.bv[A].w; }
-        if (dB) { IB0 = W.bI0[B]; IB1 = W.bI1[B]; imB = W.bv[B].w; }
+        if (dA) { IA0 = W.bI0()[A]; IA1 = W.bI1()[A]; imA = W.bv()[A].w; }
+        if (dB) { IB0 = W.bI0()[B]; IB1 = W.bI1()[B]; imB = W.bv()[B].w; }
         for (int p = 0; p < np; p++) {
             const float4 q0 = r.pt(p, 0), q1 = r.pt(p, 1), q3 = r.pt(p, 3);
             const float3 rA = f3(q0.x, q0.y, q0.z), rB = f3(q1.x, q1.y, q1.z);
@@ -564,25 +579,25 @@ __device__ __forceinline__ void prepare(const WarpMem& W, const Grp& g, bool on,
 // manifold ids by colour.  Returns true on colour overflow (manifold dropped).  Writes the
 // colour count to scal[5] and the number of coloured manifolds to scal[6].
 __device__ __forceinline__ bool colour_manifolds(const WarpMem& W, int n, const Grp& g, bool on) {
-    const int M = on ? W.scal[3] : 0, Mbb = on ? W.scal[7] : 0, Mpl = on ? W.scal[8] : 0;
-    for (int i = g.gl; i < n; i += g.G) W.mask[i] = 0u;
+    const int M = on ? W.scal()[3] : 0, Mbb = on ? W.scal()[7] : 0, Mpl = on ? W.scal()[8] : 0;
+    for (int i = g.gl; i < n; i += g.G) W.mask()[i] = 0u;
     __syncwarp();
     bool overflow = false;
     int cmax = -1;
     if (g.gl == 0) {
         for (int m = 0; m < Mbb; m++) {
-            const int ab = W.mAB[m];
+            const int ab = W.mAB()[m];
             const int A = ab & 255, B = ab >> 8;
-            const uint32_t u = W.mask[A] | W.mask[B];
+            const uint32_t u = W.mask()[A] | W.mask()[B];
             if (u == 0xffffffffu) {
-                W.mcol[m] = 255;
+                W.mcol()[m] = 255;
                 overflow = true;
                 continue;
             }
             const int c = __ffs(~u) - 1;
-            W.mcol[m] = (uint8_t)c;
-            W.mask[A] = W.mask[A] | (1u << c);
-            W.mask[B] = W.mask[B] | (1u << c);
+            W.mcol()[m] = (uint8_t)c;
+            W.mask()[A] = W.mask()[A] | (1u << c);
+            W.mask()[B] = W.mask()[B] | (1u << c);
             cmax = max(cmax, c);
         }
     }
@@ -591,17 +606,17 @@ __device__ __forceinline__ bool colour_manifolds(const WarpMem& W, int n, const 
     for (int grp = 0; grp < 2; grp++) {
         const int lo = grp == 0 ? Mbb : Mbb + Mpl, hi = grp == 0 ? Mbb + Mpl : M;
         for (int m = lo + g.gl; m < hi; m += g.G) {
-            const int ab = W.mAB[m];
+            const int ab = W.mAB()[m];
             const int box = grp == 0 ? (ab >> 8) : (ab & 255);
-            const uint32_t u = W.mask[box];
+            const uint32_t u = W.mask()[box];
             if (u == 0xffffffffu) {
-                W.mcol[m] = 255;
+                W.mcol()[m] = 255;
                 overflow = true;
                 continue;
             }
             const int c = __ffs(~u) - 1;
-            W.mcol[m] = (uint8_t)c;
-            W.mask[box] = u | (1u << c);
+            W.mcol()[m] = (uint8_t)c;
+            W.mask()[box] = u | (1u << c);
             cmax = max(cmax, c);
         }
         __syncwarp();
@@ -610,19 +625,19 @@ __device__ __forceinline__ bool colour_manifolds(const WarpMem& W, int n, const 
     const int cw = wmax(ncol), mw = wmax(M);
     int pos = 0;
     for (int c = 0; c < cw; c++) {
-        if (g.gl == 0 && c < ncol) W.cstart[c] = (uint16_t)pos;
+        if (g.gl == 0 && c < ncol) W.cstart()[c] = (uint16_t)pos;
         for (int base = 0; base < mw; base += g.G) {
             const int m = base + g.gl;
-            const bool is = c < ncol && m < M && W.mcol[m] == c;
+            const bool is = c < ncol && m < M && W.mcol()[m] == c;
             const unsigned bal = g.ballot(is);
-            if (is) W.order[pos + __popc(bal & g.lt())] = (uint16_t)m;
+            if (is) W.order()[pos + __popc(bal & g.lt())] = (uint16_t)m;
             pos += __popc(bal);
         }
     }
     if (g.gl == 0 && on) {
-        W.cstart[ncol] = (uint16_t)pos;
-        W.scal[5] = ncol;
-        W.scal[6] = pos;
+        W.cstart()[ncol] = (uint16_t)pos;
+        W.scal()[5] = ncol;
+        W.scal()[6] = pos;
     }
     __syncwarp();
     return g.any(overflow);
@@ -643,22 +658,22 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
     float imA = 0.f, imB = 0.f, muA = 0.f, muB = 0.f;
     float4 IA0 = make_float4(0.f, 0.f, 0.f, 0.f), IA1 = IA0, IB0 = IA0, IB1 = IA0;
     if (dA) {
-        const float4 a = W.bv[A], b = W.bw[A];
+        const float4 a = W.bv()[A], b = W.bw()[A];
         vA = f3(a.x, a.y, a.z);
         imA = a.w;
         wA = f3(b.x, b.y, b.z);
         muA = b.w;
-        IA0 = W.bI0[A];
-        IA1 = W.bI1[A];
+        IA0 = W.bI0()[A];
+        IA1 = W.bI1()[A];
     }
     if (dB) {
-        const float4 a = W.bv[B], b = W.bw[B];
+        const float4 a = W.bv()[B], b = W.bw()[B];
         vB = f3(a.x, a.y, a.z);
         imB = a.w;
         wB = f3(b.x, b.y, b.z);
         muB = b.w;
-        IB0 = W.bI0[B];
-        IB1 = W.bI1[B];
+        IB0 = W.bI0()[B];
+        IB1 = W.bI1()[B];
     } else if (B == kPusher) {
         vB = pusherV;
     }
@@ -705,12 +720,12 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
         wB = wB + sym_mul(IB0, IB1, cross3(rB, P));
     }
     if (dA) {
-        W.bv[A] = make_float4(vA.x, vA.y, vA.z, imA);
-        W.bw[A] = make_float4(wA.x, wA.y, wA.z, muA);
+        W.bv()[A] = make_float4(vA.x, vA.y, vA.z, imA);
+        W.bw()[A] = make_float4(wA.x, wA.y, wA.z, muA);
     }
     if (dB) {
-        W.bv[B] = make_float4(vB.x, vB.y, vB.z, imB);
-        W.bw[B] = make_float4(wB.x, wB.y, wB.z, muB);
+        W.bv()[B] = make_float4(vB.x, vB.y, vB.z, imB);
+        W.bw()[B] = make_float4(wB.x, wB.y, wB.z, muB);
     }
     if (dA && dB) bb_pts += np;
     return np;
@@ -720,13 +735,13 @@ __device__ __forceinline__ int solve_manifold(const WarpMem& W, int m, float3 pu
 // in bb_visits those of manifolds between two dynamic bodies.
 __device__ __forceinline__ int pgs(const WarpMem& W, const Grp& g, bool on, int iters, float3 pusherV,
                                    int& bb_visits) {
-    const int ncol = on ? W.scal[5] : 0;
+    const int ncol = on ? W.scal()[5] : 0;
     const int cw = wmax(ncol);
     int visits = 0;
     for (int it = 0; it < iters; it++) {
         for (int c = 0; c < cw; c++) {
-            const int a = c < ncol ? (int)W.cstart[c] : 0, b = c < ncol ? (int)W.cstart[c + 1] : 0;
-            for (int k = a + g.gl; k < b; k += g.G) visits += solve_manifold(W, W.order[k], pusherV, bb_visits);
+            const int a = c < ncol ? (int)W.cstart()[c] : 0, b = c < ncol ? (int)W.cstart()[c + 1] : 0;
+            for (int k = a + g.gl; k < b; k += g.G) visits += solve_manifold(W, W.order()[k], pusherV, bb_visits);
             __syncwarp();
         }
     }
@@ -735,23 +750,23 @@ __device__ __forceinline__ int pgs(const WarpMem& W, const Grp& g, bool on, int 
 
 // ------------------------------------------------------------------ integration
 __device__ __forceinline__ void integrate(const WarpMem& W, int n, const Grp& g, float dt) {
-    const int NB = W.NB;
+    const int NB = W.NB();
     for (int i = g.gl; i < n; i += g.G) {
-        const float4 v = W.bv[i], w = W.bw[i];
-        W.x[i] += v.x * dt;
-        W.x[NB + i] += v.y * dt;
-        W.x[2 * NB + i] += v.z * dt;
-        const float q0 = W.q[i], q1 = W.q[NB + i], q2 = W.q[2 * NB + i], q3 = W.q[3 * NB + i];
+        const float4 v = W.bv()[i], w = W.bw()[i];
+        W.x()[i] += v.x * dt;
+        W.x()[NB + i] += v.y * dt;
+        W.x()[2 * NB + i] += v.z * dt;
+        const float q0 = W.q()[i], q1 = W.q()[NB + i], q2 = W.q()[2 * NB + i], q3 = W.q()[3 * NB + i];
         const float3 om = f3(w.x, w.y, w.z), qv = f3(q1, q2, q3);
         const float dw = -dot3(om, qv);
         const float3 dv = om * q0 + cross3(om, qv);
         const float hd = 0.5f * dt;
         const float a0 = q0 + hd * dw, a1 = q1 + hd * dv.x, a2 = q2 + hd * dv.y, a3 = q3 + hd * dv.z;
         const float il = rsqrtf(a0 * a0 + a1 * a1 + a2 * a2 + a3 * a3);
-        W.q[i] = a0 * il;
-        W.q[NB + i] = a1 * il;
-        W.q[2 * NB + i] = a2 * il;
-        W.q[3 * NB + i] = a3 * il;
+        W.q()[i] = a0 * il;
+        W.q()[NB + i] = a1 * il;
+        W.q()[2 * NB + i] = a2 * il;
+        W.q()[3 * NB + i] = a3 * il;
     }
     __syncwarp();
 }
@@ -759,12 +774,12 @@ __device__ __forceinline__ void integrate(const WarpMem& W, int n, const Grp& g,
 // ------------------------------------------------------------------ footprints & tests
 // Footprints of every box at the current state into the R area (8 floats per box).
 __device__ __forceinline__ void compute_footprints(const WarpMem& W, int n, const Grp& g) {
-    const int NB = W.NB;
+    const int NB = W.NB();
     for (int i = g.gl; i < n; i += g.G) {
         float R[9];
-        quat_to_R_exact(W.q[i], W.q[NB + i], W.q[2 * NB + i], W.q[3 * NB + i], R);
-        const Foot f = footprint_exact(W.x[i], W.x[NB + i], R, W.h[i], W.h[NB + i], W.h[2 * NB + i]);
-        float* o = W.R;
+        quat_to_R_exact(W.q()[i], W.q()[NB + i], W.q()[2 * NB + i], W.q()[3 * NB + i], R);
+        const Foot f = footprint_exact(W.x()[i], W.x()[NB + i], R, W.h()[i], W.h()[NB + i], W.h()[2 * NB + i]);
+        float* o = W.R().ptr();
         o[0 * NB + i] = f.cx;
         o[1 * NB + i] = f.cy;
         o[2 * NB + i] = f.ux;
@@ -778,8 +793,8 @@ __device__ __forceinline__ void compute_footprints(const WarpMem& W, int n, cons
 }
 
 __device__ __forceinline__ Foot load_foot(const WarpMem& W, int i) {
-    const int NB = W.NB;
-    const float* o = W.R;
+    const int NB = W.NB();
+    const float* o = W.R().ptr();
     Foot f;
     f.cx = o[i];
     f.cy = o[NB + i];
