@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default launch shape")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="served-load run length (0 = skip)")
     ap.add_argument("--plan-seeds", type=int, default=1, help="planning episodes per method (0 = skip)")
     ap.add_argument("--arena-gb", type=float, default=8.0, help="device arena of the timed engine")
@@ -273,6 +274,11 @@ def run_ours(args):
         eng.step(b, 0)
         return b
 
+    # launch shape picked by the library's autotuner on this workload (untimed)
+    tuned = None
+    if not args.no_autotune:
+        tuned = eng.autotune(ids, pushes, args.depth, seeds, substeps=240)
+
     # warm-up (untimed); the first batch also gives the per-step work counts
     batches = []
     for w in range(max(args.warmup, 1)):
@@ -380,7 +386,8 @@ def run_ours(args):
                    "substeps_per_push": 240, "pgs_iters": 10, "env_steps_per_step": env_steps,
                    "box_steps_per_s": value * float(boxes.mean()),
                    "l2": "flushed before every step (256 MB device write)",
-                   "parallelism": f"one environment per warp, persistent launch; {ws} GPU(s), weak scaling"},
+                   "parallelism": f"one environment per warp, persistent launch; {ws} GPU(s), weak scaling",
+                   "launch_shape": tuned if tuned is not None else "default"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "rollout_kernel", "kernel_ms": kernel_s * 1e3,
