@@ -36,8 +36,9 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": "b966a75c22c64006", "bytes_per_launch": 43674602,
-           "note": "ncu dram bytes of a 1024-env launch scaled by env-steps to the 4096-env launch"}
+TRAFFIC = {"source_sha": "445e737255b3314f", "bytes_per_launch": 19454090,
+           "note": "ncu dram bytes (read 3.315 MB + write 1.558 MB) of a 1024-env launch in the "
+                   "32,2,0 launch shape, scaled by env-steps (371,760 -> 1,484,160) to the 4096-env launch"}
 
 
 def kernel_source_sha():
@@ -60,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch shape")
+    ap.add_argument("--shape", default=None,
+                    help="fixed launch shape 'lanes,warps_per_block,smem_manifolds' instead of autotuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="served-load run length (0 = skip)")
     ap.add_argument("--plan-seeds", type=int, default=1, help="planning episodes per method (0 = skip)")
     ap.add_argument("--arena-gb", type=float, default=8.0, help="device arena of the timed engine")
@@ -276,7 +279,11 @@ def run_ours(args):
 
     # launch shape picked by the library's autotuner on this workload (untimed)
     tuned = None
-    if not args.no_autotune:
+    if args.shape:
+        g_, w_, m_ = (int(x) for x in args.shape.split(","))
+        eng.set_launch_shape(g_, w_, -1, m_)
+        tuned = {"lanes_per_env": g_, "warps_per_block": w_, "smem_manifolds": m_, "fixed": True}
+    elif not args.no_autotune:
         tuned = eng.autotune(ids, pushes, args.depth, seeds, substeps=240)
 
     # warm-up (untimed); the first batch also gives the per-step work counts
