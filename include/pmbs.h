@@ -107,7 +107,10 @@ typedef struct {
                                    stops after its current substep, keeps its progress,
                                    and pmbs_step / pmbs_query_cost report PMBS_E_TIMEOUT;
                                    the next pmbs_step resumes it */
-    float max_initial_penetration; /* 1e-3 m: scenes with deeper box-box overlap are refused */
+    float max_initial_penetration; /* 5e-3 m: scenes with deeper box-box overlap are refused
+                                      (states the solver produces stay well inside it: it
+                                      removes overlap beyond the 0.5 mm slop at 20 % per
+                                      substep, and planners reload them as scenes) */
 } pmbs_config;
 
 /* Fill *cfg with the defaults listed above.  Never fails. */
