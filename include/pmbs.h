@@ -107,10 +107,9 @@ typedef struct {
                                    stops after its current substep, keeps its progress,
                                    and pmbs_step / pmbs_query_cost report PMBS_E_TIMEOUT;
                                    the next pmbs_step resumes it */
-    float max_initial_penetration; /* 5e-3 m: scenes with deeper box-box overlap are refused
-                                      (states the solver produces stay well inside it: it
-                                      removes overlap beyond the 0.5 mm slop at 20 % per
-                                      substep, and planners reload them as scenes) */
+    float max_initial_penetration; /* 1e-3 m: scenes with deeper box-box overlap are refused
+                                      (child states registered by pmbs_query_cost are the
+                                      engine's own output and are not re-checked) */
 } pmbs_config;
 
 /* Fill *cfg with the defaults listed above.  Never fails. */

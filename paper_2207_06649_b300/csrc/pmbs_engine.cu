@@ -1264,7 +1264,7 @@ void pmbs_default_config(pmbs_config* c) {
     c->smem_points = -1;
     c->smem_manifolds = -1;
     c->watchdog_ms = 10000.f;
-    c->max_initial_penetration = 5e-3f;
+    c->max_initial_penetration = 1e-3f;
 }
 
 pmbs_status pmbs_create(const pmbs_config* cfg, void* cuda_stream, pmbs_ctx** out) {

@@ -287,24 +287,30 @@ def run_episode(backend, scene_state, half, target, make_planner, max_actions=16
     actions to retrieval (pushes + the grasp), planning seconds per push and success."""
     state = np.asarray(scene_state, np.float32)
     pushes, plan_s = 0, []
+    h = None  # the scene's handle; after a push, the state the engine registered for it
     while pushes < max_actions:
         if backend.graspable(state, half, target):
+            if h is not None:
+                backend.release([h])
             return dict(actions=pushes + 1, plan_s=plan_s, success=True)
-        h = backend.load_state(state, half, target)
+        if h is None:
+            h = backend.load_state(state, half, target)
         planner = make_planner()
         action, info = planner.plan(h, state)
         plan_s.append(info.seconds)
         if action is None:
-            backend.release([h])
             break
         res = backend.rollout(np.array([h], np.int32), action[None], 1, np.zeros(1, np.uint64))
         backend.release([h])
+        h = None
         if res["flags"][0] & 6:
             backend.release(list(res["child_handles"]))
             break
         state = res["child_states"][0]
-        backend.release(list(res["child_handles"]))
+        h = int(res["child_handles"][0])
         pushes += 1
+    if h is not None:
+        backend.release([h])
     return dict(actions=max_actions + 1, plan_s=plan_s, success=False)
 
 

@@ -147,19 +147,19 @@ def test_scene_validation_refuses_penetration_and_size():
     eng = pm.Engine(device=0, mem_budget_bytes=256 << 20, max_boxes_per_env=8)
     sv = pm.Server(eng, n_streams=1, max_inflight=1)   # only for its arena-usage figure
     base = sv.stats()["arena_used_bytes"]
-    # 2 mm overlap (below the 5 mm limit), exact face contact, a box resting on another
-    for sc in (_pair_scene(0.06 - 2e-3), _pair_scene(0.06), _pair_scene(0.0, dz=0.06)):
+    # 0.5 mm overlap (below the 1 mm limit), exact face contact, a box resting on another
+    for sc in (_pair_scene(0.06 - 5e-4), _pair_scene(0.06), _pair_scene(0.0, dz=0.06)):
         ids = eng.load(sc)
         eng.free_scenes(ids)
     assert sv.stats()["arena_used_bytes"] == base
-    # 8 mm overlap along x; a 45-degree box whose corner reaches 10 mm into its neighbour
-    corner = 0.03 + 0.03 * np.sqrt(2) - 0.010
-    for sc in (_pair_scene(0.06 - 8e-3), _pair_scene(corner, yaw=np.pi / 4)):
+    # 2 mm overlap along x; a 45-degree box whose corner reaches 5 mm into its neighbour
+    corner = 0.03 + 0.03 * np.sqrt(2) - 0.005
+    for sc in (_pair_scene(0.06 - 2e-3), _pair_scene(corner, yaw=np.pi / 4)):
         with pytest.raises(pm.PmbsError) as ei:
             eng.load(sc)
         assert ei.value.status == pm.PMBS_E_INVALID and "penetration" in str(ei.value)
     # the penetration test looks at every scene of a call: one bad scene refuses the call
-    good, bad = _pair_scene(0.2), _pair_scene(0.04)
+    good, bad = _pair_scene(0.2), _pair_scene(0.05)
     with pytest.raises(pm.PmbsError):
         eng.load(_sg().concat([good, good, bad]))
     # more boxes than the context holds
@@ -184,9 +184,9 @@ def test_penetration_limit_is_configurable():
     with pytest.raises(pm.PmbsError):
         eng.load(_pair_scene(0.06 - 2e-2))
     eng.close()
-    eng = pm.Engine(device=0, mem_budget_bytes=64 << 20, max_initial_penetration=1e-3)
+    eng = pm.Engine(device=0, mem_budget_bytes=64 << 20, max_initial_penetration=1e-4)
     with pytest.raises(pm.PmbsError):
-        eng.load(_pair_scene(0.06 - 2e-3))
+        eng.load(_pair_scene(0.06 - 5e-4))
     eng.close()
 
 
