@@ -74,6 +74,9 @@ def lib():
         L.oracle_grasp.argtypes = [P(Params), C.c_int, C.c_int, vp, vp, C.c_int]
         L.oracle_sample_push.argtypes = [P(Params), C.c_int, C.c_int, vp, vp, C.c_uint64, C.c_int, vp]
         L.oracle_start_blocked.argtypes = [P(Params), C.c_int, C.c_int, vp, vp, C.c_float, C.c_float]
+        L.oracle_heightmap.argtypes = [C.c_int, C.c_int, vp, vp, C.c_int, C.c_int, C.c_double, C.c_double,
+                                       C.c_double, vp]
+        L.oracle_heightmap.restype = None
         L.oracle_footprints.argtypes = [C.c_int, C.c_int, vp, vp, vp]
         _lib = L
     return _lib
@@ -227,6 +230,19 @@ def start_blocked(state13, half, sx, sy, f32=True, prm: Params | None = None) ->
     st, half = _f32(state13), _f32(half)
     return bool(lib().oracle_start_blocked(C.byref(prm), 1 if f32 else 0, st.shape[0], _ptr(st),
                                            _ptr(half), C.c_float(sx), C.c_float(sy)))
+
+
+# Workspace grid of Sec. V-A: 0.288 m x 0.288 m centred on the table, 144 x 144 cells.
+HM_CELLS, HM_CELL, HM_X0 = 144, 0.002, -0.144
+
+
+def heightmap(state13, half, f32=True, cells=HM_CELLS, cell=HM_CELL, x0=HM_X0, y0=HM_X0):
+    """Top-down heightmap [rows y][cols x] of one state (binary32 twin when f32)."""
+    st, half = _f32(state13), _f32(half)
+    out = np.zeros((cells, cells), np.float32)
+    lib().oracle_heightmap(1 if f32 else 0, st.shape[0], _ptr(st), _ptr(half), cells, cells, x0, y0, cell,
+                           _ptr(out))
+    return out
 
 
 def footprints(state13, half, f32=True):

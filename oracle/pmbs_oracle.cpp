@@ -297,6 +297,53 @@ int sample_push(int n, const T* x, const T* q, const T* h, uint64_t seed, int k,
     return -1;
 }
 
+// Top-down heightmap of a state (Sec. V-A: the 0.288 m x 0.288 m workspace seen from
+// above by an orthographic camera as a 144 x 144 grid; that depth image is what the grasp
+// classifier of Sec. IV-B reads).  Cell (i, j) (column i along x, row j along y) takes
+// the height of the highest box surface above its centre x_i = x0 + (i + 1/2) cell,
+// y_j = y0 + (j + 1/2) cell, or 0 where the table shows.  For a box with centre c,
+// rotation R and half extents h, the vertical line through (x, y) written in the box
+// frame is a + b s (s = z - c_z) with a_k = R_0k (x - c_x) + R_1k (y - c_y) and
+// b_k = R_2k; it is inside the box while |a_k + b_k s| <= h_k for every k, i.e. for s
+// in the intersection of [(-h_k - a_k) / b_k, (h_k - a_k) / b_k] (ends swapped when
+// b_k < 0; when b_k = 0 the constraint holds for every s if |a_k| <= h_k and for none
+// otherwise).  A non-empty intersection [s_lo, s_hi] puts the box's top over the cell at
+// c_z + s_hi.  Every operation is written in its evaluation order (binary32 twin).
+template <typename T>
+void heightmap(int n, const T* x, const T* q, const T* h, int W, int H, T x0, T y0, T cell, T* out) {
+    std::vector<T> R(9 * n);
+    for (int b = 0; b < n; b++) quat_to_R(q + 4 * b, &R[9 * b]);
+    for (int j = 0; j < H; j++)
+        for (int i = 0; i < W; i++) {
+            const T xc = x0 + ((T)i + T(0.5)) * cell;
+            const T yc = y0 + ((T)j + T(0.5)) * cell;
+            T top = T(0);
+            for (int b = 0; b < n; b++) {
+                const T* Rb = &R[9 * b];
+                const T dx = xc - x[3 * b], dy = yc - x[3 * b + 1];
+                T s_lo = -INFINITY, s_hi = INFINITY;
+                bool hit = true;
+                for (int k = 0; k < 3 && hit; k++) {
+                    const T a = Rb[k] * dx + Rb[3 + k] * dy;
+                    const T bk = Rb[6 + k];
+                    if (bk == T(0)) {
+                        if (!(std::fabs(a) <= h[3 * b + k])) hit = false;
+                        continue;
+                    }
+                    T t0 = (-h[3 * b + k] - a) / bk, t1 = (h[3 * b + k] - a) / bk;
+                    if (bk < T(0)) std::swap(t0, t1);
+                    if (t0 > s_lo) s_lo = t0;
+                    if (t1 < s_hi) s_hi = t1;
+                }
+                if (hit && s_lo <= s_hi) {
+                    const T z = x[3 * b + 2] + s_hi;
+                    if (z > top) top = z;
+                }
+            }
+            out[(size_t)j * W + i] = top;
+        }
+}
+
 // ----------------------------------------------------------------------------------
 // Double-precision engine
 // ----------------------------------------------------------------------------------
@@ -1249,6 +1296,25 @@ void oracle_footprints(int f32, int n, const float* state13, const float* half, 
             for (int k = 0; k < 8; k++) out8[8 * i + k] = v[k];
         }
     }
+}
+
+// Heightmap (W x H cells of `cell` m from (x0, y0)) of one state, binary32 (f32 != 0)
+// or double; written as float.
+void oracle_heightmap(int f32, int n, const float* state13, const float* half, int W, int H, double x0, double y0,
+                      double cell, float* out) {
+    auto run = [&](auto zero) {
+        using T = decltype(zero);
+        std::vector<T> x(3 * n), q(4 * n), h(3 * n), o((size_t)W * H);
+        for (int i = 0; i < n; i++) {
+            for (int k = 0; k < 3; k++) x[3 * i + k] = (T)state13[13 * i + k];
+            for (int k = 0; k < 4; k++) q[4 * i + k] = (T)state13[13 * i + 3 + k];
+            for (int k = 0; k < 3; k++) h[3 * i + k] = (T)half[3 * i + k];
+        }
+        heightmap<T>(n, x.data(), q.data(), h.data(), W, H, (T)(float)x0, (T)(float)y0, (T)(float)cell, o.data());
+        for (size_t k = 0; k < o.size(); k++) out[k] = (float)o[k];
+    };
+    if (f32) run(0.0f);
+    else run(0.0);
 }
 
 }  // extern "C"

@@ -531,3 +531,79 @@ def test_dense_grid_sampler_rejections_and_noop(orc):
         a = _check_sampler(orc, st, half, sd * 7919 + 1, 2)
         seen.add(a)
     assert -1 in seen and 0 in seen and max(seen) >= 3
+
+
+# ------------------------------------------------------------------ heightmap (Sec. V-A grid)
+def _cell_centres():
+    c = -0.144 + (np.arange(144) + 0.5) * 0.002
+    return np.meshgrid(c, c)  # X[j, i], Y[j, i]
+
+
+def test_heightmap_of_yawed_upright_boxes_is_their_rectangles(orc):
+    """Upright boxes (yaw only): height c_z + h_z exactly where the cell centre lies in
+    the rotated rectangle (independent point-in-rectangle test), 0 elsewhere; several boxes
+    give the cell-wise maximum."""
+    X, Y = _cell_centres()
+    rng = np.random.default_rng(4)
+    rows, halves, want = [], [], np.zeros((144, 144))
+    for b in range(5):
+        yaw = rng.uniform(0, math.pi)
+        h = rng.uniform(0.01, 0.03, 3)
+        # quarter-cell offsets keep cell centres off the rectangle edges
+        c = np.array([rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1), h[2] + 0.01 * b]) + 0.0005
+        rows.append(G.box_row(*c, q=(math.cos(yaw / 2), 0, 0, math.sin(yaw / 2))))
+        halves.append(h)
+        u = np.array([math.cos(yaw), math.sin(yaw)])
+        v = np.array([-u[1], u[0]])
+        du = (X - c[0]) * u[0] + (Y - c[1]) * u[1]
+        dv = (X - c[0]) * v[0] + (Y - c[1]) * v[1]
+        inside = (np.abs(du) <= h[0]) & (np.abs(dv) <= h[1])
+        want = np.maximum(want, np.where(inside, c[2] + h[2], 0.0))
+    st = np.stack(rows)
+    got = orc.heightmap(st, np.array(halves), f32=False)
+    assert np.abs(got - want).max() <= 1e-8  # double result stored as float32
+    assert (got > 0).sum() > 1000
+    # the binary32 twin agrees to rounding
+    assert np.abs(orc.heightmap(st, np.array(halves), f32=True) - want).max() <= 1e-6
+
+
+def test_heightmap_of_tilted_boxes_matches_convex_hull_and_linear_programme(orc):
+    """Tilted boxes: a cell is covered iff its centre lies inside the convex hull of the
+    box's projected vertices, and the stored height is the maximum z of the box on the
+    vertical line, found by a linear programme (scipy), independent of the slab formula."""
+    from scipy.optimize import linprog
+    from scipy.spatial import ConvexHull
+    X, Y = _cell_centres()
+    rng = np.random.default_rng(7)
+    for trial in range(3):
+        q = G.quat_from_rotvec(rng.normal(size=3) * 0.8)
+        h = rng.uniform(0.015, 0.035, 3)
+        c = np.array([rng.uniform(-0.05, 0.05), rng.uniform(-0.05, 0.05), 0.08])
+        row = G.box_row(*c, q=tuple(q))
+        got = orc.heightmap(row[None], h[None], f32=False)
+        V = G.vertices(row, h)
+        hull = ConvexHull(V[:, :2])
+        eq = hull.equations  # a x + b y + d <= 0 inside
+        dist = (eq[:, :1, None] * X[None] + eq[:, 1:2, None] * Y[None] + eq[:, 2:3, None]).max(0)
+        inside, outside = dist < -1e-6, dist > 1e-6
+        assert (got[inside] > 0).all() and (got[outside] == 0).all()
+        R = G.rotmat(q)
+        idx = np.argwhere(inside)
+        for j, i in idx[rng.choice(len(idx), size=40, replace=False)]:
+            # maximise z subject to -h <= R^T (p - c) <= h with p = (x, y, z)
+            A = np.vstack([R.T, -R.T])
+            p0 = np.array([X[j, i], Y[j, i], 0.0]) - c
+            b_ub = np.concatenate([h - R.T @ p0, h + R.T @ p0])
+            res = linprog(c=[-1.0], A_ub=A[:, 2:3], b_ub=b_ub, bounds=[(None, None)], method="highs")
+            assert res.status == 0
+            # inputs enter the oracle as float32 (a quaternion off unit length by ~1e-8)
+            assert abs(got[j, i] - res.x[0]) <= 1e-7
+
+
+def test_heightmap_clamps_at_the_table_and_is_empty_without_boxes(orc):
+    st = np.stack([G.box_row(0.0, 0.0, -0.05)])      # entirely below the table
+    assert (orc.heightmap(st, np.array([[0.02, 0.02, 0.02]])) == 0).all()
+    assert (orc.heightmap(np.zeros((0, 13)), np.zeros((0, 3))) == 0).all()
+    st = np.stack([G.box_row(0.0, 0.0, 0.005)])      # half sunk: top at 0.025
+    m = orc.heightmap(st, np.array([[0.02, 0.02, 0.02]]), f32=False)
+    assert abs(m.max() - 0.025) <= 2e-9  # stored as float32
