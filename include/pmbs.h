@@ -258,6 +258,29 @@ pmbs_status pmbs_eval_start_blocked(pmbs_ctx* ctx, int n_envs, const int32_t* bo
                                     const float* states, const float* half_ext,
                                     const float* starts, uint8_t* out_blocked);
 
+/* Top-down heightmaps of the workspace grid (Sec. V-A: the 0.288 m x 0.288 m workspace
+ * centred on the table, seen by an overhead orthographic camera as 144 x 144 cells of
+ * 2 mm; this depth image is what the paper's grasp classifier reads, Sec. IV-B).
+ * out[e][j][i] (row j along y, column i along x, float32) is the height in m of the
+ * highest box surface above the cell centre x_i = -0.144 + (i + 0.5) * 0.002 (y_j
+ * likewise), or 0 where the table shows.  Each box's top over a cell is found by clipping
+ * the vertical line through the cell centre against the box's three slabs; the whole map
+ * is defined in binary32 with one rounding per operation in a fixed order, so it is
+ * reproducible bit for bit.
+ *  pmbs_render_heightmaps: a state snapshot (same arrays as pmbs_eval_pairs; 0..64 boxes
+ *    per environment) to the host array out[n_envs][144][144]; synchronous.  Bad sizes
+ *    -> PMBS_E_INVALID, no staging room -> PMBS_E_OOM.
+ *  pmbs_render_heightmaps_device: the same with device arrays (d_states and d_half hold
+ *    the rows of boxes box_offset[0] .. box_offset[n_envs]; box counts above 64 are
+ *    clamped); asynchronous on the context's stream, d_out caller-owned.
+ *  pmbs_query_heightmaps: the current states of a batch's environments (after a finished
+ *    batch: the final states) to the host array out[n_envs][144][144]; synchronous. */
+pmbs_status pmbs_render_heightmaps(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                                   const float* half_ext, float* out);
+pmbs_status pmbs_render_heightmaps_device(pmbs_ctx* ctx, int n_envs, const int32_t* d_box_offset,
+                                          const float* d_states, const float* d_half, float* d_out);
+pmbs_status pmbs_query_heightmaps(pmbs_ctx* ctx, int64_t batch, float* out);
+
 /* Launch shape the context uses for a batch whose largest scene has max_boxes boxes:
  * lanes per environment, warps per block, contact point slots and manifolds kept in
  * shared memory per environment, and shared bytes per block.  Chosen by the tuning rule

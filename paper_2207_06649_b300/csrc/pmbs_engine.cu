@@ -458,6 +458,103 @@ __global__ void __launch_bounds__(128) penetration_kernel(int n_scenes, const in
     if (lane == 0) out[s] = worst;
 }
 
+// ------------------------------------------------------------------ heightmaps
+// Top-down heightmap of the workspace grid (Sec. V-A: 0.288 m x 0.288 m seen from above,
+// 144 x 144 cells of 2 mm; the depth image the grasp classifier of Sec. IV-B reads):
+// cell (i, j) holds the height of the highest box surface above its centre, or 0.  For
+// each box the vertical line through the cell centre is written in the box frame
+// (a_k + b_k s with s = z - c_z) and clipped against the three slabs |.| <= h_k; a
+// non-empty interval puts the box's top at c_z + s_hi.  Every operation is an explicitly
+// rounded binary32 intrinsic in a fixed order, so the map is defined bit for bit.  A
+// box is only tested for cells inside its footprint's bounding square grown by 1 mm (the
+// line misses the box there by at least 1 mm, far beyond any rounding).
+struct HMCsr {  // state snapshot: CSR box ranges, 13-float states, half extents
+    const int32_t* box_offset;
+    const float* states;
+    const float* half;
+    __device__ __forceinline__ int n(int e) const { return box_offset[e + 1] - box_offset[e]; }
+    __device__ __forceinline__ const float* st(int e, int i) const {
+        return states + (size_t)(box_offset[e] - box_offset[0] + i) * 13;
+    }
+    __device__ __forceinline__ const float* h(int e, int i) const {
+        return half + (size_t)(box_offset[e] - box_offset[0] + i) * 3;
+    }
+};
+struct HMBatch {  // a rollout batch's current states (half extents from the scene records)
+    const EnvIn* env;
+    const float* state;
+    __device__ __forceinline__ int n(int e) const { return env[e].n; }
+    __device__ __forceinline__ const float* st(int e, int i) const {
+        return state + (size_t)(env[e].box_off + i) * 13;
+    }
+    __device__ __forceinline__ const float* h(int e, int i) const { return env[e].rec + (size_t)kRecFloats * i + 13; }
+};
+
+constexpr int kHMCells = 144;
+constexpr float kHMCell = 0.002f, kHMOrigin = -0.144f;
+
+template <class Src>
+__global__ void __launch_bounds__(256) heightmap_kernel(const Src src, int n_envs, float* out) {
+    __shared__ float sR[kMaxBoxes][9];
+    __shared__ float sc[kMaxBoxes][3], sh[kMaxBoxes][3], sbox[kMaxBoxes][4];
+    const int e = blockIdx.x;
+    if (e >= n_envs) return;
+    const int n = min(src.n(e), kMaxBoxes);
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        const float* s = src.st(e, b);
+        const float* hh = src.h(e, b);
+        float R[9];
+        quat_to_R_exact(s[3], s[4], s[5], s[6], R);
+        for (int k = 0; k < 9; k++) sR[b][k] = R[k];
+        for (int k = 0; k < 3; k++) {
+            sc[b][k] = s[k];
+            sh[b][k] = hh[k];
+        }
+        const float ex = aabb_half_exact(R, hh[0], hh[1], hh[2]) + 1e-3f;      // row 0: x
+        const float ey = aabb_half_exact(R + 3, hh[0], hh[1], hh[2]) + 1e-3f;  // row 1: y
+        sbox[b][0] = s[0] - ex;
+        sbox[b][1] = s[0] + ex;
+        sbox[b][2] = s[1] - ey;
+        sbox[b][3] = s[1] + ey;
+    }
+    __syncthreads();
+    float* o = out + (size_t)e * kHMCells * kHMCells;
+    for (int cidx = threadIdx.x; cidx < kHMCells * kHMCells; cidx += blockDim.x) {
+        const int i = cidx % kHMCells, j = cidx / kHMCells;
+        const float xc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)i, 0.5f), kHMCell));
+        const float yc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)j, 0.5f), kHMCell));
+        float top = 0.f;
+        for (int b = 0; b < n; b++) {
+            if (xc < sbox[b][0] || xc > sbox[b][1] || yc < sbox[b][2] || yc > sbox[b][3]) continue;
+            const float dx = __fsub_rn(xc, sc[b][0]), dy = __fsub_rn(yc, sc[b][1]);
+            float s_lo = -INFINITY, s_hi = INFINITY;
+            bool hit = true;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float a = __fadd_rn(__fmul_rn(sR[b][k], dx), __fmul_rn(sR[b][3 + k], dy));
+                const float bk = sR[b][6 + k];
+                if (bk == 0.f) {
+                    if (!(fabsf(a) <= sh[b][k])) hit = false;
+                    continue;
+                }
+                float t0 = __fdiv_rn(__fsub_rn(-sh[b][k], a), bk), t1 = __fdiv_rn(__fsub_rn(sh[b][k], a), bk);
+                if (bk < 0.f) {
+                    const float t = t0;
+                    t0 = t1;
+                    t1 = t;
+                }
+                if (t0 > s_lo) s_lo = t0;
+                if (t1 < s_hi) s_hi = t1;
+            }
+            if (hit && s_lo <= s_hi) {
+                const float z = __fadd_rn(sc[b][2], s_hi);
+                if (z > top) top = z;
+            }
+        }
+        o[cidx] = top;
+    }
+}
+
 // Scene table update: table[ids[i]] = desc[i].
 __global__ void scatter_desc_kernel(int n, const int32_t* ids, const SceneDesc* desc, SceneDesc* table) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1736,6 +1833,86 @@ pmbs_status pmbs_eval_start_blocked(pmbs_ctx* ctx, int n_envs, const int32_t* bo
     CU(cudaSetDevice(ctx->device));
     return eval_common(ctx, 3, n_envs, box_offset, states, half_ext, nullptr, nullptr, nullptr, 0, starts, nullptr,
                        nullptr, nullptr, nullptr, nullptr, nullptr, out_blocked, nullptr, nullptr);
+}
+
+pmbs_status pmbs_render_heightmaps_device(pmbs_ctx* ctx, int n_envs, const int32_t* d_box_offset,
+                                          const float* d_states, const float* d_half, float* d_out) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n_envs < 0 || (n_envs > 0 && (!d_box_offset || !d_states || !d_half || !d_out)))
+        return fail(ctx, PMBS_E_INVALID, "bad arguments");
+    if (n_envs == 0) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    heightmap_kernel<HMCsr><<<n_envs, 256, 0, ctx->stream>>>(HMCsr{d_box_offset, d_states, d_half}, n_envs, d_out);
+    CU(cudaGetLastError());
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_render_heightmaps(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                                   const float* half_ext, float* out) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n_envs < 0 || (n_envs > 0 && (!box_offset || !states || !half_ext || !out)))
+        return fail(ctx, PMBS_E_INVALID, "bad arguments");
+    if (n_envs == 0) return PMBS_OK;
+    for (int e = 0; e < n_envs; e++) {
+        const int n = box_offset[e + 1] - box_offset[e];
+        if (n < 0 || n > kMaxBoxes) return fail(ctx, PMBS_E_INVALID, "box count out of range");
+    }
+    CU(cudaSetDevice(ctx->device));
+    const int B = box_offset[n_envs] - box_offset[0];
+    const size_t map_bytes = sizeof(float) * kHMCells * kHMCells * (size_t)n_envs;
+    const size_t o_off = 0, o_st = (sizeof(int32_t) * (n_envs + 1) + 255) & ~(size_t)255;
+    const size_t o_h = o_st + ((sizeof(float) * 13 * std::max(B, 1) + 255) & ~(size_t)255);
+    const size_t o_map = o_h + ((sizeof(float) * 3 * std::max(B, 1) + 255) & ~(size_t)255);
+    const size_t sz = o_map + map_bytes;
+    const size_t boff = ctx->arena.alloc(sz);
+    if (boff == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "heightmap staging does not fit");
+    char* base = (char*)arena_ptr(ctx, boff);
+    cudaError_t e = cudaMemcpyAsync(base + o_off, box_offset, sizeof(int32_t) * (n_envs + 1), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess && B > 0)
+        e = cudaMemcpyAsync(base + o_st, states + (size_t)13 * box_offset[0], sizeof(float) * 13 * B,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && B > 0)
+        e = cudaMemcpyAsync(base + o_h, half_ext + (size_t)3 * box_offset[0], sizeof(float) * 3 * B,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        heightmap_kernel<HMCsr><<<n_envs, 256, 0, ctx->stream>>>(
+            HMCsr{(const int32_t*)(base + o_off), (const float*)(base + o_st), (const float*)(base + o_h)}, n_envs,
+            (float*)(base + o_map));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, base + o_map, map_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    else cudaStreamSynchronize(ctx->stream);
+    ctx->arena.release(boff, sz);
+    if (e != cudaSuccess) return fail(ctx, PMBS_E_CUDA, std::string("heightmaps: ") + cudaGetErrorString(e));
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_query_heightmaps(pmbs_ctx* ctx, int64_t batch, float* out) {
+    if (!ctx || !out) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b) return fail(ctx, PMBS_E_INVALID, "unknown batch");
+    if (b->n_envs == 0) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    const size_t map_bytes = sizeof(float) * kHMCells * kHMCells * (size_t)b->n_envs;
+    const size_t boff = ctx->arena.alloc(map_bytes);
+    if (boff == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "heightmap staging does not fit");
+    float* d_map = (float*)arena_ptr(ctx, boff);
+    heightmap_kernel<HMBatch><<<b->n_envs, 256, 0, b->stream>>>(HMBatch{b->env, b->state}, b->n_envs, d_map);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_map, map_bytes, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    else cudaStreamSynchronize(b->stream);
+    ctx->arena.release(boff, map_bytes);
+    if (e != cudaSuccess) return fail(ctx, PMBS_E_CUDA, std::string("heightmaps: ") + cudaGetErrorString(e));
+    return PMBS_OK;
 }
 
 pmbs_status pmbs_launch_shape(pmbs_ctx* ctx, int max_boxes, int32_t* out_lanes, int32_t* out_wpb, int32_t* out_Ps,

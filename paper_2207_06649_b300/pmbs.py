@@ -30,7 +30,8 @@ EXPORTED = ["pmbs_default_config", "pmbs_create", "pmbs_create_with_arena", "pmb
             "pmbs_eval_pairs", "pmbs_eval_grasp", "pmbs_eval_sample", "pmbs_eval_start_blocked",
             "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_rollout_noalloc",
             "pmbs_step_graph", "pmbs_autotune", "pmbs_server_create", "pmbs_server_submit",
-            "pmbs_server_wait", "pmbs_server_stats", "pmbs_server_cancel", "pmbs_server_destroy"]
+            "pmbs_server_wait", "pmbs_server_stats", "pmbs_server_cancel", "pmbs_server_destroy",
+            "pmbs_render_heightmaps", "pmbs_render_heightmaps_device", "pmbs_query_heightmaps"]
 
 
 class pmbs_config(C.Structure):
@@ -102,6 +103,9 @@ def load(build_if_missing: bool = True):
         "pmbs_server_wait": ([vp, C.c_int64, i32, vp, vp, vp, vp, P(C.c_double)], i32),
         "pmbs_server_stats": ([vp, vp], i32),
         "pmbs_server_cancel": ([vp, C.c_int64], i32),
+        "pmbs_render_heightmaps": ([vp, i32, vp, vp, vp, vp], i32),
+        "pmbs_render_heightmaps_device": ([vp, i32, vp, vp, vp, vp], i32),
+        "pmbs_query_heightmaps": ([vp, C.c_int64, vp], i32),
         "pmbs_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -328,6 +332,28 @@ class Engine:
         return out[:ne].astype(bool)
 
     # ---- launch shape and probes
+    HM_CELLS = 144
+
+    def render_heightmaps(self, box_offset, states, half):
+        """Top-down workspace heightmaps [n_envs, 144 (y), 144 (x)] of a state snapshot."""
+        box_offset, states, half = self._csr(box_offset, states, half)
+        ne = box_offset.shape[0] - 1
+        out = np.zeros((max(ne, 1), self.HM_CELLS, self.HM_CELLS), np.float32)
+        self._check(self.lib.pmbs_render_heightmaps(self.ctx, ne, _p(box_offset), _p(states), _p(half), _p(out)),
+                    "pmbs_render_heightmaps")
+        return out[:ne]
+
+    def render_heightmaps_device(self, n_envs, d_box_offset, d_states, d_half, d_out):
+        self._check(self.lib.pmbs_render_heightmaps_device(self.ctx, n_envs, C.c_void_p(d_box_offset),
+                                                           C.c_void_p(d_states), C.c_void_p(d_half),
+                                                           C.c_void_p(d_out)), "pmbs_render_heightmaps_device")
+
+    def query_heightmaps(self, batch):
+        ne, _ = self.batch_info(batch)
+        out = np.zeros((max(ne, 1), self.HM_CELLS, self.HM_CELLS), np.float32)
+        self._check(self.lib.pmbs_query_heightmaps(self.ctx, batch, _p(out)), "pmbs_query_heightmaps")
+        return out[:ne]
+
     def launch_shape(self, max_boxes):
         g, w, ps, ms, sm = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         self._check(self.lib.pmbs_launch_shape(self.ctx, max_boxes, C.byref(g), C.byref(w), C.byref(ps),
