@@ -41,6 +41,16 @@ TRAFFIC = {"source_sha": "445e737255b3314f", "bytes_per_launch": 19454090,
                    "32,2,0 launch shape, scaled by env-steps (371,760 -> 1,484,160) to the 4096-env launch"}
 
 
+def measured_hbm_gbs():
+    """Measured copy bandwidth of the B300s (MEASURED_PEAKS.json), else the
+    recipe's fallback of 6400 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2207_06649_b300", "csrc", "*"))):
@@ -61,6 +71,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch shape")
+    ap.add_argument("--no-heightmaps", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'lanes,warps_per_block,smem_manifolds' instead of autotuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="served-load run length (0 = skip)")
@@ -356,6 +367,36 @@ def run_ours(args):
         e2e = {"value": env_steps * args.steps * ws / te, "unit": "env-steps/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # top-down workspace heightmaps of the workload's final states (device entry point),
+    # timed with CUDA events on the engine's stream; output-write bound (83 KB per map)
+    heightmaps = None
+    if not args.no_heightmaps:
+        d_off = torch.from_numpy(scenes.box_offset.astype(np.int32)).to(dev)
+        d_st = torch.from_numpy(np.ascontiguousarray(st, np.float32)).to(dev)
+        d_half = torch.from_numpy(np.ascontiguousarray(scenes.half, np.float32)).to(dev)
+        d_hm = torch.empty((args.envs, 144, 144), dtype=torch.float32, device=dev)
+        render = lambda: eng.render_heightmaps_device(args.envs, d_off.data_ptr(), d_st.data_ptr(),
+                                                      d_half.data_ptr(), d_hm.data_ptr())
+        for _ in range(3):
+            render()
+        h0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        h1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            h0[i].record()
+            render()
+            h1[i].record()
+        torch.cuda.synchronize()
+        hm_s = float(np.mean([a.elapsed_time(b) for a, b in zip(h0, h1)])) / 1e3
+        out_bytes = 4.0 * 144 * 144 * args.envs
+        in_bytes = float(boxes.sum()) * (52 + 12) + 4.0 * (args.envs + 1)
+        hbm = measured_hbm_gbs()
+        heightmaps = {"maps": args.envs, "cells": "144 x 144 x 2 mm", "ms": hm_s * 1e3,
+                      "maps_per_s": args.envs / hm_s, "bytes_per_launch": out_bytes + in_bytes,
+                      "achieved_gbs": (out_bytes + in_bytes) / hm_s / 1e9, "peak_gbs": hbm,
+                      "frac": (out_bytes + in_bytes) / hm_s / 1e9 / hbm if hbm else None,
+                      "kernel": "heightmap_kernel"}
+
     serving = None
     if args.serve_seconds > 0 and ws == 1:
         pool_sc, pool_pu, _ = sg.config_uneven(seed=args.seed + 7, n_envs=512)
@@ -405,6 +446,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
         "serving": serving,
+        "heightmaps": heightmaps,
         "planning": planning,
         "gpu_launches": 2 * args.steps,
     }

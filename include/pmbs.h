@@ -272,7 +272,8 @@ pmbs_status pmbs_eval_start_blocked(pmbs_ctx* ctx, int n_envs, const int32_t* bo
  *    -> PMBS_E_INVALID, no staging room -> PMBS_E_OOM.
  *  pmbs_render_heightmaps_device: the same with device arrays (d_states and d_half hold
  *    the rows of boxes box_offset[0] .. box_offset[n_envs]; box counts above 64 are
- *    clamped); asynchronous on the context's stream, d_out caller-owned.
+ *    clamped); asynchronous on the context's stream; d_out caller-owned and 16-byte
+ *    aligned (PMBS_E_INVALID otherwise).
  *  pmbs_query_heightmaps: the current states of a batch's environments (after a finished
  *    batch: the final states) to the host array out[n_envs][144][144]; synchronous. */
 pmbs_status pmbs_render_heightmaps(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,

@@ -305,14 +305,23 @@ int sample_push(int n, const T* x, const T* q, const T* h, uint64_t seed, int k,
 // rotation R and half extents h, the vertical line through (x, y) written in the box
 // frame is a + b s (s = z - c_z) with a_k = R_0k (x - c_x) + R_1k (y - c_y) and
 // b_k = R_2k; it is inside the box while |a_k + b_k s| <= h_k for every k, i.e. for s
-// in the intersection of [(-h_k - a_k) / b_k, (h_k - a_k) / b_k] (ends swapped when
-// b_k < 0; when b_k = 0 the constraint holds for every s if |a_k| <= h_k and for none
-// otherwise).  A non-empty intersection [s_lo, s_hi] puts the box's top over the cell at
-// c_z + s_hi.  Every operation is written in its evaluation order (binary32 twin).
+// in the intersection of [-(a_k r_k) - h_k r_k, -(a_k r_k) + h_k r_k] with r_k = 1 / b_k
+// (r_k and h_k r_k rounded once per box; ends swapped when b_k < 0; when b_k = 0 the
+// constraint holds for every s if |a_k| <= h_k and for none otherwise).  A non-empty
+// intersection [s_lo, s_hi] puts the box's top over the cell at c_z + s_hi.  Every
+// operation is written in its evaluation order (binary32 twin); fma() is one fused
+// multiply-add with a single rounding: a_k = fma(R_0k, x - c_x, R_1k (y - c_y)) and the
+// slab ends fma(-a_k, r_k, -+h_k r_k).
 template <typename T>
 void heightmap(int n, const T* x, const T* q, const T* h, int W, int H, T x0, T y0, T cell, T* out) {
-    std::vector<T> R(9 * n);
-    for (int b = 0; b < n; b++) quat_to_R(q + 4 * b, &R[9 * b]);
+    std::vector<T> R(9 * n), rb(3 * n), hr(3 * n);
+    for (int b = 0; b < n; b++) {
+        quat_to_R(q + 4 * b, &R[9 * b]);
+        for (int k = 0; k < 3; k++) {
+            rb[3 * b + k] = R[9 * b + 6 + k] == T(0) ? T(0) : T(1) / R[9 * b + 6 + k];
+            hr[3 * b + k] = h[3 * b + k] * rb[3 * b + k];
+        }
+    }
     for (int j = 0; j < H; j++)
         for (int i = 0; i < W; i++) {
             const T xc = x0 + ((T)i + T(0.5)) * cell;
@@ -324,13 +333,14 @@ void heightmap(int n, const T* x, const T* q, const T* h, int W, int H, T x0, T 
                 T s_lo = -INFINITY, s_hi = INFINITY;
                 bool hit = true;
                 for (int k = 0; k < 3 && hit; k++) {
-                    const T a = Rb[k] * dx + Rb[3 + k] * dy;
+                    const T a = std::fma(Rb[k], dx, Rb[3 + k] * dy);
                     const T bk = Rb[6 + k];
                     if (bk == T(0)) {
                         if (!(std::fabs(a) <= h[3 * b + k])) hit = false;
                         continue;
                     }
-                    T t0 = (-h[3 * b + k] - a) / bk, t1 = (h[3 * b + k] - a) / bk;
+                    const T r = rb[3 * b + k];
+                    T t0 = std::fma(-a, r, -hr[3 * b + k]), t1 = std::fma(-a, r, hr[3 * b + k]);
                     if (bk < T(0)) std::swap(t0, t1);
                     if (t0 > s_lo) s_lo = t0;
                     if (t1 < s_hi) s_hi = t1;

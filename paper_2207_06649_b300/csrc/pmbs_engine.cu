@@ -463,8 +463,9 @@ __global__ void __launch_bounds__(128) penetration_kernel(int n_scenes, const in
 // 144 x 144 cells of 2 mm; the depth image the grasp classifier of Sec. IV-B reads):
 // cell (i, j) holds the height of the highest box surface above its centre, or 0.  For
 // each box the vertical line through the cell centre is written in the box frame
-// (a_k + b_k s with s = z - c_z) and clipped against the three slabs |.| <= h_k; a
-// non-empty interval puts the box's top at c_z + s_hi.  Every operation is an explicitly
+// (a_k + b_k s with s = z - c_z) and clipped against the three slabs |.| <= h_k (slab
+// ends -(a_k / b_k) -+ h_k / b_k, with 1 / b_k and h_k / b_k rounded once per box and each
+// end one fused multiply-add); a non-empty interval puts the box's top at c_z + s_hi.  Every operation is an explicitly
 // rounded binary32 intrinsic in a fixed order, so the map is defined bit for bit.  A
 // box is only tested for cells inside its footprint's bounding square grown by 1 mm (the
 // line misses the box there by at least 1 mm, far beyond any rounding).
@@ -493,13 +494,25 @@ struct HMBatch {  // a rollout batch's current states (half extents from the sce
 constexpr int kHMCells = 144;
 constexpr float kHMCell = 0.002f, kHMOrigin = -0.144f;
 
+// One block of 512 threads per environment.  Each box visits only the cells of its grown
+// footprint square (threads laid out 32 x 16 over it) and raises a shared-memory map with
+// an integer atomicMax on the bit pattern: the heights written are positive floats,
+// whose bit patterns order like their values, so the map is the exact maximum whatever
+// the order.  The finished map leaves in 16-byte stores.  Dynamic shared memory:
+// kHMCells^2 words.
+constexpr size_t kHMSmem = sizeof(unsigned int) * kHMCells * kHMCells;
+
 template <class Src>
-__global__ void __launch_bounds__(256) heightmap_kernel(const Src src, int n_envs, float* out) {
-    __shared__ float sR[kMaxBoxes][9];
+__global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_envs, float* out) {
+    __shared__ float sR[kMaxBoxes][9], srb[kMaxBoxes][3], shr[kMaxBoxes][3];
     __shared__ float sc[kMaxBoxes][3], sh[kMaxBoxes][3], sbox[kMaxBoxes][4];
+    __shared__ int srect[kMaxBoxes][4];
+    unsigned int* map = reinterpret_cast<unsigned int*>(pmbs_smem);
     const int e = blockIdx.x;
     if (e >= n_envs) return;
     const int n = min(src.n(e), kMaxBoxes);
+    uint4* m4 = reinterpret_cast<uint4*>(map);
+    for (int c = threadIdx.x; c < kHMCells * kHMCells / 4; c += blockDim.x) m4[c] = make_uint4(0u, 0u, 0u, 0u);
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
         const float* s = src.st(e, b);
         const float* hh = src.h(e, b);
@@ -509,6 +522,8 @@ __global__ void __launch_bounds__(256) heightmap_kernel(const Src src, int n_env
         for (int k = 0; k < 3; k++) {
             sc[b][k] = s[k];
             sh[b][k] = hh[k];
+            srb[b][k] = R[6 + k] == 0.f ? 0.f : __frcp_rn(R[6 + k]);  // 1 / b_k, rounded once
+            shr[b][k] = __fmul_rn(hh[k], srb[b][k]);                    // h_k / b_k
         }
         const float ex = aabb_half_exact(R, hh[0], hh[1], hh[2]) + 1e-3f;      // row 0: x
         const float ey = aabb_half_exact(R + 3, hh[0], hh[1], hh[2]) + 1e-3f;  // row 1: y
@@ -516,42 +531,58 @@ __global__ void __launch_bounds__(256) heightmap_kernel(const Src src, int n_env
         sbox[b][1] = s[0] + ex;
         sbox[b][2] = s[1] - ey;
         sbox[b][3] = s[1] + ey;
+        // cells whose centres can fall inside the square, one cell of slack on each side
+        // (the exact test below decides; the range only bounds the work)
+        const float inv = 1.f / kHMCell;
+        auto cell_of = [&](float v) {  // clamped before the conversion to int
+            return (int)floorf(fminf(fmaxf((v - kHMOrigin) * inv, -4.f), (float)kHMCells + 4.f));
+        };
+        srect[b][0] = max(0, cell_of(sbox[b][0]) - 1);
+        srect[b][1] = min(kHMCells - 1, cell_of(sbox[b][1]) + 1);
+        srect[b][2] = max(0, cell_of(sbox[b][2]) - 1);
+        srect[b][3] = min(kHMCells - 1, cell_of(sbox[b][3]) + 1);
     }
     __syncthreads();
-    float* o = out + (size_t)e * kHMCells * kHMCells;
-    for (int cidx = threadIdx.x; cidx < kHMCells * kHMCells; cidx += blockDim.x) {
-        const int i = cidx % kHMCells, j = cidx / kHMCells;
-        const float xc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)i, 0.5f), kHMCell));
-        const float yc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)j, 0.5f), kHMCell));
-        float top = 0.f;
-        for (int b = 0; b < n; b++) {
-            if (xc < sbox[b][0] || xc > sbox[b][1] || yc < sbox[b][2] || yc > sbox[b][3]) continue;
-            const float dx = __fsub_rn(xc, sc[b][0]), dy = __fsub_rn(yc, sc[b][1]);
-            float s_lo = -INFINITY, s_hi = INFINITY;
-            bool hit = true;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int b = 0; b < n; b++) {
+        const int i0 = srect[b][0], i1 = srect[b][1], j0 = srect[b][2], j1 = srect[b][3];
+        for (int j = j0 + ty; j <= j1; j += 16)
+            for (int i = i0 + tx; i <= i1; i += 32) {
+                const float xc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)i, 0.5f), kHMCell));
+                const float yc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)j, 0.5f), kHMCell));
+                if (xc < sbox[b][0] || xc > sbox[b][1] || yc < sbox[b][2] || yc > sbox[b][3]) continue;
+                const float dx = __fsub_rn(xc, sc[b][0]), dy = __fsub_rn(yc, sc[b][1]);
+                float s_lo = -INFINITY, s_hi = INFINITY;
+                bool hit = true;
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const float a = __fadd_rn(__fmul_rn(sR[b][k], dx), __fmul_rn(sR[b][3 + k], dy));
-                const float bk = sR[b][6 + k];
-                if (bk == 0.f) {
-                    if (!(fabsf(a) <= sh[b][k])) hit = false;
-                    continue;
+                for (int k = 0; k < 3; k++) {
+                    const float a = __fmaf_rn(sR[b][k], dx, __fmul_rn(sR[b][3 + k], dy));
+                    const float bk = sR[b][6 + k];
+                    if (bk == 0.f) {
+                        if (!(fabsf(a) <= sh[b][k])) hit = false;
+                        continue;
+                    }
+                    const float r = srb[b][k];
+                    float t0 = __fmaf_rn(-a, r, -shr[b][k]), t1 = __fmaf_rn(-a, r, shr[b][k]);
+                    if (bk < 0.f) {
+                        const float tt = t0;
+                        t0 = t1;
+                        t1 = tt;
+                    }
+                    if (t0 > s_lo) s_lo = t0;
+                    if (t1 < s_hi) s_hi = t1;
                 }
-                float t0 = __fdiv_rn(__fsub_rn(-sh[b][k], a), bk), t1 = __fdiv_rn(__fsub_rn(sh[b][k], a), bk);
-                if (bk < 0.f) {
-                    const float t = t0;
-                    t0 = t1;
-                    t1 = t;
+                if (hit && s_lo <= s_hi) {
+                    const float z = __fadd_rn(sc[b][2], s_hi);
+                    if (z > 0.f) atomicMax(&map[j * kHMCells + i], __float_as_uint(z));
                 }
-                if (t0 > s_lo) s_lo = t0;
-                if (t1 < s_hi) s_hi = t1;
             }
-            if (hit && s_lo <= s_hi) {
-                const float z = __fadd_rn(sc[b][2], s_hi);
-                if (z > top) top = z;
-            }
-        }
-        o[cidx] = top;
+    }
+    __syncthreads();
+    float4* o = reinterpret_cast<float4*>(out + (size_t)e * kHMCells * kHMCells);
+    for (int c = threadIdx.x; c < kHMCells * kHMCells / 4; c += blockDim.x) {
+        const uint4 v = m4[c];
+        o[c] = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w));
     }
 }
 
@@ -937,6 +968,11 @@ pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, s
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(heightmap_kernel<HMCsr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHMSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(heightmap_kernel<HMBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHMSmem);
+
     if (e != cudaSuccess) {
         if (ctx->own_arena) cudaFree(base);
         delete ctx;
@@ -1842,9 +1878,10 @@ pmbs_status pmbs_render_heightmaps_device(pmbs_ctx* ctx, int n_envs, const int32
     ctx->err.clear();
     if (n_envs < 0 || (n_envs > 0 && (!d_box_offset || !d_states || !d_half || !d_out)))
         return fail(ctx, PMBS_E_INVALID, "bad arguments");
+    if (reinterpret_cast<uintptr_t>(d_out) % 16 != 0) return fail(ctx, PMBS_E_INVALID, "d_out must be 16-byte aligned");
     if (n_envs == 0) return PMBS_OK;
     CU(cudaSetDevice(ctx->device));
-    heightmap_kernel<HMCsr><<<n_envs, 256, 0, ctx->stream>>>(HMCsr{d_box_offset, d_states, d_half}, n_envs, d_out);
+    heightmap_kernel<HMCsr><<<n_envs, 512, kHMSmem, ctx->stream>>>(HMCsr{d_box_offset, d_states, d_half}, n_envs, d_out);
     CU(cudaGetLastError());
     return PMBS_OK;
 }
@@ -1880,7 +1917,7 @@ pmbs_status pmbs_render_heightmaps(pmbs_ctx* ctx, int n_envs, const int32_t* box
         e = cudaMemcpyAsync(base + o_h, half_ext + (size_t)3 * box_offset[0], sizeof(float) * 3 * B,
                             cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) {
-        heightmap_kernel<HMCsr><<<n_envs, 256, 0, ctx->stream>>>(
+        heightmap_kernel<HMCsr><<<n_envs, 512, kHMSmem, ctx->stream>>>(
             HMCsr{(const int32_t*)(base + o_off), (const float*)(base + o_st), (const float*)(base + o_h)}, n_envs,
             (float*)(base + o_map));
         e = cudaGetLastError();
@@ -1905,7 +1942,7 @@ pmbs_status pmbs_query_heightmaps(pmbs_ctx* ctx, int64_t batch, float* out) {
     const size_t boff = ctx->arena.alloc(map_bytes);
     if (boff == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "heightmap staging does not fit");
     float* d_map = (float*)arena_ptr(ctx, boff);
-    heightmap_kernel<HMBatch><<<b->n_envs, 256, 0, b->stream>>>(HMBatch{b->env, b->state}, b->n_envs, d_map);
+    heightmap_kernel<HMBatch><<<b->n_envs, 512, kHMSmem, b->stream>>>(HMBatch{b->env, b->state}, b->n_envs, d_map);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_map, map_bytes, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
