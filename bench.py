@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": "445e737255b3314f", "bytes_per_launch": 19454090,
+TRAFFIC = {"source_sha": "2e4be2d81d48df9c", "bytes_per_launch": 19454090,
            "note": "ncu dram bytes (read 3.315 MB + write 1.558 MB) of a 1024-env launch in the "
                    "32,2,0 launch shape, scaled by env-steps (371,760 -> 1,484,160) to the 4096-env launch"}
 
@@ -52,9 +52,16 @@ def measured_hbm_gbs():
 
 
 def kernel_source_sha():
+    """Hash of the rollout kernel's device code: the three device headers and the marked
+    rollout section of the engine source (host code and other kernels excluded)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2207_06649_b300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    csrc = os.path.join(ROOT, "paper_2207_06649_b300", "csrc")
+    for f in ("pmbs_exact.cuh", "pmbs_collide.cuh", "pmbs_warp.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    eng = open(os.path.join(csrc, "pmbs_engine.cu"), "rb").read()
+    a = eng.index(b"// ---- rollout device code begins")
+    b = eng.index(b"// ---- rollout device code ends")
+    h.update(eng[a:b])
     return h.hexdigest()[:16]
 
 

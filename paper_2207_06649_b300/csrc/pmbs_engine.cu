@@ -34,6 +34,8 @@ constexpr int kRecFloats = 18;  // scene record per box: state13, half[3], mass,
 constexpr int kSceneTableCap = 1 << 18;
 constexpr int kMaxWarpsPerSM = 32;
 
+// ---- rollout device code begins (the benchmark ties its ncu traffic figure to a hash of
+// this section and of the three device headers)
 struct SceneDesc {
     const float* rec;
     int n;
@@ -357,6 +359,7 @@ __global__ void __launch_bounds__(128, 3) rollout_kernel(const __grid_constant__
     const WarpMem W = bind_mem(a.L, (uint32_t)slot * (uint32_t)a.L.bytes, a.gscratch + gslot * a.scratch_f4_per_warp);
     run_slots(a, W, g);
 }
+// ---- rollout device code ends
 
 // Batch set-up: per-env scene descriptor and box offset (block-wide scan), processing
 // order by descending box count (bucket sort), totals.  One block of 1024 threads.
