@@ -86,6 +86,11 @@ def parse():
     ap.add_argument("--arena-gb", type=float, default=8.0, help="device arena of the timed engine")
     ap.add_argument("--plan-tmax", type=float, default=2.0, help="PMBS planning budget per action (s)")
     ap.add_argument("--serial-budgets", default="2,8", help="serial MCTS budgets per action (s)")
+    ap.add_argument("--plan-c", default="1.4", help="UCB exploration constants of the planning run")
+    ap.add_argument("--planning-study", action="store_true",
+                    help="only the planning episodes (--plan-seeds, --plan-c, budgets); one JSON line")
+    ap.add_argument("--cpu-config2", action="store_true",
+                    help="only the FP64 oracle on the fixed 1024 x 15-box workload in full; one JSON line")
     return ap.parse_args()
 
 
@@ -338,7 +343,8 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     elapsed = t0.elapsed_time(t1) / 1e3
-    kernel_s = float(np.mean([a.elapsed_time(b) for a, b in zip(k0, k1)])) / 1e3
+    step_ms = [a.elapsed_time(b) for a, b in zip(k0, k1)]
+    kernel_s = float(np.mean(step_ms)) / 1e3
     for b in batches:
         eng.release_batch(b)
     elapsed, total_env_steps = multigpu.reduce_job(elapsed, env_steps * args.steps, device=dev)
@@ -442,7 +448,9 @@ def run_ours(args):
                    "box_steps_per_s": value * float(boxes.mean()),
                    "l2": "flushed before every step (256 MB device write)",
                    "parallelism": f"one environment per warp, persistent launch; {ws} GPU(s), weak scaling",
-                   "launch_shape": tuned if tuned is not None else "default"},
+                   "launch_shape": tuned if tuned is not None else "default",
+                   "step_ms_best": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms)),
+                   "env_steps_per_s_best": env_steps / (float(np.min(step_ms)) / 1e3)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "rollout_kernel", "kernel_ms": kernel_s * 1e3,
@@ -466,9 +474,47 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def planning_study(args):
+    """Planning episodes alone: for every UCB constant, PMBS and the serial budgets."""
+    from paper_2207_06649_b300 import pmbs, scenegen as sg
+    budgets = [float(x) for x in args.serial_budgets.split(",") if x]
+    out = {"study": "planning", "seeds": args.plan_seeds, "pmbs_budget_s": args.plan_tmax,
+           "config": "30-box clutter, target buried on 16 rays within 0.03 m, gamma 0.8, d_T 7 + d_s 3, "
+                     "512 rollouts per PMBS iteration, expansion candidates 16 contour points per box "
+                     "within 0.1 m, completion within 16 actions", "by_c": {}}
+    for c in [float(x) for x in args.plan_c.split(",") if x]:
+        out["by_c"][f"{c:g}"] = planning_run(pmbs, sg, 0, args.plan_seeds, args.plan_tmax, budgets, c=c)
+    print(json.dumps(out), flush=True)
+
+
+def cpu_config2(args):
+    """The FP64 oracle on the fixed workload (1024 clones of one 15-box scene, depth 3)
+    in full, one thread per host core."""
+    import oracle
+    from paper_2207_06649_b300 import scenegen as sg
+    oracle.build()
+    sc, pushes, seeds = sg.config_fixed()
+    envs = sc.gather([0] * len(pushes))
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    r = oracle.rollout(envs.box_offset, sg.state13(envs), envs.half, envs.mass, envs.mu, envs.target, pushes,
+                       depth=3, seeds=seeds, threads=cores)
+    dt = time.perf_counter() - t
+    es = int(r.steps.sum())
+    bs = int(sum(r.steps[e] * (envs.box_offset[e + 1] - envs.box_offset[e]) for e in range(len(pushes))))
+    print(json.dumps({"study": "cpu_baseline_config2", "kind": "oracle", "cores": cores, "seconds": dt,
+                      "env_steps": es, "env_steps_per_s": es / dt, "box_steps_per_s": bs / dt,
+                      "workload": "1024 clones of one 15-box scene, 1024 first pushes, depth 3 x 240 substeps",
+                      "invalid_starts": int(np.sum((r.flags & 2) != 0))}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.planning_study:
+        planning_study(a)
+    elif a.cpu_config2:
+        cpu_config2(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

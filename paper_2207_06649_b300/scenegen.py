@@ -214,7 +214,8 @@ def config_fixed(seed: int = 2, n_boxes: int = 15, n_envs: int = 1024):
     offset (e mod 16) in {-0.075 .. 0.075} step 0.01 m.  Seeds 1000+e drive the
     device-sampled pushes 2..D."""
     rng = np.random.default_rng(seed)
-    sc = make_scene(rng, n_boxes, region_half=0.11)
+    # a 0.28 m clutter square: large enough that all 15 boxes find a place
+    sc = make_scene(rng, n_boxes, region_half=0.14)
     pushes = []
     for e in range(n_envs):
         k, o = e // 16, e % 16
