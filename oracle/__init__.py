@@ -77,6 +77,7 @@ def lib():
         L.oracle_heightmap.argtypes = [C.c_int, C.c_int, vp, vp, C.c_int, C.c_int, C.c_double, C.c_double,
                                        C.c_double, vp]
         L.oracle_heightmap.restype = None
+        L.oracle_grasp_heightmap.argtypes = [P(Params), C.c_int, C.c_int, vp, vp, C.c_int, C.c_double]
         L.oracle_footprints.argtypes = [C.c_int, C.c_int, vp, vp, vp]
         _lib = L
     return _lib
@@ -243,6 +244,14 @@ def heightmap(state13, half, f32=True, cells=HM_CELLS, cell=HM_CELL, x0=HM_X0, y
     lib().oracle_heightmap(1 if f32 else 0, st.shape[0], _ptr(st), _ptr(half), cells, cells, x0, y0, cell,
                            _ptr(out))
     return out
+
+
+def grasp_heightmap(state13, half, target, depth=0.02, f32=True, prm: Params | None = None) -> bool:
+    """Heightmap form of the grasp test: finger tips `depth` below the target's top."""
+    prm = prm or params()
+    st, half = _f32(state13), _f32(half)
+    return bool(lib().oracle_grasp_heightmap(C.byref(prm), 1 if f32 else 0, st.shape[0], _ptr(st), _ptr(half),
+                                             int(target), float(depth)))
 
 
 def footprints(state13, half, f32=True):

@@ -354,6 +354,57 @@ void heightmap(int n, const T* x, const T* q, const T* h, int W, int H, T x0, T 
         }
 }
 
+// Heightmap form of the grasp test (the classifier of Sec. IV-B decides from the overhead
+// depth image; here the image decides by geometry).  Jaw angles, the opening condition
+// (i) and the two finger rectangles are those of the footprint test above.  A finger
+// rectangle is clear when no heightmap cell whose centre lies in it beyond the target's
+// side -- with p the centre relative to the rectangle centre, off - hl < s p.a <= off + hl
+// is replaced by -hl < p.a' <= hl along the rectangle's outward axis a' = s a, and
+// |p.b| <= hw -- is higher than the finger tips, which descend to
+// z_tip = top_t - depth (top_t = c_z + the target's vertical half extent).  Cells are
+// visited over the rectangle's bounding square with one cell of slack; the membership
+// test decides.
+template <typename T>
+bool graspable_hm(const T* map, int cells, T x0, T cellw, int n, const T* x, const T* q, const T* h, int t,
+                  const T* ca, const T* sa, int K, T W, T c, T f, T fw, T depth) {
+    const Foot<T> ft = footprint(x + 3 * t, q + 4 * t, h + 3 * t);
+    T R[9];
+    quat_to_R(q + 4 * t, R);
+    const T ez = (std::fabs(R[6]) * h[3 * t] + std::fabs(R[7]) * h[3 * t + 1]) + std::fabs(R[8]) * h[3 * t + 2];
+    const T z_tip = (x[3 * t + 2] + ez) - depth;
+    const T halfW = W * T(0.5), hfw = fw * T(0.5);
+    for (int k = 0; k < K; k++) {
+        const T ax = ca[k], ay = sa[k];
+        const T bx = -ay, by = ax;
+        const T wa = std::fabs(ft.ux * ax + ft.uy * ay) * ft.su + std::fabs(ft.vx * ax + ft.vy * ay) * ft.sv;
+        if (!((wa + c) * T(2) <= W)) continue;
+        const T off = ((wa + halfW) + f) * T(0.5);
+        const T hl = ((halfW + f) - wa) * T(0.5);
+        bool clear = true;
+        for (int s = 1; s >= -1 && clear; s -= 2) {
+            const T sax = T(s) * ax, say = T(s) * ay;
+            const T fcx = ft.cx + sax * off, fcy = ft.cy + say * off;
+            const T rx = std::fabs(sax) * hl + std::fabs(bx) * hfw, ry = std::fabs(say) * hl + std::fabs(by) * hfw;
+            const int i0 = std::max(0, (int)std::floor((fcx - rx - x0) / cellw) - 1);
+            const int i1 = std::min(cells - 1, (int)std::floor((fcx + rx - x0) / cellw) + 1);
+            const int j0 = std::max(0, (int)std::floor((fcy - ry - x0) / cellw) - 1);
+            const int j1 = std::min(cells - 1, (int)std::floor((fcy + ry - x0) / cellw) + 1);
+            for (int j = j0; j <= j1 && clear; j++)
+                for (int i = i0; i <= i1; i++) {
+                    const T px = (x0 + ((T)i + T(0.5)) * cellw) - fcx;
+                    const T py = (x0 + ((T)j + T(0.5)) * cellw) - fcy;
+                    const T pa = px * sax + py * say, pb = px * bx + py * by;
+                    if (pa > -hl && pa <= hl && std::fabs(pb) <= hfw && map[(size_t)j * cells + i] > z_tip) {
+                        clear = false;
+                        break;
+                    }
+                }
+        }
+        if (clear) return true;
+    }
+    return false;
+}
+
 // ----------------------------------------------------------------------------------
 // Double-precision engine
 // ----------------------------------------------------------------------------------
@@ -1325,6 +1376,34 @@ void oracle_heightmap(int f32, int n, const float* state13, const float* half, i
     };
     if (f32) run(0.0f);
     else run(0.0);
+}
+
+// Heightmap grasp decision for target t (binary32 twin when f32 != 0): the state's own
+// heightmap on the Sec. V-A grid, then the finger-rectangle test with tips `depth` below
+// the target's top.
+int oracle_grasp_heightmap(const oracle_params* P, int f32, int n, const float* state13, const float* half, int t,
+                           double depth) {
+    const int cells = 144;
+    auto run = [&](auto zero) {
+        using T = decltype(zero);
+        std::vector<T> x(3 * n), q(4 * n), h(3 * n), ca(P->grasp_angles), sa(P->grasp_angles), map(cells * cells);
+        for (int i = 0; i < n; i++) {
+            for (int k = 0; k < 3; k++) x[3 * i + k] = (T)state13[13 * i + k];
+            for (int k = 0; k < 4; k++) q[4 * i + k] = (T)state13[13 * i + 3 + k];
+            for (int k = 0; k < 3; k++) h[3 * i + k] = (T)half[3 * i + k];
+        }
+        for (int k = 0; k < P->grasp_angles; k++) {
+            const double th = k * M_PI / P->grasp_angles;
+            ca[k] = (T)(float)std::cos(th);
+            sa[k] = (T)(float)std::sin(th);
+        }
+        const T x0 = (T)-0.144f, cw = (T)0.002f;
+        heightmap<T>(n, x.data(), q.data(), h.data(), cells, cells, x0, x0, cw, map.data());
+        return graspable_hm<T>(map.data(), cells, x0, cw, n, x.data(), q.data(), h.data(), t, ca.data(), sa.data(),
+                               P->grasp_angles, (T)P->grasp_opening, (T)P->grasp_clearance, (T)P->finger_depth,
+                               (T)P->finger_width, (T)(float)depth) ? 1 : 0;
+    };
+    return f32 ? run(0.0f) : run(0.0);
 }
 
 }  // extern "C"

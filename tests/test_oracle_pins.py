@@ -607,3 +607,62 @@ def test_heightmap_clamps_at_the_table_and_is_empty_without_boxes(orc):
     st = np.stack([G.box_row(0.0, 0.0, 0.005)])      # half sunk: top at 0.025
     m = orc.heightmap(st, np.array([[0.02, 0.02, 0.02]]), f32=False)
     assert abs(m.max() - 0.025) <= 2e-9  # stored as float32
+
+
+# ------------------------------------------------------------------ heightmap grasp test
+def _ring(target_h, ring_h):
+    rows, halves = [(0, 0, target_h)], [[0.02, 0.02, target_h]]
+    for k in range(8):
+        a = k * math.pi / 4
+        d = 0.02 + 0.005 + 0.012
+        rows.append((d * math.cos(a) * (1.4 if k % 2 else 1), d * math.sin(a) * (1.4 if k % 2 else 1), ring_h,
+                     G.yaw_q(a)))
+        halves.append([0.012, 0.02, ring_h])
+    return _scene(rows, halves)
+
+
+@pytest.mark.parametrize("f32", [True, False])
+def test_heightmap_grasp_isolated_and_ringed(orc, f32):
+    st, half, t = _scene([(0, 0, 0.02)], [[0.02, 0.02, 0.02]])
+    assert orc.grasp_heightmap(st, half, t, f32=f32)
+    # a ring as tall as the target blocks every finger path (tips 2 cm below its top)
+    st, half, t = _ring(0.02, 0.02)
+    assert not orc.grasp_heightmap(st, half, t, f32=f32) and not orc.grasp(st, half, t, f32=f32)
+
+
+@pytest.mark.parametrize("f32", [True, False])
+def test_heightmap_grasp_passes_over_low_neighbours(orc, f32):
+    """A tall target (top 0.06 m) ringed by flat boxes (top 0.01 m): the footprint test
+    sees the ring and refuses, the heightmap test lets fingers that stop 2 cm below the
+    target's top pass over it; with tips 5.5 cm down the ring blocks again."""
+    st, half, t = _ring(0.03, 0.005)
+    assert not orc.grasp(st, half, t, f32=f32)
+    assert orc.grasp_heightmap(st, half, t, depth=0.02, f32=f32)
+    assert not orc.grasp_heightmap(st, half, t, depth=0.055, f32=f32)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_heightmap_grasp_is_monotone(orc, seed):
+    """Deeper finger tips can only block more, and removing other boxes can only free
+    paths (random clutter, every box as target)."""
+    sg = _sg_mod()
+    rng = np.random.default_rng(seed)
+    sc = sg.make_scene(rng, 12, half_lo=0.01, half_hi=0.03, yaw_hi=math.pi / 2, region_half=0.09)
+    st, half = sg.state13(sc), sc.half
+    n = len(st)
+    changed = 0
+    for t in range(n):
+        d1 = orc.grasp_heightmap(st, half, t, depth=0.005)
+        d2 = orc.grasp_heightmap(st, half, t, depth=0.02)
+        d3 = orc.grasp_heightmap(st, half, t, depth=0.06)
+        assert (d3 <= d2 <= d1)
+        changed += int(d1 != d3)
+        keep = [t] + [o for o in range(n) if o != t and rng.random() < 0.5]
+        sub = orc.grasp_heightmap(st[keep], half[keep], 0, depth=0.02)
+        assert sub >= d2
+    assert changed > 0
+
+
+def _sg_mod():
+    from paper_2207_06649_b300 import scenegen
+    return scenegen
