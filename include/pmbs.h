@@ -282,6 +282,17 @@ pmbs_status pmbs_render_heightmaps_device(pmbs_ctx* ctx, int n_envs, const int32
                                           const float* d_states, const float* d_half, float* d_out);
 pmbs_status pmbs_query_heightmaps(pmbs_ctx* ctx, int64_t batch, float* out);
 
+/* Heightmap form of the grasp test (the paper's classifier decides graspability from the
+ * overhead depth image, Sec. IV-B; here the heightmap decides by geometry): for each
+ * environment of a state snapshot (arrays as pmbs_eval_grasp), the target's heightmap is
+ * rendered as above and out[e] = 1 when, for some jaw angle, the opening condition and
+ * both finger rectangles of the footprint test hold with the rectangles checked against
+ * the map: no cell whose centre lies in a rectangle beyond the target's side is higher
+ * than the finger tips, `depth` m below the target's top.  Bit-exact in binary32.  Box
+ * counts 1..64, targets in range and depth >= 0, else PMBS_E_INVALID; synchronous. */
+pmbs_status pmbs_eval_grasp_heightmap(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                                      const float* half_ext, const int32_t* target, float depth, uint8_t* out);
+
 /* Launch shape the context uses for a batch whose largest scene has max_boxes boxes:
  * lanes per environment, warps per block, contact point slots and manifolds kept in
  * shared memory per environment, and shared bytes per block.  Chosen by the tuning rule

@@ -589,6 +589,68 @@ __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_env
     }
 }
 
+// Heightmap form of the grasp test, one warp per environment, one (angle, side) pair per
+// lane: the jaw angles, the opening condition and the finger rectangles of the footprint
+// test; a rectangle is clear when no map cell whose centre lies in it beyond the target's
+// side is higher than the finger tips, `depth` below the target's top.  Cells are visited
+// over the rectangle's bounding square with one cell of slack; the membership test, in
+// fixed-order binary32, decides.
+__global__ void __launch_bounds__(128) grasp_hm_kernel(const HMCsr src, const int32_t* target, const float* maps,
+                                                       int n_envs, SimConst C, float depth, uint8_t* out) {
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (e >= n_envs) return;
+    const int t = target[e];
+    const float* s = src.st(e, t);
+    const float* hh = src.h(e, t);
+    float R[9];
+    quat_to_R_exact(s[3], s[4], s[5], s[6], R);
+    const Foot ft = footprint_exact(s[0], s[1], R, hh[0], hh[1], hh[2]);
+    const float z_tip = xs(xa(s[2], aabb_half_exact(R + 6, hh[0], hh[1], hh[2])), depth);
+    const float halfW = xm(C.grasp_W, 0.5f), hfw = xm(C.grasp_fw, 0.5f);
+    const float* map = maps + (size_t)e * kHMCells * kHMCells;
+    bool any = false;
+    for (int sb = 0; sb < 2 * C.grasp_K; sb += 32) {
+        const int slot = sb + lane;
+        const int k = slot >> 1;
+        const float sg = (slot & 1) ? -1.f : 1.f;
+        bool ok = false;
+        if (k < C.grasp_K) {
+            const float ax = C.gcos[k], ay = C.gsin[k];
+            const float bx = -ay, by = ax;
+            const float wa = xa(xm(fabsf(xdot2(ft.ux, ft.uy, ax, ay)), ft.su), xm(fabsf(xdot2(ft.vx, ft.vy, ax, ay)), ft.sv));
+            if (xm(xa(wa, C.grasp_c), 2.f) <= C.grasp_W) {
+                const float off = xm(xa(xa(wa, halfW), C.grasp_f), 0.5f);
+                const float hl = xm(xs(xa(halfW, C.grasp_f), wa), 0.5f);
+                const float sax = sg * ax, say = sg * ay;
+                const float fcx = xa(ft.cx, xm(sax, off)), fcy = xa(ft.cy, xm(say, off));
+                const float rx = fabsf(sax) * hl + fabsf(bx) * hfw, ry = fabsf(say) * hl + fabsf(by) * hfw;
+                auto cell_of = [](float v) {  // clamped before the conversion to int
+                    return (int)floorf(fminf(fmaxf((v - kHMOrigin) / kHMCell, -4.f), (float)kHMCells + 4.f));
+                };
+                const int i0 = max(0, cell_of(fcx - rx) - 1), i1 = min(kHMCells - 1, cell_of(fcx + rx) + 1);
+                const int j0 = max(0, cell_of(fcy - ry) - 1), j1 = min(kHMCells - 1, cell_of(fcy + ry) + 1);
+                ok = true;
+                for (int j = j0; j <= j1 && ok; j++) {
+                    const float py = xs(xa(kHMOrigin, xm(xa((float)j, 0.5f), kHMCell)), fcy);
+                    for (int i = i0; i <= i1; i++) {
+                        const float px = xs(xa(kHMOrigin, xm(xa((float)i, 0.5f), kHMCell)), fcx);
+                        const float pa = xa(xm(px, sax), xm(py, say)), pb = xa(xm(px, bx), xm(py, by));
+                        if (pa > -hl && pa <= hl && fabsf(pb) <= hfw && map[j * kHMCells + i] > z_tip) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        // both sides of one angle sit on neighbouring lanes
+        const bool partner = __shfl_xor_sync(0xffffffffu, ok, 1) != 0;
+        any = any || __any_sync(0xffffffffu, ok && partner);
+    }
+    if (lane == 0) out[e] = any ? 1 : 0;
+}
+
 // Scene table update: table[ids[i]] = desc[i].
 __global__ void scatter_desc_kernel(int n, const int32_t* ids, const SceneDesc* desc, SceneDesc* table) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1930,6 +1992,58 @@ pmbs_status pmbs_render_heightmaps(pmbs_ctx* ctx, int n_envs, const int32_t* box
     else cudaStreamSynchronize(ctx->stream);
     ctx->arena.release(boff, sz);
     if (e != cudaSuccess) return fail(ctx, PMBS_E_CUDA, std::string("heightmaps: ") + cudaGetErrorString(e));
+    return PMBS_OK;
+}
+
+pmbs_status pmbs_eval_grasp_heightmap(pmbs_ctx* ctx, int n_envs, const int32_t* box_offset, const float* states,
+                                      const float* half_ext, const int32_t* target, float depth, uint8_t* out) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (n_envs < 0 || (n_envs > 0 && (!box_offset || !states || !half_ext || !target || !out)) || !(depth >= 0.f))
+        return fail(ctx, PMBS_E_INVALID, "bad arguments");
+    if (n_envs == 0) return PMBS_OK;
+    for (int e = 0; e < n_envs; e++) {
+        const int n = box_offset[e + 1] - box_offset[e];
+        if (n < 1 || n > kMaxBoxes) return fail(ctx, PMBS_E_INVALID, "box count out of range");
+        if (target[e] < 0 || target[e] >= n) return fail(ctx, PMBS_E_INVALID, "target out of range");
+    }
+    CU(cudaSetDevice(ctx->device));
+    const int B = box_offset[n_envs] - box_offset[0];
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_off = 0, o_st = al(sizeof(int32_t) * (n_envs + 1)), o_h = o_st + al(sizeof(float) * 13 * B);
+    const size_t o_t = o_h + al(sizeof(float) * 3 * B), o_map = o_t + al(sizeof(int32_t) * n_envs);
+    const size_t o_out = o_map + al(sizeof(float) * kHMCells * kHMCells * (size_t)n_envs);
+    const size_t sz = o_out + al(n_envs);
+    const size_t boff = ctx->arena.alloc(sz);
+    if (boff == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "grasp staging does not fit");
+    char* base = (char*)arena_ptr(ctx, boff);
+    cudaError_t e = cudaMemcpyAsync(base + o_off, box_offset, sizeof(int32_t) * (n_envs + 1), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_st, states + (size_t)13 * box_offset[0], sizeof(float) * 13 * B,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_h, half_ext + (size_t)3 * box_offset[0], sizeof(float) * 3 * B,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_t, target, sizeof(int32_t) * n_envs, cudaMemcpyHostToDevice, ctx->stream);
+    const HMCsr src{(const int32_t*)(base + o_off), (const float*)(base + o_st), (const float*)(base + o_h)};
+    if (e == cudaSuccess) {
+        heightmap_kernel<HMCsr><<<n_envs, 512, kHMSmem, ctx->stream>>>(src, n_envs, (float*)(base + o_map));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        grasp_hm_kernel<<<(n_envs + 3) / 4, 128, 0, ctx->stream>>>(src, (const int32_t*)(base + o_t),
+                                                                   (const float*)(base + o_map), n_envs, ctx->C, depth,
+                                                                   (uint8_t*)(base + o_out));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, base + o_out, n_envs, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    else cudaStreamSynchronize(ctx->stream);
+    ctx->arena.release(boff, sz);
+    if (e != cudaSuccess) return fail(ctx, PMBS_E_CUDA, std::string("grasp heightmap: ") + cudaGetErrorString(e));
     return PMBS_OK;
 }
 

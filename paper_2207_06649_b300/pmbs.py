@@ -31,7 +31,8 @@ EXPORTED = ["pmbs_default_config", "pmbs_create", "pmbs_create_with_arena", "pmb
             "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_rollout_noalloc",
             "pmbs_step_graph", "pmbs_autotune", "pmbs_server_create", "pmbs_server_submit",
             "pmbs_server_wait", "pmbs_server_stats", "pmbs_server_cancel", "pmbs_server_destroy",
-            "pmbs_render_heightmaps", "pmbs_render_heightmaps_device", "pmbs_query_heightmaps"]
+            "pmbs_render_heightmaps", "pmbs_render_heightmaps_device", "pmbs_query_heightmaps",
+            "pmbs_eval_grasp_heightmap"]
 
 
 class pmbs_config(C.Structure):
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = True):
         "pmbs_render_heightmaps": ([vp, i32, vp, vp, vp, vp], i32),
         "pmbs_render_heightmaps_device": ([vp, i32, vp, vp, vp, vp], i32),
         "pmbs_query_heightmaps": ([vp, C.c_int64, vp], i32),
+        "pmbs_eval_grasp_heightmap": ([vp, i32, vp, vp, vp, vp, C.c_float, vp], i32),
         "pmbs_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -347,6 +349,15 @@ class Engine:
         self._check(self.lib.pmbs_render_heightmaps_device(self.ctx, n_envs, C.c_void_p(d_box_offset),
                                                            C.c_void_p(d_states), C.c_void_p(d_half),
                                                            C.c_void_p(d_out)), "pmbs_render_heightmaps_device")
+
+    def eval_grasp_heightmap(self, box_offset, states, half, target, depth=0.02):
+        box_offset, states, half = self._csr(box_offset, states, half)
+        target = np.ascontiguousarray(target, np.int32)
+        ne = box_offset.shape[0] - 1
+        out = np.zeros(max(ne, 1), np.uint8)
+        self._check(self.lib.pmbs_eval_grasp_heightmap(self.ctx, ne, _p(box_offset), _p(states), _p(half), _p(target),
+                                                       float(depth), _p(out)), "pmbs_eval_grasp_heightmap")
+        return out[:ne].astype(bool)
 
     def query_heightmaps(self, batch):
         ne, _ = self.batch_info(batch)

@@ -110,3 +110,25 @@ def test_heightmaps_full_workload_sampled(eng, orc):
     for e in np.random.default_rng(0).choice(4096, size=24, replace=False):
         a, c = scenes.box_offset[e], scenes.box_offset[e + 1]
         assert _bits_equal(out[e], orc.heightmap(st[a:c], scenes.half[a:c], f32=True)), e
+
+
+@pytest.mark.parametrize("depth", [0.005, 0.02, 0.06])
+def test_heightmap_grasp_decisions_bit_exact(eng, orc, depth):
+    """Decisions of the heightmap grasp test on clutter (a random box of each scene as the
+    target, poses jittered) equal the oracle's binary32 twin, and both outcomes occur."""
+    sg = _sg()
+    rng = np.random.default_rng(int(depth * 1000))
+    parts = []
+    for _ in range(96):
+        n = int(rng.integers(3, 20))
+        parts.append(sg.make_scene(rng, n, half_lo=0.01, half_hi=0.035, yaw_hi=np.pi / 2,
+                                   density_scale=rng.uniform(0.3, 0.6)))
+    sc = sg.concat(parts)
+    st = sg.state13(sc).astype(np.float32)
+    st[:, :2] += rng.normal(scale=0.002, size=(len(st), 2)).astype(np.float32)
+    tgt = np.array([rng.integers(0, sc.box_offset[e + 1] - sc.box_offset[e]) for e in range(sc.n_scenes)], np.int32)
+    got = eng.eval_grasp_heightmap(sc.box_offset, st, sc.half, tgt, depth=depth)
+    want = [orc.grasp_heightmap(st[sc.box_offset[e]:sc.box_offset[e + 1]], sc.half[sc.box_offset[e]:sc.box_offset[e + 1]],
+                                int(tgt[e]), depth=depth, f32=True) for e in range(sc.n_scenes)]
+    assert got.tolist() == want
+    assert 0 < sum(want) < len(want)
