@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("substeps_per_push", C.c_int32), ("pgs_iters", C.c_int32),
                 ("point_cap", C.c_int32), ("manifold_cap", C.c_int32), ("pair_cap", C.c_int32),
                 ("grasp_angles", C.c_int32), ("sample_attempts", C.c_int32),
-                ("contour_points", C.c_int32)]
+                ("contour_points", C.c_int32), ("warm_start", C.c_int32), ("warm_tolerance", C.c_double)]
 
 
 def build(force: bool = False) -> str:

@@ -52,6 +52,8 @@ typedef struct {
     int32_t substeps_per_push, pgs_iters;
     int32_t point_cap, manifold_cap, pair_cap;
     int32_t grasp_angles, sample_attempts, contour_points;
+    int32_t warm_start;        // 0: impulses start at zero every substep; 1: carried over
+    double warm_tolerance;     // match distance of a carried-over contact point (m)
 } oracle_params;
 }
 
@@ -455,8 +457,15 @@ struct PushState {
     int moving = 0;
 };
 
+// A contact point carried to the next substep (warm start): its offset in the frame of
+// the manifold's key body (A when dynamic, else B), its normal impulse and its friction
+// impulse as a world vector (the tangent basis is rebuilt every substep).
+struct WarmPoint { V3 loc; double ln; V3 Pt; };
+struct WarmManifold { int A, B, np; WarmPoint p[4]; };
+
 struct Env {
     std::vector<Body> b;
+    std::vector<WarmManifold> warm;  // last substep's manifolds (warm start only)
     int target = 0;
     PushState push;
     V3 P{0, 0, 0}, V{0, 0, 0};  // pusher position (segment base xy) and velocity
@@ -1013,6 +1022,73 @@ void pgs(Env& E, std::vector<Manifold>& ms, int ncol, int iters, bool reverse_wi
         }
 }
 
+// Warm start (a reading beyond the paper, off by default): a new contact point takes the
+// impulses of the nearest point of the same body pair in the previous substep when the
+// two offsets, written in the key body's frame, lie within the tolerance (each old point
+// used once, new points in order); the friction part is the old world friction vector
+// projected on the new tangents.  The carried impulses are applied to the bodies before
+// the first iteration, manifold by manifold in colour order.
+inline V3 key_local(const Env& E, const Manifold& M, const Contact& C) {
+    const bool a = M.A >= 0;
+    const Body& k = E.b[a ? M.A : M.B];
+    const V3 r = a ? C.rA : C.rB;
+    return {k.R[0] * r.x + k.R[3] * r.y + k.R[6] * r.z, k.R[1] * r.x + k.R[4] * r.y + k.R[7] * r.z,
+            k.R[2] * r.x + k.R[5] * r.y + k.R[8] * r.z};
+}
+
+void warm_start(Env& E, std::vector<Manifold>& ms, int ncol, const oracle_params& P) {
+    for (Manifold& M : ms) {
+        const WarmManifold* W = nullptr;
+        for (const WarmManifold& w : E.warm)
+            if (w.A == M.A && w.B == M.B) { W = &w; break; }
+        if (!W) continue;
+        bool used[4] = {false, false, false, false};
+        for (int p = 0; p < M.np; p++) {
+            Contact& C = M.c[p];
+            const V3 loc = key_local(E, M, C);
+            int best = -1;
+            double bd = P.warm_tolerance * P.warm_tolerance;
+            for (int q = 0; q < W->np; q++) {
+                if (used[q]) continue;
+                const V3 d = loc - W->p[q].loc;
+                const double d2 = dot(d, d);
+                if (d2 <= bd) { bd = d2; best = q; }
+            }
+            if (best < 0) continue;
+            used[best] = true;
+            C.ln = W->p[best].ln;
+            C.lt1 = dot(W->p[best].Pt, M.t1);
+            C.lt2 = dot(W->p[best].Pt, M.t2);
+        }
+    }
+    for (int c = 0; c < ncol; c++)
+        for (Manifold& M : ms) {
+            if (M.colour != c) continue;
+            for (int p = 0; p < M.np; p++) {
+                const Contact& C = M.c[p];
+                apply_impulse(E, M, C, (M.n * C.ln + M.t1 * C.lt1) + M.t2 * C.lt2);
+            }
+        }
+}
+
+void save_warm(Env& E, const std::vector<Manifold>& ms) {
+    E.warm.clear();
+    for (const Manifold& M : ms) {
+        if (M.colour < 0) continue;
+        WarmManifold w;
+        w.A = M.A;
+        w.B = M.B;
+        w.np = M.np;
+        for (int p = 0; p < M.np; p++) {
+            const Contact& C = M.c[p];
+            w.p[p].loc = key_local(E, M, C);
+            w.p[p].ln = C.ln;
+            w.p[p].Pt = M.t1 * C.lt1 + M.t2 * C.lt2;
+        }
+        E.warm.push_back(w);
+    }
+}
+
 // Semi-implicit Euler: x += v dt; q += dt/2 (0, w) (x) q, renormalised.
 void integrate(Env& E, const oracle_params& P) {
     const double dt = P.dt;
@@ -1038,7 +1114,9 @@ void substep(Env& E, const oracle_params& P, int s, bool reverse_within_colour =
     prepare(E, ms, P);
     const int ncol = colour_manifolds(E, ms);
     E.ev[EV_COLOURS] += ncol;
+    if (P.warm_start) warm_start(E, ms, ncol, P);
     pgs(E, ms, ncol, P.pgs_iters, reverse_within_colour);
+    if (P.warm_start) save_warm(E, ms);
     integrate(E, P);
     E.ev[EV_SUBSTEPS]++;
     E.ev[EV_BOX_STEPS] += E.b.size();
@@ -1141,6 +1219,7 @@ void oracle_default_params(oracle_params* p) {
     p->substeps_per_push = 240; p->pgs_iters = 10;
     p->point_cap = 512; p->manifold_cap = 256; p->pair_cap = 1024;
     p->grasp_angles = 16; p->sample_attempts = 8; p->contour_points = 16;
+    p->warm_start = 0; p->warm_tolerance = 2e-3;
 }
 
 uint64_t oracle_splitmix64(uint64_t* state) { return splitmix64_next(*state); }
