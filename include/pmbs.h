@@ -110,6 +110,10 @@ typedef struct {
     float max_initial_penetration; /* 1e-3 m: scenes with deeper box-box overlap are refused
                                       (child states registered by pmbs_query_cost are the
                                       engine's own output and are not re-checked) */
+    int warm_start;             /* 0 (default): contact impulses start at zero every substep;
+                                   1: a point takes the impulses of the nearest point of the
+                                   same body pair in the previous substep (see DESIGN) */
+    float warm_tolerance;       /* 2e-3 m: match distance for warm starting */
 } pmbs_config;
 
 /* Fill *cfg with the defaults listed above.  Never fails. */
@@ -372,7 +376,8 @@ void pmbs_server_destroy(pmbs_server* server);
  * cfg->max_boxes_per_env <= 64.  Larger requests return PMBS_E_INVALID before any GPU
  * work.  The first call on a device looks up that array's device address (and sets the
  * kernel's shared-memory limit); make that first call before any stream capture.  The
- * call synchronises cuda_stream and returns PMBS_OK, PMBS_E_INVALID (bad argument, or
+ * call synchronises cuda_stream and returns PMBS_OK, PMBS_E_INVALID (bad argument,
+ * cfg->warm_start set (its caches need memory), or
  * an environment with a box count outside 1..max_boxes_per_env or a target out of range:
  * such environments are not simulated and their outputs are undefined), PMBS_E_TIMEOUT
  * or PMBS_E_CUDA.  Every call shares the one array and starts by clearing what must start

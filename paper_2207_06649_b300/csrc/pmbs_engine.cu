@@ -81,6 +81,8 @@ struct RolloutArgs {
     int scratch_f4_per_warp;
     long long watchdog_cycles;  // per environment and launch; exceeded -> counters[4] = 1
     int* watchdog_flag;
+    float4* warm;               // warm-start caches, warm_f4_per_env per environment (or null)
+    size_t warm_f4_per_env;
 };
 
 // ------------------------------------------------------------------ device: environments
@@ -140,7 +142,7 @@ __device__ __forceinline__ void store_state(const WarpMem& W, int n, float* dst,
 // One substep of the group's environment (on = false: the group only takes part in the
 // warp's collectives).  Returns true on a cap overflow.
 __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, int n_env, bool on, const Pusher& pu,
-                                        int s, const Grp& g) {
+                                        int s, const Grp& g, float4* warm, int& warm_n) {
     const SimConst& C = a.C;
     const int n = on ? n_env : 0;
     const int done = s < pu.moving ? s : pu.moving;
@@ -179,8 +181,13 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
     }
     prepare(W, g, on, C);
     ovf |= colour_manifolds(W, n, g, on);
+    if (C.warm && a.warm) warm_start(W, g, on, C, warm, warm_n);
     int bb_visits = 0;
     const int visits = pgs(W, g, on, C.iters, V, bb_visits);
+    if (C.warm && a.warm) {
+        const int m = warm_save(W, g, on, warm);
+        if (on) warm_n = m;
+    }
     integrate(W, n, g, C.dt);
     const int v_all = g.sum(visits), v_bb = g.sum(bb_visits);
     if (on && g.gl == 0) {
@@ -281,7 +288,8 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
         // 3. one substep
         const bool run = active && !pg.done && pg.s < C.substeps && budget > 0;
         const Pusher pu = make_pusher(C, pg.push, pg.noop != 0);
-        ovf |= substep(a, W, ei.n, run, pu, pg.s, g);
+        ovf |= substep(a, W, ei.n, run, pu, pg.s, g, a.warm ? a.warm + (size_t)(e < 0 ? 0 : e) * a.warm_f4_per_env : nullptr,
+                       pg.pad[0]);
         // bounded run time per environment and launch (the shuffle runs in every lane)
         const bool late = g.bcast((int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
         if (run) {
@@ -834,6 +842,7 @@ struct Batch {
     uint8_t* flags = nullptr;
     int32_t* steps = nullptr;
     unsigned long long* events = nullptr;
+    float4* warm = nullptr;         // warm-start caches (cfg.warm_start), one per environment
     bool finished = false;
     int G = 32, wpb = 4, Ms = 0;
     cudaStream_t stream = nullptr;  // stream of this batch's launches (the context's by default)
@@ -906,6 +915,8 @@ void fill_const(const pmbs_config& c, SimConst& C) {
     C.sample_clear = c.sample_clearance;
     C.substeps = c.substeps_per_push;
     C.iters = c.pgs_iters;
+    C.warm = c.warm_start ? 1 : 0;
+    C.warm_tol2 = c.warm_tolerance * c.warm_tolerance;
     C.grasp_K = c.grasp_angles;
     C.attempts = c.sample_attempts;
     C.npts = c.contour_points;
@@ -992,6 +1003,7 @@ pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, s
         c.sample_attempts > 32 || c.contour_points < 1 || c.contact_cap < 4 || c.manifold_cap < 1 ||
         c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096 || !(c.pusher_speed > 0) ||
         !(c.pusher_radius > 0) || !(c.watchdog_ms > 0) || !(c.max_initial_penetration >= 0) ||
+        !(c.warm_start == 0 || c.warm_start == 1) || !(c.warm_tolerance >= 0) ||
         !(c.lanes_per_env == 0 || c.lanes_per_env == 8 || c.lanes_per_env == 16 ||
                                     c.lanes_per_env == 32))
         return PMBS_E_INVALID;
@@ -1104,6 +1116,8 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
                  o_child = take(sizeof(float) * 13 * std::max(boxes, (size_t)1)), o_cost = take(sizeof(int32_t) * ne),
                  o_rew = take(sizeof(float) * ne), o_flags = take(ne), o_steps = take(sizeof(int32_t) * ne),
                  o_ev = take(sizeof(unsigned long long) * kNumEvents * ne);
+    const size_t warm_f4 = (size_t)kWarmF4 * ctx->cfg.manifold_cap;
+    const size_t o_warm = ctx->cfg.warm_start ? take(sizeof(float4) * warm_f4 * ne) : 0;
     b.off = ctx->arena.alloc(sz);
     if (b.off == SIZE_MAX) return fail(ctx, PMBS_E_OOM, "batch does not fit in the device arena");
     b.bytes = sz;
@@ -1122,6 +1136,7 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
     b.flags = (uint8_t*)(base + o_flags);
     b.steps = (int32_t*)(base + o_steps);
     b.events = (unsigned long long*)(base + o_ev);
+    b.warm = ctx->cfg.warm_start ? (float4*)(base + o_warm) : nullptr;
     auto bail = [&](const char* what, cudaError_t e) {
         ctx->arena.release(b.off, b.bytes);
         return fail(ctx, PMBS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -1216,6 +1231,8 @@ pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaStream
     a.scratch_f4_per_warp = scratch_f4_per_warp(c.manifold_cap);
     a.watchdog_cycles = (long long)((double)c.watchdog_ms * 2.0e6);  // SM cycles at up to 2 GHz
     a.watchdog_flag = b.counters + 4;
+    a.warm = b.warm;
+    a.warm_f4_per_env = (size_t)kWarmF4 * c.manifold_cap;
     CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), stream));
     rollout_kernel<<<blocks, threads, smem, stream>>>(a);
     CU(cudaGetLastError());
@@ -1463,6 +1480,8 @@ void pmbs_default_config(pmbs_config* c) {
     c->smem_manifolds = -1;
     c->watchdog_ms = 10000.f;
     c->max_initial_penetration = 1e-3f;
+    c->warm_start = 0;
+    c->warm_tolerance = 2e-3f;
 }
 
 pmbs_status pmbs_create(const pmbs_config* cfg, void* cuda_stream, pmbs_ctx** out) {
@@ -2575,7 +2594,7 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     if (n_envs < 0 || n_envs > kNoAllocMaxEnvs || depth < 1 || depth > 64 || c.max_boxes_per_env < 1 ||
         c.max_boxes_per_env > kMaxBoxes || c.device < 0 || c.device >= kNoAllocMaxDevices || c.grasp_angles < 1 ||
         c.grasp_angles > 32 || c.sample_attempts < 1 || c.sample_attempts > 32 || c.contact_cap < 4 ||
-        c.manifold_cap < 1 || c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096)
+        c.manifold_cap < 1 || c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096 || c.warm_start)
         return PMBS_E_INVALID;
     if (n_envs == 0) return PMBS_OK;
     if (!d_box_offset || !d_records || !d_target || !d_first_push || (!d_seeds && depth > 1) || !d_state_out ||
@@ -2669,6 +2688,8 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     a.scratch_f4_per_warp = f4_per_warp;
     a.watchdog_cycles = (long long)((double)c.watchdog_ms * 2.0e6);
     a.watchdog_flag = counters + 4;
+    a.warm = nullptr;  // no room for caches in the fixed scratch: warm start is refused above
+    a.warm_f4_per_env = 0;
     rollout_kernel<<<blocks, 32 * wpb, smem, stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;
     int host_cnt[8];

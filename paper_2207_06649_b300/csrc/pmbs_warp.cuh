@@ -37,6 +37,8 @@ struct SimConst {
     float grasp_W, grasp_c, grasp_f, grasp_fw;
     float margin, slop, baumgarte, sample_clear;
     int substeps, iters, grasp_K, attempts, npts;
+    int warm;         // carry contact impulses over substeps
+    float warm_tol2;  // squared match distance
     int Pcap, Mcap, pair_cap;
     float gcos[32], gsin[32];
 };
@@ -746,6 +748,140 @@ __device__ __forceinline__ int pgs(const WarpMem& W, const Grp& g, bool on, int 
         }
     }
     return visits;
+}
+
+// ------------------------------------------------------------------ warm start (option)
+// Cache record of one manifold (kWarmF4 float4 in global memory, per environment):
+// [0] = (body-pair key A | B << 8, np, -, -) as integer bits; point p: [1 + 2p] =
+// (offset in the key body's frame, lambda_n), [2 + 2p] = (world friction impulse, -).
+// The key body is A when dynamic, else B.
+constexpr int kWarmF4 = 9;
+
+__device__ __forceinline__ float3 key_local(const WarpMem& W, int kb, float3 r) {
+    const int NB = W.NB();
+    const float* R = W.R().ptr();
+    return f3(R[kb] * r.x + R[3 * NB + kb] * r.y + R[6 * NB + kb] * r.z,
+              R[NB + kb] * r.x + R[4 * NB + kb] * r.y + R[7 * NB + kb] * r.z,
+              R[2 * NB + kb] * r.x + R[5 * NB + kb] * r.y + R[8 * NB + kb] * r.z);
+}
+
+// A new point takes the impulses of the nearest unused point of the same body pair in the
+// previous substep's cache within the tolerance (new points in order; the friction
+// vector is projected on the new tangents); then the carried impulses are applied to the
+// bodies, colour by colour (within a colour the manifolds share no dynamic body).
+__device__ __forceinline__ void warm_start(const WarpMem& W, const Grp& g, bool on, const SimConst& C,
+                                           const float4* cache, int Mold) {
+    const int M = on ? W.scal()[3] : 0;
+    for (int m = g.gl; m < M; m += g.G) {
+        if (W.mcol()[m] == 255) continue;
+        const CRef r = cref(W, m);
+        const float4 h1 = r.f(1), h2 = r.f(2);
+        const float3 t1 = f3(h1.x, h1.y, h1.z), t2 = f3(h2.x, h2.y, h2.z);
+        const int ids = __float_as_int(h1.w);
+        const int A = ids & 255, B = (ids >> 8) & 255, np = (ids >> 16) & 255;
+        const int key = A | (B << 8);
+        int om = -1;
+        for (int q = 0; q < Mold; q++)
+            if (__float_as_int(cache[(size_t)q * kWarmF4].x) == key) {
+                om = q;
+                break;
+            }
+        if (om < 0) continue;
+        const float4* rec = cache + (size_t)om * kWarmF4;
+        const int onp = __float_as_int(rec[0].y);
+        const bool kA = A < kPusher;
+        const int kb = kA ? A : B;
+        unsigned used = 0u;
+        for (int p = 0; p < np; p++) {
+            const float4 q = kA ? r.pt(p, 0) : r.pt(p, 1);
+            const float3 loc = key_local(W, kb, f3(q.x, q.y, q.z));
+            int best = -1;
+            float bd = C.warm_tol2;
+            for (int o = 0; o < onp; o++) {
+                if (used >> o & 1u) continue;
+                const float4 ol = rec[1 + 2 * o];
+                const float3 d = loc - f3(ol.x, ol.y, ol.z);
+                const float d2 = dot3(d, d);
+                if (d2 <= bd) {
+                    bd = d2;
+                    best = o;
+                }
+            }
+            if (best < 0) continue;
+            used |= 1u << best;
+            const float4 ol = rec[1 + 2 * best], op = rec[2 + 2 * best];
+            const float3 Pt = f3(op.x, op.y, op.z);
+            float4 q2 = r.pt(p, 2);
+            q2.x = ol.w;
+            q2.y = dot3(Pt, t1);
+            q2.z = dot3(Pt, t2);
+            r.pt(p, 2) = q2;
+        }
+    }
+    __syncwarp();
+    const int ncol = on ? W.scal()[5] : 0;
+    const int cw = wmax(ncol);
+    for (int c = 0; c < cw; c++) {
+        const int a = c < ncol ? (int)W.cstart()[c] : 0, b = c < ncol ? (int)W.cstart()[c + 1] : 0;
+        for (int k = a + g.gl; k < b; k += g.G) {
+            const CRef r = cref(W, W.order()[k]);
+            const float4 h0 = r.f(0), h1 = r.f(1), h2 = r.f(2);
+            const float3 n = f3(h0.x, h0.y, h0.z), t1 = f3(h1.x, h1.y, h1.z), t2 = f3(h2.x, h2.y, h2.z);
+            const int ids = __float_as_int(h1.w);
+            const int A = ids & 255, B = (ids >> 8) & 255, np = (ids >> 16) & 255;
+            float3 PA = f3(0.f, 0.f, 0.f), LA = PA, LB = PA;
+            for (int p = 0; p < np; p++) {
+                const float4 q0 = r.pt(p, 0), q1 = r.pt(p, 1), q2 = r.pt(p, 2);
+                const float3 P = (n * q2.x + t1 * q2.y) + t2 * q2.z;
+                PA = PA + P;
+                LA = LA + cross3(f3(q0.x, q0.y, q0.z), P);
+                LB = LB + cross3(f3(q1.x, q1.y, q1.z), P);
+            }
+            if (A < kPusher) {
+                const float4 v = W.bv()[A], w = W.bw()[A];
+                const float3 nv = f3(v.x, v.y, v.z) - PA * v.w;
+                const float3 nw = f3(w.x, w.y, w.z) - sym_mul(W.bI0()[A], W.bI1()[A], LA);
+                W.bv()[A] = make_float4(nv.x, nv.y, nv.z, v.w);
+                W.bw()[A] = make_float4(nw.x, nw.y, nw.z, w.w);
+            }
+            if (B < kPusher) {
+                const float4 v = W.bv()[B], w = W.bw()[B];
+                const float3 nv = f3(v.x, v.y, v.z) + PA * v.w;
+                const float3 nw = f3(w.x, w.y, w.z) + sym_mul(W.bI0()[B], W.bI1()[B], LB);
+                W.bv()[B] = make_float4(nv.x, nv.y, nv.z, v.w);
+                W.bw()[B] = make_float4(nw.x, nw.y, nw.z, w.w);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Cache this substep's manifolds (before integration, so offsets are taken in the frames
+// the next substep's contacts will be compared in after their own update).  Returns the
+// number of records (manifolds dropped by the colour cap are recorded with no points).
+__device__ __forceinline__ int warm_save(const WarpMem& W, const Grp& g, bool on, float4* cache) {
+    const int M = on ? W.scal()[3] : 0;
+    for (int m = g.gl; m < M; m += g.G) {
+        const CRef r = cref(W, m);
+        const float4 h1 = r.f(1), h2 = r.f(2);
+        const float3 t1 = f3(h1.x, h1.y, h1.z), t2 = f3(h2.x, h2.y, h2.z);
+        const int ids = __float_as_int(h1.w);
+        const int A = ids & 255, B = (ids >> 8) & 255;
+        const int np = W.mcol()[m] == 255 ? 0 : (ids >> 16) & 255;
+        float4* rec = cache + (size_t)m * kWarmF4;
+        rec[0] = make_float4(__int_as_float(A | (B << 8)), __int_as_float(np), 0.f, 0.f);
+        const bool kA = A < kPusher;
+        const int kb = kA ? A : B;
+        for (int p = 0; p < np; p++) {
+            const float4 q = kA ? r.pt(p, 0) : r.pt(p, 1), q2 = r.pt(p, 2);
+            const float3 loc = key_local(W, kb, f3(q.x, q.y, q.z));
+            const float3 Pt = t1 * q2.y + t2 * q2.z;
+            rec[1 + 2 * p] = make_float4(loc.x, loc.y, loc.z, q2.x);
+            rec[2 + 2 * p] = make_float4(Pt.x, Pt.y, Pt.z, 0.f);
+        }
+    }
+    __syncwarp();
+    return M;
 }
 
 // ------------------------------------------------------------------ integration

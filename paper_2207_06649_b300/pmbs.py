@@ -49,7 +49,8 @@ class pmbs_config(C.Structure):
                 ("pair_cap", C.c_int), ("lanes_per_env", C.c_int), ("warps_per_block", C.c_int),
                 ("smem_points", C.c_int),
                 ("smem_manifolds", C.c_int), ("watchdog_ms", C.c_float),
-                ("max_initial_penetration", C.c_float)]
+                ("max_initial_penetration", C.c_float), ("warm_start", C.c_int),
+                ("warm_tolerance", C.c_float)]
 
 
 class PmbsError(RuntimeError):
