@@ -310,27 +310,35 @@ __device__ __forceinline__ bool broadphase(const WarpMem& W, int n, const Grp& g
                                            float Px, float Py, const SimConst& C) {
     const int NB = W.NB();
     const int cap = min(pair_cap, W.pairS());
-    const int T = n * (n - 1) / 2;
-    const int Tw = wmax(T);
+    // Row by row: the lane of row i tests every j > i (neighbouring lanes read
+    // neighbouring boxes, so the shared loads do not conflict) and keeps a bit mask; rows
+    // are emitted in order and bits in ascending j, which is the lexicographic pair order.
+    const int rw = wmax(n);
     int np = 0;
     bool overflow = false;
-    for (int base = 0; base < Tw; base += g.G) {
-        const int t = base + g.gl;
-        bool ov = false;
-        int i = 0, j = 0;
-        if (t < T) {
-            pair_of_index(t, n, i, j);
-            ov = W.lo()[i] <= W.hi()[j] && W.lo()[j] <= W.hi()[i] && W.lo()[NB + i] <= W.hi()[NB + j] &&
-                 W.lo()[NB + j] <= W.hi()[NB + i] && W.lo()[2 * NB + i] <= W.hi()[2 * NB + j] &&
-                 W.lo()[2 * NB + j] <= W.hi()[2 * NB + i];
+    for (int base = 0; base < rw; base += g.G) {
+        const int i = base + g.gl;
+        unsigned long long mask = 0ull;
+        if (i < n) {
+            const float lx = W.lo()[i], hx = W.hi()[i], ly = W.lo()[NB + i], hy = W.hi()[NB + i];
+            const float lz = W.lo()[2 * NB + i], hz = W.hi()[2 * NB + i];
+            for (int j = i + 1; j < n; j++) {
+                const bool ov = lx <= W.hi()[j] && W.lo()[j] <= hx && ly <= W.hi()[NB + j] && W.lo()[NB + j] <= hy &&
+                                lz <= W.hi()[2 * NB + j] && W.lo()[2 * NB + j] <= hz;
+                mask |= (unsigned long long)ov << j;
+            }
         }
-        const unsigned m = g.ballot(ov);
-        const int pos = np + __popc(m & g.lt());
-        if (ov) {
+        int total;
+        const int pos0 = np + g.excl_scan(__popcll(mask), total);
+        int pos = pos0;
+        while (mask) {
+            const int j = __ffsll((long long)mask) - 1;
+            mask &= mask - 1ull;
             if (pos < cap) W.pairs()[pos] = (uint16_t)(i | (j << 8));
             else overflow = true;
+            pos++;
         }
-        np += __popc(m);
+        np += total;
     }
     overflow = g.any(overflow);
     int npl = 0, npu = 0;

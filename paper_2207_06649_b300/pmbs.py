@@ -283,8 +283,15 @@ class Engine:
     # ---- snapshot predicates
     @staticmethod
     def _csr(box_offset, states, half):
-        return (np.ascontiguousarray(box_offset, np.int32), np.ascontiguousarray(states, np.float32),
-                np.ascontiguousarray(half, np.float32))
+        """CSR arrays for the snapshot calls; refuses ranges the arrays do not hold (the C
+        calls trust the sizes)."""
+        off = np.ascontiguousarray(box_offset, np.int32)
+        st = np.ascontiguousarray(states, np.float32).reshape(-1, 13)
+        h = np.ascontiguousarray(half, np.float32).reshape(-1, 3)
+        if off.ndim != 1 or off.shape[0] < 1 or off[0] < 0 or np.any(np.diff(off) < 0) or \
+                st.shape[0] < off[-1] or h.shape[0] < off[-1]:
+            raise ValueError("box_offset does not describe the given state and half-extent arrays")
+        return off, st, h
 
     def eval_pairs(self, box_offset, states, half, pusher_xy=None):
         off, st, h = self._csr(box_offset, states, half)

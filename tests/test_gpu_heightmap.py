@@ -52,8 +52,9 @@ def test_heightmaps_bit_exact_on_tilted_snapshots(eng, orc, seed):
 def test_heightmaps_of_clutter_empty_and_64_boxes(eng, orc):
     sg = _sg()
     rng = np.random.default_rng(3)
-    sc = sg.make_scene(rng, 64, region_half=0.14)
+    sc = sg.make_scene(rng, 64, half_lo=0.008, half_hi=0.02, region_half=0.19)
     st64 = sg.state13(sc).astype(np.float32)
+    assert len(st64) == 64
     empty = np.zeros((0, 13), np.float32)
     off = np.array([0, 0, 64], np.int32)
     got = eng.render_heightmaps(off, np.concatenate([empty, st64]), sc.half)
