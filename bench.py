@@ -36,8 +36,8 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": "69ceb30f05932c12", "bytes_per_launch": 19696307,
-           "note": "ncu dram bytes (read 3.354 MB + write 1.580 MB) of a 1024-env launch in the "
+TRAFFIC = {"source_sha": "4ab5247526ad84d7", "bytes_per_launch": 18932861,
+           "note": "ncu dram bytes (read 3.239 MB + write 1.503 MB) of a 1024-env launch in the "
                    "32,2,0 launch shape, scaled by env-steps (371,760 -> 1,484,160) to the 4096-env launch"}
 
 
