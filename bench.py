@@ -16,8 +16,8 @@ batched rollout of all environments.  Metric: simulated environment-substeps per
   roofline  the rollout kernel against the FP32 CUDA-core peak (ALU bound).
   cpu_baseline  the FP64 CPU oracle on the host cores, on a bounded sample.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on the same
-workload and metric.  Under torchrun each rank runs its own 4096-environment workload on
+--impl reference times the FP64 CPU oracle (a plain sequential restatement of the method,
+the comparison arm) on the same workload and metric.  Under torchrun each rank runs its own 4096-environment workload on
 its own GPU (weak scaling, no data-path collective).
 """
 import argparse
