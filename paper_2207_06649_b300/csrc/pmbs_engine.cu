@@ -1702,38 +1702,62 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
     const int saved[4] = {ctx->fixed_G, ctx->fixed_wpb, ctx->fixed_Ps, ctx->fixed_Ms};
     ctx->tuned.erase(shape_bucket(nb));
     const int Gs[3] = {32, 16, 8}, Ws[3] = {4, 2, 1}, Mss[4] = {0, 8, 16, 40};
-    float best_ms = 1e30f;
-    std::array<int, 3> best = {32, 4, -1};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     pmbs_status result = PMBS_OK;
+    // time one candidate: best of two freshly built batches (identical work), advancing
+    // every environment by up to `steps` substeps (0: the whole rollout)
+    auto time_shape = [&](int G, int wpb, int Ms, int steps, float& ms, int& used_Ms) {
+        ctx->fixed_G = G;
+        ctx->fixed_wpb = wpb;
+        ctx->fixed_Ps = -1;
+        ctx->fixed_Ms = Ms;
+        ms = 1e30f;
+        cudaError_t e = cudaSuccess;
+        for (int rep = 0; rep < 2 && e == cudaSuccess && result == PMBS_OK; rep++) {
+            int64_t id = 0;
+            result = rollout_common(ctx, n_envs, scene_ids, first_push, depth, seeds, false, &id);
+            if (result != PMBS_OK) break;
+            Batch& b = ctx->batches[id];
+            float t = 0.f;
+            e = cudaEventRecord(e0, b.stream);
+            if (e == cudaSuccess) result = launch_rollout(ctx, b, steps, b.stream);
+            if (e == cudaSuccess && result == PMBS_OK) e = cudaEventRecord(e1, b.stream);
+            if (e == cudaSuccess && result == PMBS_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && result == PMBS_OK) e = cudaEventElapsedTime(&t, e0, e1);
+            used_Ms = b.Ms;
+            release_batch_mem(ctx, b);
+            ctx->batches.erase(id);
+            ms = std::min(ms, t);
+        }
+        if (e != cudaSuccess) result = fail(ctx, PMBS_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    };
+    // screening on the first `substeps` substeps, then the three fastest shapes timed over
+    // the whole rollout (a batch's time follows its longest environments, which the first
+    // push alone does not rank reliably)
+    std::vector<std::pair<float, std::array<int, 3>>> screen;
     for (int gi = 0; gi < 3 && result == PMBS_OK; gi++)
         for (int wi = 0; wi < 3 && result == PMBS_OK; wi++)
             for (int mi = 0; mi < 4 && result == PMBS_OK; mi++) {
-                ctx->fixed_G = Gs[gi];
-                ctx->fixed_wpb = Ws[wi];
-                ctx->fixed_Ps = -1;
-                ctx->fixed_Ms = Mss[mi];
-                int64_t id = 0;
-                result = rollout_common(ctx, n_envs, scene_ids, first_push, depth, seeds, false, &id);
-                if (result != PMBS_OK) break;
-                Batch& b = ctx->batches[id];
                 float ms = 0.f;
-                cudaError_t e = cudaEventRecord(e0, b.stream);
-                if (e == cudaSuccess) result = launch_rollout(ctx, b, substeps, b.stream);
-                if (e == cudaSuccess && result == PMBS_OK) e = cudaEventRecord(e1, b.stream);
-                if (e == cudaSuccess && result == PMBS_OK) e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess && result == PMBS_OK) e = cudaEventElapsedTime(&ms, e0, e1);
-                const int used_Ms = b.Ms;
-                release_batch_mem(ctx, b);
-                ctx->batches.erase(id);
-                if (e != cudaSuccess) result = fail(ctx, PMBS_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-                if (result == PMBS_OK && ms < best_ms) {
-                    best_ms = ms;
-                    best = {Gs[gi], Ws[wi], used_Ms};
-                }
+                int used = -1;
+                time_shape(Gs[gi], Ws[wi], Mss[mi], substeps, ms, used);
+                if (result == PMBS_OK) screen.push_back({ms, {Gs[gi], Ws[wi], used}});
             }
+    std::sort(screen.begin(), screen.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    float best_ms = 1e30f;
+    std::array<int, 3> best = {32, 4, -1};
+    for (size_t k = 0; k < std::min<size_t>(3, screen.size()) && result == PMBS_OK; k++) {
+        float ms = 0.f;
+        int used = -1;
+        const auto& sh = screen[k].second;
+        time_shape(sh[0], sh[1], sh[2], 0, ms, used);
+        if (result == PMBS_OK && ms < best_ms) {
+            best_ms = ms;
+            best = {sh[0], sh[1], used};
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->fixed_G = saved[0];
