@@ -302,12 +302,15 @@ def run_ours(args):
 
     # launch shape picked by the library's autotuner on this workload (untimed)
     tuned = None
+    rollout_launches = 1
     if args.shape:
         g_, w_, m_ = (int(x) for x in args.shape.split(","))
         eng.set_launch_shape(g_, w_, -1, m_)
         tuned = {"lanes_per_env": g_, "warps_per_block": w_, "smem_manifolds": m_, "fixed": True}
     elif not args.no_autotune:
         tuned = eng.autotune(ids, pushes, args.depth, seeds, substeps=240)
+        k = tuned.get("substeps_per_launch", 0)
+        rollout_launches = 1 if k <= 0 else -(-args.depth * 240 // k)
 
     # warm-up (untimed); the first batch also gives the per-step work counts
     batches = []
@@ -463,7 +466,8 @@ def run_ours(args):
         "serving": serving,
         "heightmaps": heightmaps,
         "planning": planning,
-        "gpu_launches": 2 * args.steps,
+        # per timed step: the batch set-up kernel and the rollout launch(es) of the tiling
+        "gpu_launches": args.steps * (1 + rollout_launches),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scenes, pushes, seeds, args.depth, args.cpu_sample, "workload's")

@@ -191,13 +191,15 @@ pmbs_status pmbs_step_graph(pmbs_ctx* ctx, int64_t batch, int substeps_per_launc
  * given batch once per candidate shape (lanes per environment 32/16/8, warps per block
  * 4/2/1, manifolds per environment kept in shared memory 0/8/16/40), times its first
  * `substeps` substeps (best of two freshly built batches), re-times the three fastest
- * over the whole rollout
+ * over the whole rollout, then picks the iteration tiling of the winner (one persistent
+ * launch, or launches of one push or a quarter push of substeps each; the same results)
  * with CUDA events, and records the fastest shape for the batch's box-count bucket; later
  * batches in that bucket use it unless a shape is fixed.  Outputs may be NULL.  Blocks
  * until the timings finish. */
 pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push,
                           int depth, const uint64_t* seeds, int substeps, int32_t* out_lanes_per_env,
-                          int32_t* out_warps_per_block, int32_t* out_smem_manifolds, float* out_ms);
+                          int32_t* out_warps_per_block, int32_t* out_smem_manifolds, float* out_ms,
+                          int32_t* out_substeps_per_launch);
 
 /* Results of a finished batch, copied to host arrays of n_envs entries: cost (pushes
  * until graspable, depth+1 if never), reward (gamma^(cost-1) or 0), flags (PMBS_FLAG_*).

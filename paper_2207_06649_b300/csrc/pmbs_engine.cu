@@ -845,6 +845,7 @@ struct Batch {
     float4* warm = nullptr;         // warm-start caches (cfg.warm_start), one per environment
     bool finished = false;
     int G = 32, wpb = 4, Ms = 0;
+    int tile = 0;  // substeps per launch when run to completion (0: one persistent launch)
     cudaStream_t stream = nullptr;  // stream of this batch's launches (the context's by default)
     bool own_scratch = false;       // contact spill scratch of its own (batches that may overlap)
     size_t scr_off = 0, scr_bytes = 0;
@@ -872,7 +873,9 @@ struct pmbs_ctx {
     float4* gscratch = nullptr;
     size_t gscratch_off = 0, gscratch_bytes = 0;
     int fixed_wpb = 0, fixed_Ps = -1, fixed_Ms = -1, fixed_G = 0;
+    int fixed_tile = -1;  // substeps per launch forced by the autotuner while it times (-1: none)
     std::map<int, std::array<int, 3>> tuned;  // box-count bucket -> {G, wpb, Ms} from pmbs_autotune
+    std::map<int, int> tuned_tile;            // box-count bucket -> substeps per launch (0: persistent)
     SimConst C;
 };
 
@@ -1167,13 +1170,33 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
     b.finished = n_envs == 0;
     b.stream = ctx->stream;
     choose_shape(ctx, nb, b.G, b.wpb, b.Ms);
+    {
+        const auto t = ctx->tuned_tile.find(shape_bucket(nb));
+        b.tile = ctx->fixed_tile >= 0 ? ctx->fixed_tile : (t != ctx->tuned_tile.end() ? t->second : 0);
+    }
     const int64_t id = ctx->next_batch++;
     ctx->batches[id] = b;
     *out_batch = id;
     return PMBS_OK;
 }
 
+pmbs_status launch_rollout_once(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaStream_t stream);
+
+// A launch of the whole rollout (max_substeps <= 0) follows the batch's iteration tiling:
+// one persistent launch, or launches of `tile` substeps each (every environment advances
+// by up to `tile` substeps per launch; results are the same either way).
 pmbs_status launch_rollout(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaStream_t stream) {
+    if (max_substeps > 0 || b.tile <= 0) return launch_rollout_once(ctx, b, max_substeps, stream);
+    const long total = (long)b.depth * ctx->cfg.substeps_per_push;
+    const long launches = (total + b.tile - 1) / b.tile;
+    for (long i = 0; i < launches; i++) {
+        const pmbs_status st = launch_rollout_once(ctx, b, b.tile, stream);
+        if (st != PMBS_OK) return st;
+    }
+    return PMBS_OK;
+}
+
+pmbs_status launch_rollout_once(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaStream_t stream) {
     const pmbs_config& c = ctx->cfg;
     const int nb = b.nb;
     const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
@@ -1686,7 +1709,7 @@ pmbs_status pmbs_step_graph(pmbs_ctx* ctx, int64_t batch, int substeps_per_launc
 
 pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push, int depth,
                           const uint64_t* seeds, int substeps, int32_t* out_lanes_per_env, int32_t* out_warps_per_block,
-                          int32_t* out_smem_manifolds, float* out_ms) {
+                          int32_t* out_smem_manifolds, float* out_ms, int32_t* out_substeps_per_launch) {
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -1701,6 +1724,7 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
     }
     const int saved[4] = {ctx->fixed_G, ctx->fixed_wpb, ctx->fixed_Ps, ctx->fixed_Ms};
     ctx->tuned.erase(shape_bucket(nb));
+    ctx->tuned_tile.erase(shape_bucket(nb));
     const int Gs[3] = {32, 16, 8}, Ws[3] = {4, 2, 1}, Mss[4] = {0, 8, 16, 40};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
@@ -1748,6 +1772,8 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
     std::sort(screen.begin(), screen.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
     float best_ms = 1e30f;
     std::array<int, 3> best = {32, 4, -1};
+    const int saved_tile = ctx->fixed_tile;
+    ctx->fixed_tile = 0;
     for (size_t k = 0; k < std::min<size_t>(3, screen.size()) && result == PMBS_OK; k++) {
         float ms = 0.f;
         int used = -1;
@@ -1758,6 +1784,21 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
             best = {sh[0], sh[1], used};
         }
     }
+    // iteration tiling of the chosen shape: one persistent launch, or launches of one push
+    // or a quarter push each
+    int best_tile = 0;
+    const int tiles[2] = {ctx->cfg.substeps_per_push, std::max(1, ctx->cfg.substeps_per_push / 4)};
+    for (int k = 0; k < 2 && result == PMBS_OK; k++) {
+        ctx->fixed_tile = tiles[k];
+        float ms = 0.f;
+        int used = -1;
+        time_shape(best[0], best[1], best[2], 0, ms, used);
+        if (result == PMBS_OK && ms < best_ms) {
+            best_ms = ms;
+            best_tile = tiles[k];
+        }
+    }
+    ctx->fixed_tile = saved_tile;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->fixed_G = saved[0];
@@ -1766,10 +1807,12 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
     ctx->fixed_Ms = saved[3];
     if (result != PMBS_OK) return result;
     ctx->tuned[shape_bucket(nb)] = best;
+    ctx->tuned_tile[shape_bucket(nb)] = best_tile;
     if (out_lanes_per_env) *out_lanes_per_env = best[0];
     if (out_warps_per_block) *out_warps_per_block = best[1];
     if (out_smem_manifolds) *out_smem_manifolds = best[2];
     if (out_ms) *out_ms = best_ms;
+    if (out_substeps_per_launch) *out_substeps_per_launch = best_tile;
     return PMBS_OK;
 }
 

@@ -85,7 +85,7 @@ def load(build_if_missing: bool = True):
         "pmbs_rollout_pushes_device": ([vp, i32, vp, vp, i32, vp, vp], i32),
         "pmbs_step": ([vp, i64, i32], i32),
         "pmbs_step_graph": ([vp, i64, i32], i32),
-        "pmbs_autotune": ([vp, i32, vp, vp, i32, vp, i32, vp, vp, vp, vp], i32),
+        "pmbs_autotune": ([vp, i32, vp, vp, i32, vp, i32, vp, vp, vp, vp, vp], i32),
         "pmbs_query_cost": ([vp, i64, vp, vp, vp, vp, vp], i32),
         "pmbs_query_cost_device": ([vp, i64, vp, vp, vp], i32),
         "pmbs_query_states": ([vp, i64, vp, vp], i32),
@@ -234,10 +234,12 @@ class Engine:
         first_push = np.ascontiguousarray(first_push, np.float32)
         n = scene_ids.shape[0]
         seeds = np.ascontiguousarray(np.zeros(n, np.uint64) if seeds is None else seeds, np.uint64)
-        g, w, m, t = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
+        g, w, m, t, k = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float(), C.c_int32()
         self._check(self.lib.pmbs_autotune(self.ctx, n, _p(scene_ids), _p(first_push), depth, _p(seeds), substeps,
-                                           C.byref(g), C.byref(w), C.byref(m), C.byref(t)), "pmbs_autotune")
-        return dict(lanes_per_env=g.value, warps_per_block=w.value, smem_manifolds=m.value, ms=t.value)
+                                           C.byref(g), C.byref(w), C.byref(m), C.byref(t), C.byref(k)),
+                    "pmbs_autotune")
+        return dict(lanes_per_env=g.value, warps_per_block=w.value, smem_manifolds=m.value, ms=t.value,
+                    substeps_per_launch=k.value)
 
     def batch_info(self, batch):
         ne, nb = C.c_int32(), C.c_int32()

@@ -47,7 +47,7 @@ def test_autotune_picks_a_shape_and_keeps_results(work):
     ref = eng.rollout(ids, pushes, depth=2, seeds=seeds)
     best = eng.autotune(ids, pushes, 2, seeds, substeps=60)
     assert best["lanes_per_env"] in (8, 16, 32) and best["warps_per_block"] in (1, 2, 4) and best["ms"] > 0
-    assert 0 <= best["smem_manifolds"] <= 40
+    assert 0 <= best["smem_manifolds"] <= 40 and best["substeps_per_launch"] in (0, 240, 60)
     shape = eng.launch_shape(int(scenes.counts().max()))
     assert shape["lanes_per_env"] == best["lanes_per_env"]
     out = eng.rollout(ids, pushes, depth=2, seeds=seeds)
