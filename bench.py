@@ -36,9 +36,9 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": "4ab5247526ad84d7", "bytes_per_launch": 18932861,
-           "note": "ncu dram bytes (read 3.239 MB + write 1.503 MB) of a 1024-env launch in the "
-                   "32,2,0 launch shape, scaled by env-steps (371,760 -> 1,484,160) to the 4096-env launch"}
+TRAFFIC = {"source_sha": "4ab5247526ad84d7", "bytes_per_launch": 101632880,
+           "note": "ncu dram bytes (read 19.54 MB + write 47.78 MB) of a one-push launch of the same "
+                   "4096 scenes in the 32,2,0 launch shape, scaled by env-steps (983,040 -> 1,484,160)"}
 
 
 def measured_hbm_gbs():
@@ -101,7 +101,7 @@ def dist_info():
     return ws, rank, local
 
 
-WORKLOAD = "uneven rollout: 4096 scenes x U{5..40} boxes, depth 3 x 240 substeps"
+WORKLOAD = "uneven rollout: {envs} scenes x U{{5..40}} boxes, depth {depth} x 240 substeps"
 METRIC = "env-steps/s at 4096 uneven envs"
 
 
@@ -189,7 +189,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "envs": args.envs, "depth": args.depth,
+            "config": {"workload": WORKLOAD.format(envs=args.envs, depth=args.depth), "envs": args.envs, "depth": args.depth,
                        "per_step_sample": per_step},
             "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": v,
                              "unit": "env-steps/s"},
@@ -439,13 +439,14 @@ def run_ours(args):
     peak = flops.fp32_peak_tflops(sms, max_mhz)
     achieved = flops_per_launch / kernel_s / 1e12
     sha = kernel_source_sha()
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha else None
+    default_workload = (args.envs, args.depth, args.seed) == (4096, 3, 3)
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and default_workload else None
     state_bytes = float(boxes.sum()) * (72 + 52 + 52) + args.envs * (28 + 64 + 13)
     line = {
         "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "envs": args.envs, "boxes_per_env_mean": float(boxes.mean()),
+        "config": {"workload": WORKLOAD.format(envs=args.envs, depth=args.depth), "envs": args.envs, "boxes_per_env_mean": float(boxes.mean()),
                    "boxes_per_env_range": [int(boxes.min()), int(boxes.max())], "depth": args.depth,
                    "substeps_per_push": 240, "pgs_iters": 10, "env_steps_per_step": env_steps,
                    "box_steps_per_s": value * float(boxes.mean()),
