@@ -88,12 +88,58 @@ void quat_to_R(const T* q, T* R) {
     R[6] = T(2) * (xz - wy);         R[7] = T(2) * (yz + wx);         R[8] = T(1) - T(2) * (xx + yy);
 }
 
+// Cylinders.  A row of half extents (r, -r, h) marks a cylinder of radius r and half
+// height h about its body z axis; (hx, hy, hz) with all three positive is a box.  For
+// contact, footprints and heightmaps a cylinder is the right prism over the regular
+// 16-gon inscribed in its circle: vertex k of a cap at angle k pi/8 in the body xy plane,
+// side face s with outward normal at angle (2s + 1) pi/16 and apothem r cos(pi/16), cap
+// edges of half length r sin(pi/16).  Its mass properties are those of the solid
+// cylinder.  Direction tables (cos, sin): vertex directions k = 0..7 (k + 8 is the
+// negation) and side normals s = 0..7 (likewise); the values are the closed forms of the
+// angles, rounded once to T.
+template <typename T>
+struct Gon {
+    T vc[8], vs[8], fc[8], fs[8];
+    T apo, half_edge;  // cos(pi/16), sin(pi/16)
+    Gon() {
+        const double C1 = std::cos(M_PI / 8), S1 = std::sin(M_PI / 8), H = std::sqrt(0.5);
+        const double D1 = std::cos(M_PI / 16), E1 = std::sin(M_PI / 16);
+        const double D3 = std::cos(3 * M_PI / 16), E3 = std::sin(3 * M_PI / 16);
+        const double vcd[8] = {1, C1, H, S1, 0, -S1, -H, -C1}, vsd[8] = {0, S1, H, C1, 1, C1, H, S1};
+        const double fcd[8] = {D1, D3, E3, E1, -E1, -E3, -D3, -D1}, fsd[8] = {E1, E3, D3, D1, D1, D3, E3, E1};
+        for (int k = 0; k < 8; k++) { vc[k] = (T)vcd[k]; vs[k] = (T)vsd[k]; fc[k] = (T)fcd[k]; fs[k] = (T)fsd[k]; }
+        apo = (T)D1;
+        half_edge = (T)E1;
+    }
+};
+template <typename T>
+const Gon<T>& gon() {
+    static const Gon<T> g;
+    return g;
+}
+template <typename T>
+inline bool is_cyl(const T* h) { return h[1] < T(0); }
+
+// Radial support of the unit-radius 16-gon along the body-plane direction (p0, p1):
+// max over the eight vertex directions of |c_k p0 + s_k p1|.
+template <typename T>
+T gon_support(T p0, T p1) {
+    const Gon<T>& G = gon<T>();
+    T m = T(0);
+    for (int k = 0; k < 8; k++) {
+        const T v = std::fabs(G.vc[k] * p0 + G.vs[k] * p1);
+        if (v > m) m = v;
+    }
+    return m;
+}
+
 // World AABB of a box: half-width e_k = (|R_k0| h0 + |R_k1| h1) + |R_k2| h2, grown by
-// the contact margin on every side.
+// the contact margin on every side.  A cylinder uses its bounding box (r, r, h).
 template <typename T>
 void box_aabb(const T* c, const T* R, const T* h, T m, T* lo, T* hi) {
+    const T h1 = std::fabs(h[1]);
     for (int k = 0; k < 3; k++) {
-        const T e = (std::fabs(R[3 * k]) * h[0] + std::fabs(R[3 * k + 1]) * h[1]) +
+        const T e = (std::fabs(R[3 * k]) * h[0] + std::fabs(R[3 * k + 1]) * h1) +
                     std::fabs(R[3 * k + 2]) * h[2];
         lo[k] = (c[k] - e) - m;
         hi[k] = (c[k] + e) + m;
@@ -149,7 +195,9 @@ PairList<T> broadphase(int n, const T* x /*[n][3]*/, const T* q /*[n][4]*/, cons
 // Top-down footprint of a box: centre, unit axes u (the horizontal part of the box's
 // x axis, or of its y axis when x is vertical) and v = perp(u), and the support
 // half-widths of the 3-D box along u and v.  Exact for upright boxes, conservative
-// otherwise.
+// otherwise.  A cylinder's support along u is r times the 16-gon's radial support of
+// (u.x_b, u.y_b) plus h |u.z_b| (x_b, y_b, z_b its body axes): the footprint is the
+// rectangle bounding the prism's projection along u and v.
 template <typename T>
 struct Foot { T cx, cy, ux, uy, vx, vy, su, sv; };
 
@@ -165,6 +213,13 @@ Foot<T> footprint(const T* x, const T* q, const T* h) {
     f.cx = x[0]; f.cy = x[1];
     f.ux = ex / len; f.uy = ey / len;
     f.vx = -f.uy; f.vy = f.ux;
+    if (is_cyl(h)) {
+        f.su = gon_support(R[0] * f.ux + R[3] * f.uy, R[1] * f.ux + R[4] * f.uy) * h[0] +
+               std::fabs(R[2] * f.ux + R[5] * f.uy) * h[2];
+        f.sv = gon_support(R[0] * f.vx + R[3] * f.vy, R[1] * f.vx + R[4] * f.vy) * h[0] +
+               std::fabs(R[2] * f.vx + R[5] * f.vy) * h[2];
+        return f;
+    }
     f.su = (std::fabs(R[0] * f.ux + R[3] * f.uy) * h[0] + std::fabs(R[1] * f.ux + R[4] * f.uy) * h[1]) +
            std::fabs(R[2] * f.ux + R[5] * f.uy) * h[2];
     f.sv = (std::fabs(R[0] * f.vx + R[3] * f.vy) * h[0] + std::fabs(R[1] * f.vx + R[4] * f.vy) * h[1]) +
@@ -310,19 +365,38 @@ int sample_push(int n, const T* x, const T* q, const T* h, uint64_t seed, int k,
 // in the intersection of [-(a_k r_k) - h_k r_k, -(a_k r_k) + h_k r_k] with r_k = 1 / b_k
 // (r_k and h_k r_k rounded once per box; ends swapped when b_k < 0; when b_k = 0 the
 // constraint holds for every s if |a_k| <= h_k and for none otherwise).  A non-empty
-// intersection [s_lo, s_hi] puts the box's top over the cell at c_z + s_hi.  Every
+// intersection [s_lo, s_hi] puts the box's top over the cell at c_z + s_hi.  A cylinder
+// is the intersection of nine such slabs (its cap axis and the 16-gon's eight side
+// normal directions).  Every
 // operation is written in its evaluation order (binary32 twin); fma() is one fused
 // multiply-add with a single rounding: a_k = fma(R_0k, x - c_x, R_1k (y - c_y)) and the
 // slab ends fma(-a_k, r_k, -+h_k r_k).
 template <typename T>
 void heightmap(int n, const T* x, const T* q, const T* h, int W, int H, T x0, T y0, T cell, T* out) {
-    std::vector<T> R(9 * n), rb(3 * n), hr(3 * n);
+    // Per body its slabs: world normal (wx, wy, wz), half thickness, r = 1/wz and
+    // half * r.  A box has its three axes; a cylinder its cap axis and the eight side
+    // normal directions of its 16-gon (wx = c_s R_00 + s_s R_01 and so on, half
+    // thickness r cos(pi/16) rounded once).
+    const Gon<T>& G = gon<T>();
+    std::vector<int> first(n + 1, 0);
+    std::vector<T> sw;  // 6 per slab
     for (int b = 0; b < n; b++) {
-        quat_to_R(q + 4 * b, &R[9 * b]);
-        for (int k = 0; k < 3; k++) {
-            rb[3 * b + k] = R[9 * b + 6 + k] == T(0) ? T(0) : T(1) / R[9 * b + 6 + k];
-            hr[3 * b + k] = h[3 * b + k] * rb[3 * b + k];
+        T R[9];
+        quat_to_R(q + 4 * b, R);
+        const T* hb = h + 3 * b;
+        auto add = [&](T wx, T wy, T wz, T half) {
+            const T rb = wz == T(0) ? T(0) : T(1) / wz;
+            sw.insert(sw.end(), {wx, wy, wz, half, rb, half * rb});
+        };
+        if (is_cyl(hb)) {
+            add(R[2], R[5], R[8], hb[2]);
+            const T apo = hb[0] * G.apo;
+            for (int k = 0; k < 8; k++)
+                add(G.fc[k] * R[0] + G.fs[k] * R[1], G.fc[k] * R[3] + G.fs[k] * R[4], G.fc[k] * R[6] + G.fs[k] * R[7], apo);
+        } else {
+            for (int k = 0; k < 3; k++) add(R[k], R[3 + k], R[6 + k], hb[k]);
         }
+        first[b + 1] = (int)sw.size() / 6;
     }
     for (int j = 0; j < H; j++)
         for (int i = 0; i < W; i++) {
@@ -330,19 +404,19 @@ void heightmap(int n, const T* x, const T* q, const T* h, int W, int H, T x0, T 
             const T yc = y0 + ((T)j + T(0.5)) * cell;
             T top = T(0);
             for (int b = 0; b < n; b++) {
-                const T* Rb = &R[9 * b];
                 const T dx = xc - x[3 * b], dy = yc - x[3 * b + 1];
                 T s_lo = -INFINITY, s_hi = INFINITY;
                 bool hit = true;
-                for (int k = 0; k < 3 && hit; k++) {
-                    const T a = std::fma(Rb[k], dx, Rb[3 + k] * dy);
-                    const T bk = Rb[6 + k];
+                for (int k = first[b]; k < first[b + 1] && hit; k++) {
+                    const T* S = &sw[6 * k];
+                    const T a = std::fma(S[0], dx, S[1] * dy);
+                    const T bk = S[2];
                     if (bk == T(0)) {
-                        if (!(std::fabs(a) <= h[3 * b + k])) hit = false;
+                        if (!(std::fabs(a) <= S[3])) hit = false;
                         continue;
                     }
-                    const T r = rb[3 * b + k];
-                    T t0 = std::fma(-a, r, -hr[3 * b + k]), t1 = std::fma(-a, r, hr[3 * b + k]);
+                    const T r = S[4];
+                    T t0 = std::fma(-a, r, -S[5]), t1 = std::fma(-a, r, S[5]);
                     if (bk < T(0)) std::swap(t0, t1);
                     if (t0 > s_lo) s_lo = t0;
                     if (t1 < s_hi) s_hi = t1;
@@ -372,7 +446,9 @@ bool graspable_hm(const T* map, int cells, T x0, T cellw, int n, const T* x, con
     const Foot<T> ft = footprint(x + 3 * t, q + 4 * t, h + 3 * t);
     T R[9];
     quat_to_R(q + 4 * t, R);
-    const T ez = (std::fabs(R[6]) * h[3 * t] + std::fabs(R[7]) * h[3 * t + 1]) + std::fabs(R[8]) * h[3 * t + 2];
+    const T* ht = h + 3 * t;
+    const T ez = is_cyl(ht) ? gon_support(R[6], R[7]) * ht[0] + std::fabs(R[8]) * ht[2]
+                            : (std::fabs(R[6]) * ht[0] + std::fabs(R[7]) * ht[1]) + std::fabs(R[8]) * ht[2];
     const T z_tip = (x[3 * t + 2] + ez) - depth;
     const T halfW = W * T(0.5), hfw = fw * T(0.5);
     for (int k = 0; k < K; k++) {
@@ -422,7 +498,8 @@ inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
 struct Body {
     V3 x, v, w;
     double q[4];
-    double h[3], m, invm, mu, invIb[3];
+    double h[3], m, invm, mu, invIb[3];  // h = (r, r, half height) for a cylinder
+    bool cyl;
     double R[9], invIw[6];   // refreshed every substep
 };
 inline V3 axis(const Body& b, int k) { return {b.R[k], b.R[3 + k], b.R[6 + k]}; }
@@ -482,15 +559,23 @@ void load_env(Env& E, int n, const double* s13, const float* half, const float* 
         for (int k = 0; k < 4; k++) b.q[k] = s[3 + k];
         b.v = {s[7], s[8], s[9]};
         b.w = {s[10], s[11], s[12]};
-        for (int k = 0; k < 3; k++) b.h[k] = half[3 * i + k];
+        b.cyl = half[3 * i + 1] < 0.f;
+        for (int k = 0; k < 3; k++) b.h[k] = std::fabs((double)half[3 * i + k]);
         b.m = mass[i];
         b.invm = 1.0 / b.m;
         b.mu = mu[i];
-        // solid box inertia about its centre, from half extents: m/3 (h_j^2 + h_k^2)
         const double hx2 = b.h[0] * b.h[0], hy2 = b.h[1] * b.h[1], hz2 = b.h[2] * b.h[2];
-        b.invIb[0] = 1.0 / (b.m / 3.0 * (hy2 + hz2));
-        b.invIb[1] = 1.0 / (b.m / 3.0 * (hx2 + hz2));
-        b.invIb[2] = 1.0 / (b.m / 3.0 * (hx2 + hy2));
+        if (b.cyl) {
+            // solid cylinder of radius r and height 2h: m (3 r^2 + 4 h^2) / 12 about the
+            // two diameters, m r^2 / 2 about its axis
+            b.invIb[0] = b.invIb[1] = 1.0 / (b.m * (3.0 * hx2 + 4.0 * hz2) / 12.0);
+            b.invIb[2] = 1.0 / (b.m * hx2 / 2.0);
+        } else {
+            // solid box inertia about its centre, from half extents: m/3 (h_j^2 + h_k^2)
+            b.invIb[0] = 1.0 / (b.m / 3.0 * (hy2 + hz2));
+            b.invIb[1] = 1.0 / (b.m / 3.0 * (hx2 + hz2));
+            b.invIb[2] = 1.0 / (b.m / 3.0 * (hx2 + hy2));
+        }
     }
 }
 
@@ -561,11 +646,12 @@ bool box_plane(const Body& b, int bi, const oracle_params& P, Manifold& M) {
 }
 
 // Sutherland-Hodgman clip of a polygon against the half space dot(p - o, a) - h <= 0.
-// At most eight vertices are kept (the bound for a convex quad clipped four times).
-std::vector<V3> clip_side(const std::vector<V3>& poly, V3 o, V3 a, double h) {
+// At most `cap` vertices are kept (eight, the bound for a convex quad clipped four
+// times; 32 for faces of cylinders).
+std::vector<V3> clip_side(const std::vector<V3>& poly, V3 o, V3 a, double h, size_t cap = 8) {
     std::vector<V3> out;
     const size_t N = poly.size();
-    auto add = [&](V3 p) { if (out.size() < 8) out.push_back(p); };
+    auto add = [&](V3 p) { if (out.size() < cap) out.push_back(p); };
     for (size_t i = 0; i < N; i++) {
         const V3 cur = poly[i], prev = poly[(i + N - 1) % N];
         const double dc = dot(cur - o, a) - h, dp = dot(prev - o, a) - h;
@@ -577,6 +663,51 @@ std::vector<V3> clip_side(const std::vector<V3>& poly, V3 o, V3 a, double h) {
         }
     }
     return out;
+}
+
+// At most four of the candidate points kp (separations kd) with face normal nref: all
+// of them when there are four or fewer; else the deepest (earliest on ties); then the
+// farthest from it; then the one spanning the largest triangle with those two; then the
+// one adding the largest area outside an edge of that triangle.
+int reduce_points(const std::vector<V3>& kp, const std::vector<double>& kd, V3 nref, V3* pts, double* dep) {
+    const int nk = (int)kp.size();
+    if (nk <= 4) {
+        for (int i = 0; i < nk; i++) { pts[i] = kp[i]; dep[i] = kd[i]; }
+        return nk;
+    }
+    std::vector<bool> used(nk, false);
+    int sel[4];
+    int i1 = 0;
+    for (int i = 1; i < nk; i++) if (kd[i] < kd[i1]) i1 = i;
+    used[i1] = true;
+    int i2 = -1; double b2 = -1;
+    for (int i = 0; i < nk; i++) {
+        if (used[i]) continue;
+        const V3 e = kp[i] - kp[i1];
+        const double l = dot(e, e);
+        if (i2 < 0 || l > b2) { b2 = l; i2 = i; }
+    }
+    used[i2] = true;
+    auto area = [&](int a, int b, V3 p) { return dot(cross(kp[b] - kp[a], p - kp[a]), nref); };
+    int i3 = -1; double b3 = -1;
+    for (int i = 0; i < nk; i++) {
+        if (used[i]) continue;
+        const double A = std::fabs(area(i1, i2, kp[i]));
+        if (i3 < 0 || A > b3) { b3 = A; i3 = i; }
+    }
+    used[i3] = true;
+    const double sgn = area(i1, i2, kp[i3]) < 0 ? -1.0 : 1.0;
+    int i4 = -1; double b4 = 0;
+    for (int i = 0; i < nk; i++) {
+        if (used[i]) continue;
+        double A = -sgn * area(i1, i2, kp[i]);
+        A = std::max(A, -sgn * area(i2, i3, kp[i]));
+        A = std::max(A, -sgn * area(i3, i1, kp[i]));
+        if (i4 < 0 || A > b4) { b4 = A; i4 = i; }
+    }
+    sel[0] = i1; sel[1] = i2; sel[2] = i3; sel[3] = i4;
+    for (int i = 0; i < 4; i++) { pts[i] = kp[sel[i]]; dep[i] = kd[sel[i]]; }
+    return 4;
 }
 
 // Face contact: clip the incident face of box `inc` against the side planes of the
@@ -613,47 +744,7 @@ int face_contact(const Body& ref, int k, V3 nref, const Body& inc, const oracle_
         const double d = dot(p - fc, nref);
         if (d < P.margin) { kp.push_back(p); kd.push_back(d); }
     }
-    const int nk = (int)kp.size();
-    if (nk <= 4) {
-        for (int i = 0; i < nk; i++) { pts[i] = kp[i]; dep[i] = kd[i]; }
-        return nk;
-    }
-    // Reduction to four points: the deepest; then the farthest from it; then the one
-    // spanning the largest triangle with those two; then the one adding the largest
-    // area outside an edge of that triangle.
-    bool used[8] = {false};
-    int sel[4];
-    int i1 = 0;
-    for (int i = 1; i < nk; i++) if (kd[i] < kd[i1]) i1 = i;
-    used[i1] = true;
-    int i2 = -1; double b2 = -1;
-    for (int i = 0; i < nk; i++) {
-        if (used[i]) continue;
-        const V3 e = kp[i] - kp[i1];
-        const double l = dot(e, e);
-        if (i2 < 0 || l > b2) { b2 = l; i2 = i; }
-    }
-    used[i2] = true;
-    auto area = [&](int a, int b, V3 p) { return dot(cross(kp[b] - kp[a], p - kp[a]), nref); };
-    int i3 = -1; double b3 = -1;
-    for (int i = 0; i < nk; i++) {
-        if (used[i]) continue;
-        const double A = std::fabs(area(i1, i2, kp[i]));
-        if (i3 < 0 || A > b3) { b3 = A; i3 = i; }
-    }
-    used[i3] = true;
-    const double sgn = area(i1, i2, kp[i3]) < 0 ? -1.0 : 1.0;
-    int i4 = -1; double b4 = 0;
-    for (int i = 0; i < nk; i++) {
-        if (used[i]) continue;
-        double A = -sgn * area(i1, i2, kp[i]);
-        A = std::max(A, -sgn * area(i2, i3, kp[i]));
-        A = std::max(A, -sgn * area(i3, i1, kp[i]));
-        if (i4 < 0 || A > b4) { b4 = A; i4 = i; }
-    }
-    sel[0] = i1; sel[1] = i2; sel[2] = i3; sel[3] = i4;
-    for (int i = 0; i < 4; i++) { pts[i] = kp[sel[i]]; dep[i] = kd[sel[i]]; }
-    return 4;
+    return reduce_points(kp, kd, nref, pts, dep);
 }
 
 struct SatResult {
@@ -820,6 +911,348 @@ bool capsule_box(const Body& b, int bi, V3 Pp, const oracle_params& P, Manifold&
     return true;
 }
 
+// ---- cylinders (16-gon prisms) ---------------------------------------------------------
+// Pairs with a cylinder use the general separating-axis test of two convex polyhedra:
+// candidate axes are the face normal directions of A (box: its 3 axes; cylinder: its cap
+// axis, then the 8 side normal directions), those of B, and the cross products of an edge
+// direction of A with one of B (box: its 3 axes; cylinder: its axis, then the 8 cap edge
+// directions), skipped when |cross|^2 < 1e-12.  Separation along a unit axis L is
+// |L.(c_B - c_A)| minus the two support half widths; the selection thresholds are those of
+// the box-box test.  Contact: the reference face (the selected face, facing the other
+// body) clips the other body's incident face (the one whose outward normal is most
+// anti-parallel), up to 32 clipped vertices, reduced to four as for boxes; an edge axis
+// gives one point midway between the closest points of the two supporting edges.
+
+const Gon<double>& G64() { return gon<double>(); }
+// body-plane unit vectors: vertex direction k, side normal s and side tangent s (k, s in 0..15)
+inline void gon_vdir(int k, double& c, double& sn) { const double g = k < 8 ? 1 : -1; c = g * G64().vc[k & 7]; sn = g * G64().vs[k & 7]; }
+inline void gon_fdir(int s, double& c, double& sn) { const double g = s < 8 ? 1 : -1; c = g * G64().fc[s & 7]; sn = g * G64().fs[s & 7]; }
+inline V3 plane_vec(const Body& b, double c, double sn) { return axis(b, 0) * c + axis(b, 1) * sn; }
+inline V3 side_normal(const Body& b, int s) { double c, sn; gon_fdir(s, c, sn); return plane_vec(b, c, sn); }
+inline V3 side_tangent(const Body& b, int s) { double c, sn; gon_fdir(s, c, sn); return plane_vec(b, -sn, c); }
+inline V3 cyl_vertex(const Body& b, int k, double sz) {
+    double c, sn;
+    gon_vdir(k & 15, c, sn);
+    return b.x + plane_vec(b, c * b.h[0], sn * b.h[0]) + axis(b, 2) * (sz * b.h[2]);
+}
+inline double cyl_apothem(const Body& b) { return b.h[0] * G64().apo; }
+
+double support(const Body& b, V3 L) {
+    if (b.cyl) return gon_support(dot(axis(b, 0), L), dot(axis(b, 1), L)) * b.h[0] + std::fabs(dot(axis(b, 2), L)) * b.h[2];
+    return (b.h[0] * std::fabs(dot(axis(b, 0), L)) + b.h[1] * std::fabs(dot(axis(b, 1), L))) + b.h[2] * std::fabs(dot(axis(b, 2), L));
+}
+inline int n_dirs(const Body& b) { return b.cyl ? 9 : 3; }
+inline V3 face_dir(const Body& b, int f) { return !b.cyl ? axis(b, f) : (f == 0 ? axis(b, 2) : side_normal(b, f - 1)); }
+inline double face_half(const Body& b, int f) { return !b.cyl ? b.h[f] : (f == 0 ? b.h[2] : cyl_apothem(b)); }
+inline V3 edge_dir(const Body& b, int j) { return !b.cyl ? axis(b, j) : (j == 0 ? axis(b, 2) : side_tangent(b, j - 1)); }
+
+struct ConvexSat {
+    bool touching;
+    int kind;   // 0 face of A, 1 face of B, 2 edge pair
+    int i, j;   // face index, or edge of A and edge of B
+    double sep;
+    V3 n;       // from A to B
+};
+
+ConvexSat sat_convex(const Body& A, const Body& B, double margin) {
+    ConvexSat r{false, 0, -1, -1, 0, {0, 0, 0}};
+    const V3 D = B.x - A.x;
+    int fa = -1; double sa = 0;
+    for (int f = 0; f < n_dirs(A); f++) {
+        const V3 L = face_dir(A, f);
+        const double s = std::fabs(dot(D, L)) - (face_half(A, f) + support(B, L));
+        if (s >= margin) return r;
+        if (fa < 0 || s > sa) { fa = f; sa = s; }
+    }
+    int fb = -1; double sb = 0;
+    for (int f = 0; f < n_dirs(B); f++) {
+        const V3 L = face_dir(B, f);
+        const double s = std::fabs(dot(D, L)) - (support(A, L) + face_half(B, f));
+        if (s >= margin) return r;
+        if (fb < 0 || s > sb) { fb = f; sb = s; }
+    }
+    int ea = -1, eb = -1; double se = 0; V3 le{0, 0, 0};
+    for (int i = 0; i < n_dirs(A); i++)
+        for (int j = 0; j < n_dirs(B); j++) {
+            const V3 L = cross(edge_dir(A, i), edge_dir(B, j));
+            const double l2 = dot(L, L);
+            if (l2 < 1e-12) continue;
+            const double len = std::sqrt(l2);
+            const V3 u = L * (1.0 / len);
+            const double s = std::fabs(dot(D, u)) - (support(A, u) + support(B, u));
+            if (s >= margin) return r;
+            if (ea < 0 || s > se) { ea = i; eb = j; se = s; le = u; }
+        }
+    int kind = 0, i = fa, j = -1; double s = sa; V3 L = face_dir(A, fa);
+    if (sb > sa + 1e-5) { kind = 1; i = fb; s = sb; L = face_dir(B, fb); }
+    if (ea >= 0 && se > s + 1e-4 + 0.05 * std::fabs(s)) { kind = 2; i = ea; j = eb; s = se; L = le; }
+    if (dot(L, D) < 0) L = -L;
+    r.touching = true; r.kind = kind; r.i = i; r.j = j; r.sep = s; r.n = L;
+    return r;
+}
+
+// Face contact between convex bodies: reference face f of `ref` with outward normal nref.
+int face_contact_convex(const Body& ref, int f, V3 nref, const Body& inc, const oracle_params& P,
+                        V3* pts, double* dep, uint64_t* ev) {
+    struct Side { V3 a; double h; };
+    std::vector<Side> sides;
+    V3 fc;
+    if (!ref.cyl) {
+        fc = ref.x + nref * ref.h[f];
+        const int k1 = (f == 0) ? 1 : 0, k2 = (f == 2) ? 1 : 2;
+        const V3 u = axis(ref, k1), v = axis(ref, k2);
+        sides = {{u, ref.h[k1]}, {-u, ref.h[k1]}, {v, ref.h[k2]}, {-v, ref.h[k2]}};
+    } else if (f == 0) {
+        fc = ref.x + nref * ref.h[2];
+        for (int s = 0; s < 16; s++) sides.push_back({side_normal(ref, s), cyl_apothem(ref)});
+    } else {
+        const int s = dot(side_normal(ref, f - 1), nref) > 0 ? f - 1 : f + 7;
+        fc = ref.x + nref * cyl_apothem(ref);
+        const V3 ez = axis(ref, 2), t = side_tangent(ref, s);
+        const double w = ref.h[0] * G64().half_edge;
+        sides = {{ez, ref.h[2]}, {-ez, ref.h[2]}, {t, w}, {-t, w}};
+    }
+    std::vector<V3> poly;
+    if (!inc.cyl) {
+        int best_f = 0;
+        double best = 0;
+        for (int m = 0; m < 3; m++) {
+            const double dm = dot(axis(inc, m), nref);
+            if (m == 0 || dm < best) { best = dm; best_f = 2 * m; }
+            if (-dm < best) { best = -dm; best_f = 2 * m + 1; }
+        }
+        const int mi = best_f / 2;
+        const double si = (best_f % 2 == 0) ? 1.0 : -1.0;
+        const int m1 = (mi == 0) ? 1 : 0, m2 = (mi == 2) ? 1 : 2;
+        const V3 fi = inc.x + axis(inc, mi) * (si * inc.h[mi]);
+        const V3 e1 = axis(inc, m1) * inc.h[m1], e2 = axis(inc, m2) * inc.h[m2];
+        poly = {fi + e1 + e2, fi - e1 + e2, fi - e1 - e2, fi + e1 - e2};
+    } else {
+        // candidates in order: top cap, bottom cap, sides 0..15
+        const double dz = dot(axis(inc, 2), nref);
+        int best_c = 0;
+        double best = dz;
+        if (-dz < best) { best = -dz; best_c = 1; }
+        for (int s = 0; s < 16; s++) {
+            const double dm = dot(side_normal(inc, s), nref);
+            if (dm < best) { best = dm; best_c = 2 + s; }
+        }
+        if (best_c < 2) {
+            const double sz = best_c == 0 ? 1.0 : -1.0;
+            for (int k = 0; k < 16; k++) poly.push_back(cyl_vertex(inc, k, sz));
+        } else {
+            const int s = best_c - 2;
+            poly = {cyl_vertex(inc, s, 1.0), cyl_vertex(inc, s + 1, 1.0), cyl_vertex(inc, s + 1, -1.0),
+                    cyl_vertex(inc, s, -1.0)};
+        }
+    }
+    for (const Side& sd : sides) poly = clip_side(poly, fc, sd.a, sd.h, 32);
+    ev[EV_CLIP_VERTS] += poly.size();
+    std::vector<V3> kp;
+    std::vector<double> kd;
+    for (const V3& p : poly) {
+        const double d = dot(p - fc, nref);
+        if (d < P.margin) { kp.push_back(p); kd.push_back(d); }
+    }
+    return reduce_points(kp, kd, nref, pts, dep);
+}
+
+// Supporting edge of direction index j of body b toward L: centre, direction, half length.
+void support_edge(const Body& b, int j, V3 L, V3& c, V3& d, double& hl) {
+    if (!b.cyl) {
+        c = b.x;
+        for (int k = 0; k < 3; k++) {
+            if (k == j) continue;
+            const double sg = dot(axis(b, k), L) < 0 ? -1.0 : 1.0;
+            c = c + axis(b, k) * (sg * b.h[k]);
+        }
+        d = axis(b, j);
+        hl = b.h[j];
+    } else if (j == 0) {
+        int kb = 0;
+        double best = 0;
+        for (int k = 0; k < 16; k++) {
+            double vc, vs;
+            gon_vdir(k, vc, vs);
+            const double v = dot(plane_vec(b, vc, vs), L);
+            if (k == 0 || v > best) { best = v; kb = k; }
+        }
+        c = cyl_vertex(b, kb, 0.0);
+        d = axis(b, 2);
+        hl = b.h[2];
+    } else {
+        const int s = dot(side_normal(b, j - 1), L) >= 0 ? j - 1 : j + 7;
+        const double sz = dot(axis(b, 2), L) >= 0 ? 1.0 : -1.0;
+        c = b.x + side_normal(b, s) * cyl_apothem(b) + axis(b, 2) * (sz * b.h[2]);
+        d = side_tangent(b, s);
+        hl = b.h[0] * G64().half_edge;
+    }
+}
+
+bool convex_pair(const Body& A, int ia, const Body& B, int ib, const oracle_params& P, Manifold& M, uint64_t* ev) {
+    ev[EV_SAT]++;
+    const ConvexSat s = sat_convex(A, B, P.margin);
+    if (!s.touching) return false;
+    V3 pts[4];
+    double dep[4];
+    int np = 0;
+    if (s.kind == 0) {
+        ev[EV_FACE]++;
+        np = face_contact_convex(A, s.i, s.n, B, P, pts, dep, ev);
+    } else if (s.kind == 1) {
+        ev[EV_FACE]++;
+        np = face_contact_convex(B, s.i, -s.n, A, P, pts, dep, ev);
+    } else {
+        ev[EV_EDGE]++;
+        V3 pA, pB, dA, dB;
+        double ha, hb;
+        support_edge(A, s.i, s.n, pA, dA, ha);
+        support_edge(B, s.j, -s.n, pB, dB, hb);
+        const V3 r = pA - pB;
+        const double bb = dot(dA, dB), c = dot(dA, r), f = dot(dB, r);
+        const double den = 1.0 - bb * bb;
+        double sa = 0, tb;
+        if (den > 1e-12) { sa = (bb * f - c) / den; tb = f + sa * bb; }
+        else tb = f;
+        sa = std::min(std::max(sa, -ha), ha);
+        tb = std::min(std::max(tb, -hb), hb);
+        const V3 qa = pA + dA * sa, qb = pB + dB * tb;
+        pts[0] = (qa + qb) * 0.5;
+        dep[0] = s.sep;
+        np = 1;
+    }
+    if (np == 0) return false;
+    M.A = ia; M.B = ib;
+    M.n = s.n;
+    M.np = np;
+    for (int k = 0; k < np; k++) {
+        M.c[k].p = pts[k];
+        M.c[k].d = dep[k];
+        M.c[k].rA = pts[k] - A.x;
+        M.c[k].rB = pts[k] - B.x;
+    }
+    return true;
+}
+
+// Cylinder against the table plane: its 32 vertices (bottom cap k = 0..15, then top cap)
+// lower than the margin; four or fewer are kept deepest first (ties by vertex index),
+// more are reduced to four as for face contacts.  Normal +z.
+bool cyl_plane(const Body& b, int bi, const oracle_params& P, Manifold& M) {
+    std::vector<V3> kp;
+    std::vector<double> kd;
+    std::vector<int> kv;
+    for (int v = 0; v < 32; v++) {
+        const V3 r = cyl_vertex(b, v & 15, v < 16 ? -1.0 : 1.0) - b.x;
+        const double d = b.x.z + r.z;
+        if (d < P.margin) { kp.push_back(r); kd.push_back(d); kv.push_back(v); }
+    }
+    const int nc = (int)kp.size();
+    if (nc == 0) return false;
+    V3 pts[4];
+    double dep[4];
+    int np;
+    if (nc <= 4) {
+        std::vector<int> o(nc);
+        for (int i = 0; i < nc; i++) o[i] = i;
+        std::sort(o.begin(), o.end(), [&](int a, int c) { return kd[a] < kd[c] || (kd[a] == kd[c] && kv[a] < kv[c]); });
+        for (int i = 0; i < nc; i++) { pts[i] = kp[o[i]]; dep[i] = kd[o[i]]; }
+        np = nc;
+    } else {
+        np = reduce_points(kp, kd, {0, 0, 1}, pts, dep);
+    }
+    M.A = PLANE; M.B = bi;
+    M.n = {0, 0, 1};
+    M.np = np;
+    for (int k = 0; k < np; k++) {
+        Contact& C = M.c[k];
+        C.rB = pts[k];
+        C.p = b.x + pts[k];
+        C.rA = {0, 0, 0};
+        C.d = dep[k];
+    }
+    return true;
+}
+
+// Capsule pusher against a cylinder: as against a box, with the cylinder's vertical
+// extent h |R_22| + r (16-gon support of (R_20, R_21)) and its closest point to a
+// segment point S -- the prism is the 16-gon times [-h, h] in its frame, so the closest
+// point is the 16-gon's closest point to S's body-plane coordinates (S's own when
+// inside; else the nearest point of the nearest edge, earliest edge on ties) with the
+// axial coordinate clamped.  Inside the prism the depth is the smallest distance to a
+// face.
+bool capsule_cyl(const Body& b, int bi, V3 Pp, const oracle_params& P, Manifold& M) {
+    const double ez = gon_support(b.R[6], b.R[7]) * b.h[0] + std::fabs(b.R[8]) * b.h[2];
+    const double zlo = b.x.z - ez, zhi = b.x.z + ez;
+    const double za = std::max(P.pusher_z0, zlo), zb = std::min(P.pusher_z1, zhi);
+    double zc[2];
+    int nc;
+    if (za > zb) { zc[0] = (zhi < P.pusher_z0) ? P.pusher_z0 : P.pusher_z1; nc = 1; }
+    else if (zb - za < 1e-3) { zc[0] = (za + zb) * 0.5; nc = 1; }
+    else { zc[0] = za; zc[1] = zb; nc = 2; }
+    const double r = b.h[0], apo = cyl_apothem(b);
+    int np = 0;
+    double best_d = 0;
+    V3 best_n{1, 0, 0};
+    for (int i = 0; i < nc; i++) {
+        const V3 S = {Pp.x, Pp.y, zc[i]};
+        const V3 rel = S - b.x;
+        const double lx = dot(axis(b, 0), rel), ly = dot(axis(b, 1), rel), lz = dot(axis(b, 2), rel);
+        bool inside = true;
+        double pen_side = 1e300;
+        for (int s = 0; s < 16; s++) {
+            double fcs, fss;
+            gon_fdir(s, fcs, fss);
+            const double g = apo - (fcs * lx + fss * ly);
+            if (g < 0) inside = false;
+            pen_side = std::min(pen_side, g);
+        }
+        double qx = lx, qy = ly;
+        if (!inside) {
+            double bd = 0;
+            for (int s = 0; s < 16; s++) {
+                double c0, s0, c1, s1;
+                gon_vdir(s, c0, s0);
+                gon_vdir((s + 1) & 15, c1, s1);
+                const double ax = r * c0, ay = r * s0, ex = r * c1 - ax, ey = r * s1 - ay;
+                double t = ((lx - ax) * ex + (ly - ay) * ey) / (ex * ex + ey * ey);
+                t = std::min(std::max(t, 0.0), 1.0);
+                const double px = ax + ex * t, py = ay + ey * t;
+                const double dd = (lx - px) * (lx - px) + (ly - py) * (ly - py);
+                if (s == 0 || dd < bd) { bd = dd; qx = px; qy = py; }
+            }
+        }
+        const double qz = std::min(std::max(lz, -b.h[2]), b.h[2]);
+        const V3 Q = b.x + axis(b, 0) * qx + axis(b, 1) * qy + axis(b, 2) * qz;
+        const V3 diff = S - Q;
+        const double dist = norm(diff);
+        V3 nrm;
+        double d;
+        if (dist > 1e-6) {
+            nrm = diff * (1.0 / dist);
+            d = dist - P.pusher_radius;
+        } else {
+            const double pen = std::min(b.h[2] - std::fabs(lz), pen_side);
+            d = -pen - P.pusher_radius;
+            const V3 w = {S.x - b.x.x, S.y - b.x.y, 0};
+            const double lw = norm(w);
+            nrm = lw > 1e-9 ? w * (1.0 / lw) : V3{1, 0, 0};
+        }
+        if (!(d < P.margin)) continue;
+        Contact& C = M.c[np];
+        C.p = Q;
+        C.d = d;
+        C.rA = Q - b.x;
+        C.rB = {0, 0, 0};
+        if (np == 0 || d < best_d) { best_d = d; best_n = nrm; }
+        np++;
+    }
+    if (np == 0) return false;
+    M.A = bi; M.B = PUSHER;
+    M.n = best_n;
+    M.np = np;
+    return true;
+}
+
 // ---- one substep ---------------------------------------------------------------------
 
 void refresh_body_frames(Env& E) {
@@ -849,6 +1282,7 @@ std::vector<Manifold> collide(Env& E, const oracle_params& P) {
         x[3 * i] = E.b[i].x.x; x[3 * i + 1] = E.b[i].x.y; x[3 * i + 2] = E.b[i].x.z;
         for (int k = 0; k < 4; k++) q[4 * i + k] = E.b[i].q[k];
         for (int k = 0; k < 3; k++) h[3 * i + k] = E.b[i].h[k];
+        if (E.b[i].cyl) h[3 * i + 1] = -h[3 * i + 1];  // keep the cylinder mark
     }
     const double Pxy[2] = {E.P.x, E.P.y};
     PairList<double> pl = broadphase<double>(n, x.data(), q.data(), h.data(), P.margin, E.push.active, Pxy,
@@ -868,7 +1302,9 @@ std::vector<Manifold> collide(Env& E, const oracle_params& P) {
     for (size_t k = 0; k < pl.bb_i.size() && !stop; k++) {
         Manifold M;
         const int i = pl.bb_i[k], j = pl.bb_j[k];
-        if (box_box(E.b[i], i, E.b[j], j, P, M, E.ev)) {
+        const bool hit = (E.b[i].cyl || E.b[j].cyl) ? convex_pair(E.b[i], i, E.b[j], j, P, M, E.ev)
+                                                    : box_box(E.b[i], i, E.b[j], j, P, M, E.ev);
+        if (hit) {
             const double mu = std::sqrt(E.b[i].mu * E.b[j].mu);
             M.mu = mu;
             const size_t before = ms.size();
@@ -880,13 +1316,13 @@ std::vector<Manifold> collide(Env& E, const oracle_params& P) {
         if (stop) break;
         E.ev[EV_PLANE]++;
         Manifold M;
-        if (box_plane(E.b[i], i, P, M)) { M.mu = std::sqrt(E.b[i].mu * P.table_mu); emit(M); }
+        if (E.b[i].cyl ? cyl_plane(E.b[i], i, P, M) : box_plane(E.b[i], i, P, M)) { M.mu = std::sqrt(E.b[i].mu * P.table_mu); emit(M); }
     }
     for (int i : pl.pusher) {
         if (stop) break;
         E.ev[EV_PUSHER]++;
         Manifold M;
-        if (capsule_box(E.b[i], i, E.P, P, M)) { M.mu = std::sqrt(E.b[i].mu * P.pusher_mu); emit(M); }
+        if (E.b[i].cyl ? capsule_cyl(E.b[i], i, E.P, P, M) : capsule_box(E.b[i], i, E.P, P, M)) { M.mu = std::sqrt(E.b[i].mu * P.pusher_mu); emit(M); }
     }
     E.ev[EV_MANIFOLDS] += ms.size();
     E.ev[EV_POINTS] += npts;
@@ -1140,6 +1576,7 @@ void env_arrays(const Env& E, std::vector<double>& x, std::vector<double>& q, st
         x[3 * i] = E.b[i].x.x; x[3 * i + 1] = E.b[i].x.y; x[3 * i + 2] = E.b[i].x.z;
         for (int k = 0; k < 4; k++) q[4 * i + k] = E.b[i].q[k];
         for (int k = 0; k < 3; k++) h[3 * i + k] = E.b[i].h[k];
+        if (E.b[i].cyl) h[3 * i + 1] = -h[3 * i + 1];  // keep the cylinder mark
     }
 }
 
@@ -1298,7 +1735,9 @@ int oracle_contacts(const oracle_params* P, int n, const double* state13, const 
 
 // Separating-axis result for a pair of boxes (state rows of 13): separation, axis id,
 // normal A->B, contact points and depths.  Returns the number of contact points, or -1
-// when the boxes are farther apart than the margin.
+// when the boxes are farther apart than the margin.  When either body is a cylinder the
+// general convex test decides and the axis id is f (face f of A), 100 + f (face f of B)
+// or 200 + 9 i + j (edge directions i of A and j of B).
 int oracle_box_box(const double* sA, const float* hA, const double* sB, const float* hB, double margin,
                    double* out_sep, int32_t* out_axis, double* out_n, double* out_p, double* out_d) {
     oracle_params P;
@@ -1312,6 +1751,20 @@ int oracle_box_box(const double* sA, const float* hA, const double* sB, const fl
     const float m[2] = {1, 1}, mu[2] = {0.5f, 0.5f};
     load_env(E, 2, s, h, m, mu);
     refresh_body_frames(E);
+    if (E.b[0].cyl || E.b[1].cyl) {
+        const ConvexSat c = sat_convex(E.b[0], E.b[1], margin);
+        if (!c.touching) return -1;
+        *out_sep = c.sep;
+        *out_axis = c.kind == 2 ? 200 + 9 * c.i + c.j : 100 * c.kind + c.i;
+        out_n[0] = c.n.x; out_n[1] = c.n.y; out_n[2] = c.n.z;
+        Manifold M;
+        if (!convex_pair(E.b[0], 0, E.b[1], 1, P, M, E.ev)) return 0;
+        for (int k = 0; k < M.np; k++) {
+            out_p[3 * k] = M.c[k].p.x; out_p[3 * k + 1] = M.c[k].p.y; out_p[3 * k + 2] = M.c[k].p.z;
+            out_d[k] = M.c[k].d;
+        }
+        return M.np;
+    }
     const SatResult r = sat(E.b[0], E.b[1], margin);
     if (!r.touching) return -1;
     *out_sep = r.sep; *out_axis = r.axis;

@@ -11,7 +11,8 @@ Scene arrays (CSR over boxes, all little-endian, C-contiguous):
   box_offset int32[S+1]   boxes of scene s are rows box_offset[s]:box_offset[s+1]
   pose       float32[B,7] x, y, z, qw, qx, qy, qz
   vel        float32[B,6] linear xyz, angular xyz (zeros: boxes start at rest)
-  half       float32[B,3] half-extents (m)
+  half       float32[B,3] half-extents (m); a row (r, -r, h) is an upright cylinder of
+                          radius r and half height h about its body z axis
   mass       float32[B]   kg
   mu         float32[B]   Coulomb friction coefficient
   target     int32[S]     local index of the target box in its scene
@@ -73,6 +74,16 @@ def concat(parts) -> Scenes:
                    else np.zeros(0, np.int32)).astype(np.int32))
 
 
+def cylinder_half(r: float, h: float) -> np.ndarray:
+    """Half-extent row of a cylinder of radius r and half height h."""
+    return np.array([r, -r, h], np.float32)
+
+
+def is_cylinder(half) -> np.ndarray:
+    """Cylinder mask of half-extent rows (negative second entry)."""
+    return np.asarray(half)[..., 1] < 0
+
+
 def _corners(cx, cy, hx, hy, yaw):
     """Corners [..., 4, 2] of yawed rectangles (broadcast over leading dims)."""
     c, s = np.cos(yaw), np.sin(yaw)
@@ -122,15 +133,25 @@ def _yaw_quat(yaw):
 def make_scene(rng: np.random.Generator, n: int, *, half_lo=0.015, half_hi=0.03,
                mass_lo=0.05, mass_hi=0.2, mu_lo=0.5, mu_hi=0.5, yaw_hi=0.0,
                region_half=0.08, density_scale=None, attempts=1000,
-               target_at_centre=False) -> Scenes:
+               target_at_centre=False, cyl_frac=0.0, target_cylinder=False) -> Scenes:
     """One scene of up to n boxes placed by rejection sampling inside a centred square
     clutter region; boxes rest on the plane (z = h_z) with zero velocity.  Boxes that
     fail `attempts` placements are dropped (so the final count may be below n).
-    Box 0 is the target."""
+    Box 0 is the target.  With cyl_frac > 0 each object is an upright cylinder with that
+    probability (radius min(h_x, h_y) of its drawn extents, half height h_z), and
+    target_cylinder makes object 0 one; these draws follow all the others, so scenes
+    without cylinders are unchanged."""
     halves = rng.uniform(half_lo, half_hi, size=(n, 3))
     masses = rng.uniform(mass_lo, mass_hi, size=n) if mass_hi > mass_lo else np.full(n, mass_lo)
     mus = rng.uniform(mu_lo, mu_hi, size=n) if mu_hi > mu_lo else np.full(n, mu_lo)
     yaws = rng.uniform(0.0, yaw_hi, size=n) if yaw_hi > 0 else np.zeros(n)
+    cyl = np.zeros(n, bool)
+    if cyl_frac > 0 or target_cylinder:
+        cyl = rng.uniform(size=n) < cyl_frac
+        cyl[0] |= target_cylinder
+        r = np.minimum(halves[:, 0], halves[:, 1])
+        halves[cyl, 0] = r[cyl]
+        halves[cyl, 1] = r[cyl]
     if density_scale is not None:
         area = float(np.sum(4 * halves[:, 0] * halves[:, 1]))
         region_half = min(math.sqrt(area / density_scale) / 2, TABLE_HALF)
@@ -156,7 +177,7 @@ def make_scene(rng: np.random.Generator, n: int, *, half_lo=0.015, half_hi=0.03,
             if free.any():
                 j = int(np.argmax(free))
                 cx, cy = xy[j]
-                placed.append((cx, cy, hx, hy, yaws[i], halves[i, 2], masses[i], mus[i]))
+                placed.append((cx, cy, hx, hy, yaws[i], halves[i, 2], masses[i], mus[i], bool(cyl[i])))
                 arr = np.vstack([arr, [cx, cy, hx, hy, yaws[i]]])
                 ok = True
         if not ok and i == 0:
@@ -168,6 +189,8 @@ def make_scene(rng: np.random.Generator, n: int, *, half_lo=0.015, half_hi=0.03,
         pose[k, :3] = (p[0], p[1], p[5])
         pose[k, 3:] = _yaw_quat(p[4])
         half[k] = (p[2], p[3], p[5])
+        if p[8]:
+            half[k, 1] = -p[2]
     return Scenes(np.array([0, m], np.int32), pose.astype(np.float32),
                   np.zeros((m, 6), np.float32), half.astype(np.float32),
                   np.array([p[6] for p in placed], np.float32),
@@ -175,7 +198,10 @@ def make_scene(rng: np.random.Generator, n: int, *, half_lo=0.015, half_hi=0.03,
 
 
 def _support_half_width(half, quat, d):
-    """Half-width of an upright yawed box's footprint along the unit 2-D direction d."""
+    """Half-width of an upright yawed box's footprint along the unit 2-D direction d (a
+    cylinder's radius)."""
+    if half[1] < 0:
+        return float(half[0])
     yaw = 2 * math.atan2(quat[3], quat[0])
     u = (math.cos(yaw), math.sin(yaw))
     v = (-u[1], u[0])
@@ -244,7 +270,7 @@ def _random_valid_push(rng, sc: Scenes, s: int, attempts=200):
             dx, dy = sx - pose[i, 0], sy - pose[i, 1]
             lu, lv = c * dx + sn * dy, -sn * dx + c * dy
             qu = max(abs(lu) - half[i, 0], 0.0)
-            qv = max(abs(lv) - half[i, 1], 0.0)
+            qv = max(abs(lv) - abs(half[i, 1]), 0.0)
             if qu * qu + qv * qv < (PUSHER_RADIUS + 1e-3) ** 2:
                 clear = False
                 break
@@ -282,6 +308,39 @@ def config_uneven(seed: int = 3, n_envs: int = 4096, n_lo=5, n_hi=40, workers: i
             res = pool.map(_uneven_scene, jobs, chunksize=max(1, n_envs // (8 * workers)))
     else:
         res = [_uneven_scene(j) for j in jobs]
+    scenes = concat([r[0] for r in res])
+    pushes = np.stack([r[1] for r in res]) if res else np.zeros((0, 4), np.float32)
+    seeds = np.random.default_rng(children[-1]).integers(0, 2 ** 63, size=n_envs, dtype=np.uint64)
+    return scenes, pushes, seeds
+
+
+def _cyl_scene(args):
+    ss, n_lo, n_hi, frac = args
+    rng = np.random.default_rng(ss)
+    n = int(rng.integers(n_lo, n_hi + 1))
+    rho = rng.uniform(0.2, 0.6)
+    sc = make_scene(rng, n, half_lo=0.01, half_hi=0.04, mu_lo=0.3, mu_hi=0.8,
+                    yaw_hi=math.pi / 2, density_scale=rho, attempts=1000,
+                    cyl_frac=frac, target_cylinder=True)
+    return sc, _random_valid_push(rng, sc, 0)
+
+
+def config_cylinders(seed: int = 5, n_envs: int = 4096, n_lo=5, n_hi=40, cyl_frac=0.3, workers: int = 0):
+    """The uneven workload with cylinders: per scene the same distributions as
+    config_uneven, each object an upright cylinder with probability cyl_frac and the
+    target always one (the paper's target object is a small cylinder)."""
+    root = np.random.SeedSequence(seed)
+    children = root.spawn(n_envs + 1)
+    jobs = [(children[e], n_lo, n_hi, cyl_frac) for e in range(n_envs)]
+    if workers == 0:
+        import os
+        workers = (os.cpu_count() or 1) if n_envs >= 256 else 1
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_cyl_scene, jobs, chunksize=max(1, n_envs // (8 * workers)))
+    else:
+        res = [_cyl_scene(j) for j in jobs]
     scenes = concat([r[0] for r in res])
     pushes = np.stack([r[1] for r in res]) if res else np.zeros((0, 4), np.float32)
     seeds = np.random.default_rng(children[-1]).integers(0, 2 ** 63, size=n_envs, dtype=np.uint64)

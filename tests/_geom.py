@@ -48,3 +48,30 @@ def box_row(x, y, z, q=(1, 0, 0, 0), v=(0, 0, 0), w=(0, 0, 0)):
 
 def yaw_q(yaw):
     return (math.cos(yaw / 2), 0.0, 0.0, math.sin(yaw / 2))
+
+
+def cyl_vertices(state_row, r, h):
+    """The 32 corners of the right prism over the regular 16-gon inscribed in a cylinder
+    of radius r and half height h: cap vertex k at angle k pi/8 in the body xy plane,
+    bottom cap (k = 0..15) then top cap."""
+    R = rotmat(state_row[3:7])
+    c = np.asarray(state_row[:3], np.float64)
+    ang = np.arange(16) * np.pi / 8
+    out = []
+    for z in (-h, h):
+        for a in ang:
+            out.append(c + R @ np.array([r * math.cos(a), r * math.sin(a), z]))
+    return np.array(out)
+
+
+def body_vertices(state_row, half):
+    """Corners of a box, or of a cylinder's prism when half = (r, -r, h)."""
+    half = np.asarray(half, np.float64)
+    if half[1] < 0:
+        return cyl_vertices(state_row, half[0], half[2])
+    return vertices(state_row, half)
+
+
+def body_gap(stA, hA, stB, hB, L):
+    """min over B's corners of L.x minus max over A's corners of L.x."""
+    return (body_vertices(stB, hB) @ L).min() - (body_vertices(stA, hA) @ L).max()
