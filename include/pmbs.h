@@ -112,8 +112,15 @@ typedef struct {
                                       engine's own output and are not re-checked) */
     int warm_start;             /* 0 (default): contact impulses start at zero every substep;
                                    1: a point takes the impulses of the nearest point of the
-                                   same body pair in the previous substep (see DESIGN) */
+                                   same body pair in the previous substep (matched within
+                                   warm_tolerance in the frame of the pair's first dynamic
+                                   body; friction carried as a world vector) */
     float warm_tolerance;       /* 2e-3 m: match distance for warm starting */
+    int cylinders;              /* pmbs_rollout_noalloc only: 1 = the records may hold cylinders
+                                   (runs the solver built with the cylinder contact paths);
+                                   0 (default) = boxes only, cylinder rows are then simulated
+                                   as nothing sensible and must not be passed.  The other
+                                   entry points decide from the loaded scenes. */
 } pmbs_config;
 
 /* Fill *cfg with the defaults listed above.  Never fails. */

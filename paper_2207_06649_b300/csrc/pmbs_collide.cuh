@@ -9,6 +9,8 @@
 #pragma once
 #include <cstdint>
 
+#include "pmbs_exact.cuh"
+
 namespace pmbs {
 
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
@@ -22,11 +24,13 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 }
 __device__ __forceinline__ float norm3(float3 a) { return sqrtf(dot3(a, a)); }
 
-// A box for collision: centre, row-major rotation (columns = axes), half extents.
+// A box (or cylinder) for collision: centre, row-major rotation (columns = axes), half
+// extents; a cylinder has cyl set and h = (r, r, half height).
 struct CBox {
     float3 c;
     float R[9];
     float h[3];
+    bool cyl;
     __device__ __forceinline__ float3 ax(int k) const { return f3(R[k], R[3 + k], R[6 + k]); }
     // runtime index through selects (keeps the box in registers)
     __device__ __forceinline__ float3 axs(int k) const { return k == 0 ? ax(0) : (k == 1 ? ax(1) : ax(2)); }
@@ -384,6 +388,506 @@ __device__ __forceinline__ void collide_capsule_box(const CBox& b, float px, flo
             pen = fminf(pen, b.h[1] - fabsf(loc[1]));
             pen = fminf(pen, b.h[2] - fabsf(loc[2]));
             d = -pen - r;
+            const float3 w = f3(S.x - b.c.x, S.y - b.c.y, 0.f);
+            const float lw = norm3(w);
+            nrm = lw > 1e-9f ? w * (1.f / lw) : f3(1.f, 0.f, 0.f);
+        }
+        if (!(d < margin)) continue;
+        if (M.np == 0) {
+            M.p[0] = Q;
+            M.d[0] = d;
+        } else {
+            M.p[1] = Q;
+            M.d[1] = d;
+        }
+        if (M.np == 0 || d < best_d) {
+            best_d = d;
+            best_n = nrm;
+        }
+        M.np++;
+    }
+    M.n = best_n;
+}
+
+// ------------------------------------------------------------------ cylinders
+// Pairs with a cylinder (a 16-gon prism, see pmbs_exact.cuh) take the general
+// separating-axis test of two convex polyhedra: face normal directions of A (box: its 3
+// axes; cylinder: its cap axis, then the 8 side normal directions), those of B, and the
+// cross products of an edge direction of A with one of B (box: its 3 axes; cylinder: its
+// axis, then the 8 cap edge directions; skipped when |cross|^2 < 1e-12).  Separation along
+// a unit axis is |L.D| minus both support half widths; the selection thresholds are the
+// box-box test's.  A face axis clips the other body's incident face (most anti-parallel
+// outward normal) against the reference face's side planes (at most 32 vertices) and
+// reduces to four points; an edge axis gives one point midway between the closest points
+// of the two supporting edges.
+
+__device__ __forceinline__ void gon_vdir(int k, float& c, float& s) {
+    const float g = k < 8 ? 1.f : -1.f;
+    c = g * kGonC[k & 7];
+    s = g * kGonS[k & 7];
+}
+__device__ __forceinline__ void gon_fdir(int k, float& c, float& s) {
+    const float g = k < 8 ? 1.f : -1.f;
+    c = g * kGonFC[k & 7];
+    s = g * kGonFS[k & 7];
+}
+__device__ __forceinline__ float3 plane_vec(const CBox& b, float c, float s) { return b.ax(0) * c + b.ax(1) * s; }
+__device__ __forceinline__ float3 side_normal(const CBox& b, int k) {
+    float c, s;
+    gon_fdir(k, c, s);
+    return plane_vec(b, c, s);
+}
+__device__ __forceinline__ float3 side_tangent(const CBox& b, int k) {
+    float c, s;
+    gon_fdir(k, c, s);
+    return plane_vec(b, -s, c);
+}
+__device__ __forceinline__ float3 cyl_vertex(const CBox& b, int k, float sz) {
+    float c, s;
+    gon_vdir(k & 15, c, s);
+    return b.c + plane_vec(b, c * b.h[0], s * b.h[0]) + b.ax(2) * (sz * b.h[2]);
+}
+__device__ __forceinline__ float gon_sup(float p0, float p1) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) m = fmaxf(m, fabsf(kGonC[k] * p0 + kGonS[k] * p1));
+    return m;
+}
+__device__ __forceinline__ float support(const CBox& b, float3 L) {
+    if (b.cyl) return gon_sup(dot3(b.ax(0), L), dot3(b.ax(1), L)) * b.h[0] + fabsf(dot3(b.ax(2), L)) * b.h[2];
+    return (b.h[0] * fabsf(dot3(b.ax(0), L)) + b.h[1] * fabsf(dot3(b.ax(1), L))) + b.h[2] * fabsf(dot3(b.ax(2), L));
+}
+__device__ __forceinline__ int n_dirs(const CBox& b) { return b.cyl ? 9 : 3; }
+__device__ __forceinline__ float3 face_dir(const CBox& b, int f) {
+    return !b.cyl ? b.axs(f) : (f == 0 ? b.ax(2) : side_normal(b, f - 1));
+}
+__device__ __forceinline__ float face_half(const CBox& b, int f) {
+    return !b.cyl ? b.hs(f) : (f == 0 ? b.h[2] : b.h[0] * kGonApo);
+}
+__device__ __forceinline__ float3 edge_dir(const CBox& b, int j) {
+    return !b.cyl ? b.axs(j) : (j == 0 ? b.ax(2) : side_tangent(b, j - 1));
+}
+
+// At most four of nk candidate points B (separations kd, normal nref): all when nk <= 4;
+// else the deepest (earliest on ties), the farthest from it, the one spanning the largest
+// triangle with those two, the one adding the largest area outside an edge.
+__device__ __forceinline__ int reduce_points(const float3* B, const float* kd, int nk, float3 nref, CManifold& M) {
+    if (nk <= 4) {
+        for (int i = 0; i < nk; i++) {
+            M.p[i] = B[i];
+            M.d[i] = kd[i];
+        }
+        return nk;
+    }
+    unsigned used = 0;
+    int i1 = 0;
+    for (int i = 1; i < nk; i++)
+        if (kd[i] < kd[i1]) i1 = i;
+    used |= 1u << i1;
+    int i2 = -1;
+    float b2 = -1.f;
+    for (int i = 0; i < nk; i++) {
+        if (used >> i & 1u) continue;
+        const float3 e = B[i] - B[i1];
+        const float l = dot3(e, e);
+        if (i2 < 0 || l > b2) {
+            b2 = l;
+            i2 = i;
+        }
+    }
+    used |= 1u << i2;
+    int i3 = -1;
+    float b3 = -1.f;
+    for (int i = 0; i < nk; i++) {
+        if (used >> i & 1u) continue;
+        const float a = fabsf(dot3(cross3(B[i2] - B[i1], B[i] - B[i1]), nref));
+        if (i3 < 0 || a > b3) {
+            b3 = a;
+            i3 = i;
+        }
+    }
+    used |= 1u << i3;
+    const float sgn = dot3(cross3(B[i2] - B[i1], B[i3] - B[i1]), nref) < 0.f ? -1.f : 1.f;
+    int i4 = -1;
+    float b4 = 0.f;
+    for (int i = 0; i < nk; i++) {
+        if (used >> i & 1u) continue;
+        float a = -sgn * dot3(cross3(B[i2] - B[i1], B[i] - B[i1]), nref);
+        a = fmaxf(a, -sgn * dot3(cross3(B[i3] - B[i2], B[i] - B[i2]), nref));
+        a = fmaxf(a, -sgn * dot3(cross3(B[i1] - B[i3], B[i] - B[i3]), nref));
+        if (i4 < 0 || a > b4) {
+            b4 = a;
+            i4 = i;
+        }
+    }
+    M.p[0] = B[i1];
+    M.d[0] = kd[i1];
+    M.p[1] = B[i2];
+    M.d[1] = kd[i2];
+    M.p[2] = B[i3];
+    M.d[2] = kd[i3];
+    M.p[3] = B[i4];
+    M.d[3] = kd[i4];
+    return 4;
+}
+
+// Sutherland-Hodgman clip against dot(p - o, a) - h <= 0, at most 32 vertices kept.
+__device__ __forceinline__ int clip_side32(const float3* in, int n, float3* out, float3 o, float3 a, float h) {
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        const float3 cur = in[i];
+        const float3 prev = in[(i + n - 1) % n];
+        const float dc = dot3(cur - o, a) - h, dp = dot3(prev - o, a) - h;
+        if (dc <= 0.f) {
+            if (dp > 0.f && m < 32) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
+            if (m < 32) out[m++] = cur;
+        } else if (dp <= 0.f) {
+            if (m < 32) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
+        }
+    }
+    return m;
+}
+
+// Face contact between convex bodies: reference face f of ref (outward normal nref).
+__device__ __noinline__ int face_contact_convex(const CBox& ref, int f, float3 nref, const CBox& inc, float margin,
+                                                CManifold& M, int& clip_verts) {
+    // reference face: centre and side planes (origin fc)
+    float3 fc;
+    int nside, rs = 0;
+    if (!ref.cyl) {
+        fc = ref.c + nref * ref.hs(f);
+        nside = 4;
+    } else if (f == 0) {
+        fc = ref.c + nref * ref.h[2];
+        nside = 16;
+    } else {
+        rs = dot3(side_normal(ref, f - 1), nref) > 0.f ? f - 1 : f + 7;
+        fc = ref.c + nref * (ref.h[0] * kGonApo);
+        nside = 4;
+    }
+    float3 P[2][32];
+    int n;
+    if (!inc.cyl) {
+        int best_f = 0;
+        float best = 0.f;
+        for (int m = 0; m < 3; m++) {
+            const float dm = dot3(inc.axs(m), nref);
+            if (m == 0 || dm < best) {
+                best = dm;
+                best_f = 2 * m;
+            }
+            if (-dm < best) {
+                best = -dm;
+                best_f = 2 * m + 1;
+            }
+        }
+        const int mi = best_f >> 1;
+        const float si = (best_f & 1) ? -1.f : 1.f;
+        const int m1 = (mi == 0) ? 1 : 0, m2 = (mi == 2) ? 1 : 2;
+        const float3 fi = inc.c + inc.axs(mi) * (si * inc.hs(mi));
+        const float3 e1 = inc.axs(m1) * inc.hs(m1), e2 = inc.axs(m2) * inc.hs(m2);
+        P[0][0] = fi + e1 + e2;
+        P[0][1] = fi - e1 + e2;
+        P[0][2] = fi - e1 - e2;
+        P[0][3] = fi + e1 - e2;
+        n = 4;
+    } else {
+        // candidates: top cap, bottom cap, sides 0..15
+        const float dz = dot3(inc.ax(2), nref);
+        int best_c = 0;
+        float best = dz;
+        if (-dz < best) {
+            best = -dz;
+            best_c = 1;
+        }
+        for (int k = 0; k < 16; k++) {
+            const float dm = dot3(side_normal(inc, k), nref);
+            if (dm < best) {
+                best = dm;
+                best_c = 2 + k;
+            }
+        }
+        if (best_c < 2) {
+            const float sz = best_c == 0 ? 1.f : -1.f;
+            for (int k = 0; k < 16; k++) P[0][k] = cyl_vertex(inc, k, sz);
+            n = 16;
+        } else {
+            const int k = best_c - 2;
+            P[0][0] = cyl_vertex(inc, k, 1.f);
+            P[0][1] = cyl_vertex(inc, k + 1, 1.f);
+            P[0][2] = cyl_vertex(inc, k + 1, -1.f);
+            P[0][3] = cyl_vertex(inc, k, -1.f);
+            n = 4;
+        }
+    }
+    // the polygon alternates between the two buffers; an even number of sides ends in P[0]
+    for (int i = 0; i < nside; i++) {
+        float3 a;
+        float h;
+        if (!ref.cyl) {
+            const int k1 = (f == 0) ? 1 : 0, k2 = (f == 2) ? 1 : 2;
+            const int kk = i < 2 ? k1 : k2;
+            a = (i & 1) ? -ref.axs(kk) : ref.axs(kk);
+            h = ref.hs(kk);
+        } else if (f == 0) {
+            a = side_normal(ref, i);
+            h = ref.h[0] * kGonApo;
+        } else {
+            const float3 base = i < 2 ? ref.ax(2) : side_tangent(ref, rs);
+            a = (i & 1) ? -base : base;
+            h = i < 2 ? ref.h[2] : ref.h[0] * kGonHalfEdge;
+        }
+        n = clip_side32(P[i & 1], n, P[(i & 1) ^ 1], fc, a, h);
+    }
+    clip_verts += n;
+    float kd[32];
+    int nk = 0;
+    for (int i = 0; i < n; i++) {
+        const float d = dot3(P[0][i] - fc, nref);
+        if (d < margin) {
+            P[1][nk] = P[0][i];
+            kd[nk] = d;
+            nk++;
+        }
+    }
+    return reduce_points(P[1], kd, nk, nref, M);
+}
+
+// Supporting edge of direction index j of b toward L: centre, direction, half length.
+__device__ __forceinline__ void support_edge(const CBox& b, int j, float3 L, float3& c, float3& d, float& hl) {
+    if (!b.cyl) {
+        c = b.c;
+        for (int k = 0; k < 3; k++) {
+            if (k == j) continue;
+            const float sg = dot3(b.axs(k), L) < 0.f ? -1.f : 1.f;
+            c = c + b.axs(k) * (sg * b.hs(k));
+        }
+        d = b.axs(j);
+        hl = b.hs(j);
+    } else if (j == 0) {
+        int kb = 0;
+        float best = 0.f;
+        for (int k = 0; k < 16; k++) {
+            float vc, vs;
+            gon_vdir(k, vc, vs);
+            const float v = dot3(plane_vec(b, vc, vs), L);
+            if (k == 0 || v > best) {
+                best = v;
+                kb = k;
+            }
+        }
+        c = cyl_vertex(b, kb, 0.f);
+        d = b.ax(2);
+        hl = b.h[2];
+    } else {
+        const int s = dot3(side_normal(b, j - 1), L) >= 0.f ? j - 1 : j + 7;
+        const float sz = dot3(b.ax(2), L) >= 0.f ? 1.f : -1.f;
+        c = b.c + side_normal(b, s) * (b.h[0] * kGonApo) + b.ax(2) * (sz * b.h[2]);
+        d = side_tangent(b, s);
+        hl = b.h[0] * kGonHalfEdge;
+    }
+}
+
+// Convex pair with a cylinder (A = lower index).  Returns 0 none, 1 face, 2 edge; the
+// separation of the chosen axis in *sep_out when given.
+__device__ __noinline__ int collide_convex(const CBox& A, const CBox& B, float margin, CManifold& M, int& clip_verts,
+                                           float* sep_out = nullptr) {
+    M.np = 0;
+    const float3 D = B.c - A.c;
+    int fa = -1;
+    float sa = 0.f;
+    for (int f = 0; f < n_dirs(A); f++) {
+        const float3 L = face_dir(A, f);
+        const float s = fabsf(dot3(D, L)) - (face_half(A, f) + support(B, L));
+        if (s >= margin) return 0;
+        if (fa < 0 || s > sa) {
+            fa = f;
+            sa = s;
+        }
+    }
+    int fb = -1;
+    float sb = 0.f;
+    for (int f = 0; f < n_dirs(B); f++) {
+        const float3 L = face_dir(B, f);
+        const float s = fabsf(dot3(D, L)) - (support(A, L) + face_half(B, f));
+        if (s >= margin) return 0;
+        if (fb < 0 || s > sb) {
+            fb = f;
+            sb = s;
+        }
+    }
+    int ea = -1, eb = -1;
+    float se = 0.f;
+    float3 le = f3(0.f, 0.f, 0.f);
+    for (int i = 0; i < n_dirs(A); i++) {
+        const float3 dA = edge_dir(A, i);
+        for (int j = 0; j < n_dirs(B); j++) {
+            const float3 L = cross3(dA, edge_dir(B, j));
+            const float l2 = dot3(L, L);
+            if (l2 < 1e-12f) continue;
+            const float3 u = L * rsqrtf(l2);
+            const float s = fabsf(dot3(D, u)) - (support(A, u) + support(B, u));
+            if (s >= margin) return 0;
+            if (ea < 0 || s > se) {
+                ea = i;
+                eb = j;
+                se = s;
+                le = u;
+            }
+        }
+    }
+    int kind = 0, fi = fa;
+    float s = sa;
+    float3 L = face_dir(A, fa);
+    if (sb > sa + 1e-5f) {
+        kind = 1;
+        fi = fb;
+        s = sb;
+        L = face_dir(B, fb);
+    }
+    if (ea >= 0 && se > s + 1e-4f + 0.05f * fabsf(s)) {
+        kind = 2;
+        s = se;
+        L = le;
+    }
+    if (dot3(L, D) < 0.f) L = -L;
+    M.n = L;
+    if (sep_out) *sep_out = s;
+    if (kind < 2) {
+        const bool ar = kind == 0;
+        M.np = face_contact_convex(ar ? A : B, fi, ar ? L : -L, ar ? B : A, margin, M, clip_verts);
+        return M.np ? 1 : 0;
+    }
+    float3 pA, pB, dA, dB;
+    float ha, hb;
+    support_edge(A, ea, L, pA, dA, ha);
+    support_edge(B, eb, -L, pB, dB, hb);
+    const float3 r = pA - pB;
+    const float bb = dot3(dA, dB), c = dot3(dA, r), f = dot3(dB, r);
+    const float den = 1.f - bb * bb;
+    float ta = 0.f, tb;
+    if (den > 1e-12f) {
+        ta = (bb * f - c) / den;
+        tb = f + ta * bb;
+    } else {
+        tb = f;
+    }
+    ta = fminf(fmaxf(ta, -ha), ha);
+    tb = fminf(fmaxf(tb, -hb), hb);
+    const float3 qa = pA + dA * ta, qb = pB + dB * tb;
+    M.p[0] = (qa + qb) * 0.5f;
+    M.d[0] = s;
+    M.np = 1;
+    return 2;
+}
+
+// Cylinder against the plane z = 0 (A = plane, B = cylinder): its 32 vertices (bottom cap
+// k = 0..15, then top) below the margin; four or fewer kept deepest first (ties by vertex
+// index), more reduced to four as for face contacts.  p = offset from the centre.
+__device__ __noinline__ void collide_cyl_plane(const CBox& b, float margin, CManifold& M) {
+    M.np = 0;
+    M.n = f3(0.f, 0.f, 1.f);
+    float3 B[32];
+    float kd[32];
+    int nk = 0;
+    for (int v = 0; v < 32; v++) {
+        const float3 r = cyl_vertex(b, v & 15, v < 16 ? -1.f : 1.f) - b.c;
+        const float d = b.c.z + r.z;
+        if (d < margin) {
+            B[nk] = r;
+            kd[nk] = d;
+            nk++;
+        }
+    }
+    if (nk > 4) {
+        M.np = reduce_points(B, kd, nk, M.n, M);
+        return;
+    }
+    // stable insertion by depth (candidates arrive in vertex order)
+    for (int i = 0; i < nk; i++) {
+        int k = M.np;
+        while (k > 0 && kd[i] < M.d[k - 1]) {
+            M.d[k] = M.d[k - 1];
+            M.p[k] = M.p[k - 1];
+            k--;
+        }
+        M.d[k] = kd[i];
+        M.p[k] = B[i];
+        M.np++;
+    }
+}
+
+// Vertical capsule against a cylinder (A = cylinder, B = pusher): as against a box, with
+// the cylinder's vertical extent and its closest point to a segment point S (the 16-gon's
+// closest point to S's body-plane coordinates -- S's own when inside, else the nearest
+// point of the nearest edge, earliest on ties -- with the axial coordinate clamped);
+// inside the prism the depth is the smallest distance to a face.
+__device__ __noinline__ void collide_capsule_cyl(const CBox& b, float px, float py, float z0, float z1, float rp,
+                                                 float margin, CManifold& M) {
+    M.np = 0;
+    const float ez = gon_sup(b.R[6], b.R[7]) * b.h[0] + fabsf(b.R[8]) * b.h[2];
+    const float zlo = b.c.z - ez, zhi = b.c.z + ez;
+    const float za = fmaxf(z0, zlo), zb = fminf(z1, zhi);
+    float zc0, zc1 = 0.f;
+    int nc;
+    if (za > zb) {
+        zc0 = (zhi < z0) ? z0 : z1;
+        nc = 1;
+    } else if (zb - za < 1e-3f) {
+        zc0 = (za + zb) * 0.5f;
+        nc = 1;
+    } else {
+        zc0 = za;
+        zc1 = zb;
+        nc = 2;
+    }
+    const float r = b.h[0], apo = r * kGonApo;
+    float best_d = 0.f;
+    float3 best_n = f3(1.f, 0.f, 0.f);
+    for (int i = 0; i < nc; i++) {
+        const float3 S = f3(px, py, i == 0 ? zc0 : zc1);
+        const float3 rel = S - b.c;
+        const float lx = dot3(b.ax(0), rel), ly = dot3(b.ax(1), rel), lz = dot3(b.ax(2), rel);
+        bool inside = true;
+        float pen_side = 3.0e38f;
+        for (int s = 0; s < 16; s++) {
+            float fcs, fss;
+            gon_fdir(s, fcs, fss);
+            const float gq = apo - (fcs * lx + fss * ly);
+            if (gq < 0.f) inside = false;
+            pen_side = fminf(pen_side, gq);
+        }
+        float qx = lx, qy = ly;
+        if (!inside) {
+            float bd = 0.f;
+            for (int s = 0; s < 16; s++) {
+                float c0, s0, c1, s1;
+                gon_vdir(s, c0, s0);
+                gon_vdir((s + 1) & 15, c1, s1);
+                const float ax = r * c0, ay = r * s0, ex = r * c1 - ax, ey = r * s1 - ay;
+                float t = ((lx - ax) * ex + (ly - ay) * ey) / (ex * ex + ey * ey);
+                t = fminf(fmaxf(t, 0.f), 1.f);
+                const float ppx = ax + ex * t, ppy = ay + ey * t;
+                const float dd = (lx - ppx) * (lx - ppx) + (ly - ppy) * (ly - ppy);
+                if (s == 0 || dd < bd) {
+                    bd = dd;
+                    qx = ppx;
+                    qy = ppy;
+                }
+            }
+        }
+        const float qz = fminf(fmaxf(lz, -b.h[2]), b.h[2]);
+        const float3 Q = b.c + b.ax(0) * qx + b.ax(1) * qy + b.ax(2) * qz;
+        const float3 diff = S - Q;
+        const float dist = norm3(diff);
+        float3 nrm;
+        float d;
+        if (dist > 1e-6f) {
+            nrm = diff * (1.f / dist);
+            d = dist - rp;
+        } else {
+            const float pen = fminf(b.h[2] - fabsf(lz), pen_side);
+            d = -pen - rp;
             const float3 w = f3(S.x - b.c.x, S.y - b.c.y, 0.f);
             const float lw = norm3(w);
             nrm = lw > 1e-9f ? w * (1.f / lw) : f3(1.f, 0.f, 0.f);

@@ -110,9 +110,18 @@ __device__ __forceinline__ void load_env(const RolloutArgs& a, const WarpMem& W,
         W.bv()[i] = make_float4(s[7], s[8], s[9], 1.f / m);
         W.bw()[i] = make_float4(s[10], s[11], s[12], mu);
         const float hx2 = h0 * h0, hy2 = h1 * h1, hz2 = h2 * h2;
-        W.ib()[i] = 1.f / (m / 3.f * (hy2 + hz2));
-        W.ib()[NB + i] = 1.f / (m / 3.f * (hx2 + hz2));
-        W.ib()[2 * NB + i] = 1.f / (m / 3.f * (hx2 + hy2));
+        if (h1 < 0.f) {
+            // solid cylinder (radius h0, height 2 h2): m (3 r^2 + 4 h^2) / 12 about a
+            // diameter, m r^2 / 2 about its axis
+            const float id = 1.f / (m * (3.f * hx2 + 4.f * hz2) / 12.f);
+            W.ib()[i] = id;
+            W.ib()[NB + i] = id;
+            W.ib()[2 * NB + i] = 1.f / (m * hx2 / 2.f);
+        } else {
+            W.ib()[i] = 1.f / (m / 3.f * (hy2 + hz2));
+            W.ib()[NB + i] = 1.f / (m / 3.f * (hx2 + hz2));
+            W.ib()[2 * NB + i] = 1.f / (m / 3.f * (hx2 + hy2));
+        }
     }
     __syncwarp();
 }
@@ -141,6 +150,7 @@ __device__ __forceinline__ void store_state(const WarpMem& W, int n, float* dst,
 
 // One substep of the group's environment (on = false: the group only takes part in the
 // warp's collectives).  Returns true on a cap overflow.
+template <bool kCyl>
 __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, int n_env, bool on, const Pusher& pu,
                                         int s, const Grp& g, float4* warm, int& warm_n) {
     const SimConst& C = a.C;
@@ -161,7 +171,7 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
     bool ovf = broadphase(W, n, g, C.pair_cap, on && pu.active, Px, Py, C);
     {
         NarrowStats st{0, 0, 0, 0, 0, 0, 0};
-        ovf |= narrowphase(W, g, on, C, Px, Py, st);
+        ovf |= narrowphase<kCyl>(W, g, on, C, Px, Py, st);
         // count now, so that nothing of the narrowphase stays live through the solve
         if (on && g.gl == 0) {
             unsigned long long* ev = W.ev().ptr();
@@ -206,6 +216,7 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
 // (target graspable; Sec. IV-C hands such environments other work) takes the
 // next one while the other groups continue.  Push set-up and end-of-push phases run when
 // any group needs them; groups without work take part in the collectives only.
+template <bool kCyl>
 __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W, const Grp& g) {
     const SimConst& C = a.C;
     int e = -1;
@@ -288,7 +299,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
         // 3. one substep
         const bool run = active && !pg.done && pg.s < C.substeps && budget > 0;
         const Pusher pu = make_pusher(C, pg.push, pg.noop != 0);
-        ovf |= substep(a, W, ei.n, run, pu, pg.s, g, a.warm ? a.warm + (size_t)(e < 0 ? 0 : e) * a.warm_f4_per_env : nullptr,
+        ovf |= substep<kCyl>(a, W, ei.n, run, pu, pg.s, g, a.warm ? a.warm + (size_t)(e < 0 ? 0 : e) * a.warm_f4_per_env : nullptr,
                        pg.pad[0]);
         // bounded run time per environment and launch (the shuffle runs in every lane)
         const bool late = g.bcast((int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
@@ -358,6 +369,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
 
 // 128 threads (up to four warps) per block and a register budget for two blocks per SM:
 // the solver keeps its working set in registers without spilling.
+template <bool kCyl>
 __global__ void __launch_bounds__(128, 3) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const Grp g(a.G, lane);
@@ -365,7 +377,7 @@ __global__ void __launch_bounds__(128, 3) rollout_kernel(const __grid_constant__
     const int slot = wib * per_warp + (lane / a.G);
     const size_t gslot = (size_t)blockIdx.x * (blockDim.x >> 5) * per_warp + slot;
     const WarpMem W = bind_mem(a.L, (uint32_t)slot * (uint32_t)a.L.bytes, a.gscratch + gslot * a.scratch_f4_per_warp);
-    run_slots(a, W, g);
+    run_slots<kCyl>(a, W, g);
 }
 // ---- rollout device code ends
 
@@ -457,13 +469,19 @@ __global__ void __launch_bounds__(128) penetration_kernel(int n_scenes, const in
         quat_to_R_exact(ra[3], ra[4], ra[5], ra[6], A.R);
         quat_to_R_exact(rb[3], rb[4], rb[5], rb[6], B.R);
         for (int k = 0; k < 3; k++) {
-            A.h[k] = ra[13 + k];
-            B.h[k] = rb[13 + k];
+            A.h[k] = fabsf(ra[13 + k]);
+            B.h[k] = fabsf(rb[13 + k]);
         }
+        A.cyl = ra[14] < 0.f;
+        B.cyl = rb[14] < 0.f;
         CManifold cm;
         int clip = 0;
-        if (collide_box_box(A, B, 0.f, cm, clip))
+        if (A.cyl || B.cyl) {
+            float sep = 0.f;
+            if (collide_convex(A, B, 0.f, cm, clip, &sep)) worst = fmaxf(worst, -sep);
+        } else if (collide_box_box(A, B, 0.f, cm, clip)) {
             for (int p = 0; p < cm.np; p++) worst = fmaxf(worst, -cm.d[p]);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
     if (lane == 0) out[s] = worst;
@@ -474,7 +492,8 @@ __global__ void __launch_bounds__(128) penetration_kernel(int n_scenes, const in
 // 144 x 144 cells of 2 mm; the depth image the grasp classifier of Sec. IV-B reads):
 // cell (i, j) holds the height of the highest box surface above its centre, or 0.  For
 // each box the vertical line through the cell centre is written in the box frame
-// (a_k + b_k s with s = z - c_z) and clipped against the three slabs |.| <= h_k (slab
+// (a_k + b_k s with s = z - c_z) and clipped against the three slabs |.| <= h_k (a
+// cylinder: nine slabs, its cap axis and the 16-gon's side normal directions) (slab
 // ends -(a_k / b_k) -+ h_k / b_k, with 1 / b_k and h_k / b_k rounded once per box and each
 // end one fused multiply-add); a non-empty interval puts the box's top at c_z + s_hi.  Every operation is an explicitly
 // rounded binary32 intrinsic in a fixed order, so the map is defined bit for bit.  A
@@ -515,9 +534,11 @@ constexpr size_t kHMSmem = sizeof(unsigned int) * kHMCells * kHMCells;
 
 template <class Src>
 __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_envs, float* out) {
-    __shared__ float sR[kMaxBoxes][9], srb[kMaxBoxes][3], shr[kMaxBoxes][3];
-    __shared__ float sc[kMaxBoxes][3], sh[kMaxBoxes][3], sbox[kMaxBoxes][4];
-    __shared__ int srect[kMaxBoxes][4];
+    // per body its slabs: world normal (x, y, z components), half thickness, 1 / z and
+    // half / z (a box: its three axes; a cylinder: its cap axis and 8 side normals)
+    __shared__ float sw[kMaxBoxes][9][4], srb[kMaxBoxes][9], shr[kMaxBoxes][9];
+    __shared__ float sc[kMaxBoxes][3], sbox[kMaxBoxes][4];
+    __shared__ int srect[kMaxBoxes][4], sns[kMaxBoxes];
     unsigned int* map = reinterpret_cast<unsigned int*>(pmbs_smem);
     const int e = blockIdx.x;
     if (e >= n_envs) return;
@@ -529,12 +550,25 @@ __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_env
         const float* hh = src.h(e, b);
         float R[9];
         quat_to_R_exact(s[3], s[4], s[5], s[6], R);
-        for (int k = 0; k < 9; k++) sR[b][k] = R[k];
-        for (int k = 0; k < 3; k++) {
-            sc[b][k] = s[k];
-            sh[b][k] = hh[k];
-            srb[b][k] = R[6 + k] == 0.f ? 0.f : __frcp_rn(R[6 + k]);  // 1 / b_k, rounded once
-            shr[b][k] = __fmul_rn(hh[k], srb[b][k]);                    // h_k / b_k
+        for (int k = 0; k < 3; k++) sc[b][k] = s[k];
+        auto slab = [&](int k, float wx, float wy, float wz, float half) {
+            sw[b][k][0] = wx;
+            sw[b][k][1] = wy;
+            sw[b][k][2] = wz;
+            sw[b][k][3] = half;
+            srb[b][k] = wz == 0.f ? 0.f : __frcp_rn(wz);  // 1 / b_k, rounded once
+            shr[b][k] = __fmul_rn(half, srb[b][k]);      // h_k / b_k
+        };
+        if (hh[1] < 0.f) {
+            slab(0, R[2], R[5], R[8], hh[2]);
+            const float apo = __fmul_rn(hh[0], kGonApo);
+            for (int k = 0; k < 8; k++)
+                slab(1 + k, xa(xm(kGonFC[k], R[0]), xm(kGonFS[k], R[1])), xa(xm(kGonFC[k], R[3]), xm(kGonFS[k], R[4])),
+                     xa(xm(kGonFC[k], R[6]), xm(kGonFS[k], R[7])), apo);
+            sns[b] = 9;
+        } else {
+            for (int k = 0; k < 3; k++) slab(k, R[k], R[3 + k], R[6 + k], hh[k]);
+            sns[b] = 3;
         }
         const float ex = aabb_half_exact(R, hh[0], hh[1], hh[2]) + 1e-3f;      // row 0: x
         const float ey = aabb_half_exact(R + 3, hh[0], hh[1], hh[2]) + 1e-3f;  // row 1: y
@@ -565,12 +599,12 @@ __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_env
                 const float dx = __fsub_rn(xc, sc[b][0]), dy = __fsub_rn(yc, sc[b][1]);
                 float s_lo = -INFINITY, s_hi = INFINITY;
                 bool hit = true;
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float a = __fmaf_rn(sR[b][k], dx, __fmul_rn(sR[b][3 + k], dy));
-                    const float bk = sR[b][6 + k];
+                const int ns = sns[b];
+                for (int k = 0; k < ns && hit; k++) {
+                    const float a = __fmaf_rn(sw[b][k][0], dx, __fmul_rn(sw[b][k][1], dy));
+                    const float bk = sw[b][k][2];
                     if (bk == 0.f) {
-                        if (!(fabsf(a) <= sh[b][k])) hit = false;
+                        if (!(fabsf(a) <= sw[b][k][3])) hit = false;
                         continue;
                     }
                     const float r = srb[b][k];
@@ -614,7 +648,7 @@ __global__ void __launch_bounds__(128) grasp_hm_kernel(const HMCsr src, const in
     float R[9];
     quat_to_R_exact(s[3], s[4], s[5], s[6], R);
     const Foot ft = footprint_exact(s[0], s[1], R, hh[0], hh[1], hh[2]);
-    const float z_tip = xs(xa(s[2], aabb_half_exact(R + 6, hh[0], hh[1], hh[2])), depth);
+    const float z_tip = xs(xa(s[2], vertical_half_exact(R, hh[0], hh[1], hh[2])), depth);
     const float halfW = xm(C.grasp_W, 0.5f), hfw = xm(C.grasp_fw, 0.5f);
     const float* map = maps + (size_t)e * kHMCells * kHMCells;
     bool any = false;
@@ -814,6 +848,7 @@ struct SceneRec {
     size_t rec_off = 0;           // byte offset of its records inside the arena
     int n = 0, target = 0;
     int uses = 0;                 // batches referencing it (host-submitted ids only)
+    bool cyl = false;             // holds a cylinder
     std::vector<float> host;      // records, kRecFloats per box
 };
 
@@ -846,6 +881,7 @@ struct Batch {
     bool finished = false;
     int G = 32, wpb = 4, Ms = 0;
     int tile = 0;  // substeps per launch when run to completion (0: one persistent launch)
+    bool cyl = false;  // may hold cylinders: run the kernel with the cylinder contact paths
     cudaStream_t stream = nullptr;  // stream of this batch's launches (the context's by default)
     bool own_scratch = false;       // contact spill scratch of its own (batches that may overlap)
     size_t scr_off = 0, scr_bytes = 0;
@@ -1046,7 +1082,10 @@ pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, s
     ctx->d_table = (SceneDesc*)(base + ctx->table_off);
     e = cudaMemsetAsync(ctx->d_table, 0, sizeof(SceneDesc) * kSceneTableCap, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(heightmap_kernel<HMCsr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHMSmem);
@@ -1094,13 +1133,17 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
                 return fail(ctx, PMBS_E_INVALID, "unknown scene id " + std::to_string(s));
             boxes += ctx->scenes[s].n;
             nb = std::max(nb, ctx->scenes[s].n);
+            b.cyl = b.cyl || ctx->scenes[s].cyl;
             const float* p = first_push + 4 * e;
             if (!finite(p[0]) || !finite(p[1]) || !finite(p[2]) || !finite(p[3]))
                 return fail(ctx, PMBS_E_INVALID, "non-finite push");
         }
     } else {
         for (const SceneRec& r : ctx->scenes)
-            if (r.live) nb = std::max(nb, r.n);
+            if (r.live) {
+                nb = std::max(nb, r.n);
+                b.cyl = b.cyl || r.cyl;
+            }
         boxes = (size_t)n_envs * nb;
     }
     b.nb = nb;
@@ -1205,7 +1248,8 @@ pmbs_status launch_rollout_once(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaS
     const int threads = 32 * b.wpb;
     const size_t smem = (size_t)L.bytes * b.wpb * K;
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel, threads, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.cyl ? rollout_kernel<true> : rollout_kernel<false>,
+                                                     threads, smem));
     if (per_sm < 1) return fail(ctx, PMBS_E_INVALID, "launch shape does not fit on an SM");
     per_sm = std::min(per_sm, kMaxWarpsPerSM / b.wpb);
     const int per_block = b.wpb * K;
@@ -1257,7 +1301,8 @@ pmbs_status launch_rollout_once(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaS
     a.warm = b.warm;
     a.warm_f4_per_env = (size_t)kWarmF4 * c.manifold_cap;
     CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), stream));
-    rollout_kernel<<<blocks, threads, smem, stream>>>(a);
+    if (b.cyl) rollout_kernel<true><<<blocks, threads, smem, stream>>>(a);
+    else rollout_kernel<false><<<blocks, threads, smem, stream>>>(a);
     CU(cudaGetLastError());
     return PMBS_OK;
 }
@@ -1343,6 +1388,8 @@ pmbs_status register_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offs
                       rec_host + (size_t)kRecFloats * (box_offset[s + 1] - box_offset[0]));
         r.live = true;
         r.uses = 0;
+        r.cyl = false;
+        for (int i = 0; i < r.n; i++) r.cyl = r.cyl || r.host[(size_t)kRecFloats * i + 14] < 0.f;
         desc[s] = SceneDesc{(const float*)arena_ptr(ctx, r.rec_off), r.n, r.target};
     }
     SceneBlock blk;
@@ -1563,7 +1610,10 @@ pmbs_status pmbs_load_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_off
             if (!finite(r[k])) return fail(ctx, PMBS_E_INVALID, "non-finite scene value");
         const double qn = std::sqrt((double)r[3] * r[3] + (double)r[4] * r[4] + (double)r[5] * r[5] + (double)r[6] * r[6]);
         if (std::fabs(qn - 1.0) > 1e-3) return fail(ctx, PMBS_E_INVALID, "quaternion is not unit length");
-        if (!(h[0] > 0 && h[1] > 0 && h[2] > 0) || !(r[16] > 0) || !(r[17] >= 0))
+        // a box has three positive half extents; a cylinder of radius r and half height h
+        // is the row (r, -r, h)
+        const bool cyl = h[1] < 0 && h[1] == -h[0];
+        if (!(h[0] > 0 && (h[1] > 0 || cyl) && h[2] > 0) || !(r[16] > 0) || !(r[17] >= 0))
             return fail(ctx, PMBS_E_INVALID, "non-positive half extent or mass, or negative friction");
     }
     return register_scenes(ctx, n_scenes, box_offset, rec.data(), target, out_scene_ids, true);
@@ -2678,8 +2728,10 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PMBS_E_CUDA;
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return PMBS_E_CUDA;
-            if (cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-                cudaSuccess)
+            if (cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+                    cudaSuccess ||
+                cudaFuncSetAttribute(rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+                    cudaSuccess)
                 return PMBS_E_CUDA;
             dv.scratch = (unsigned char*)p;
             dv.num_sms = sms;
@@ -2718,7 +2770,8 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     const size_t smem = (size_t)L.bytes * wpb * K;
     if (smem > 227 * 1024) return PMBS_E_INVALID;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel, 32 * wpb, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.cylinders ? rollout_kernel<true> : rollout_kernel<false>,
+                                                      32 * wpb, smem) != cudaSuccess)
         return PMBS_E_CUDA;
     if (per_sm < 1) return PMBS_E_INVALID;
     const int per_block = wpb * K;
@@ -2757,7 +2810,8 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     a.watchdog_flag = counters + 4;
     a.warm = nullptr;  // no room for caches in the fixed scratch: warm start is refused above
     a.warm_f4_per_env = 0;
-    rollout_kernel<<<blocks, 32 * wpb, smem, stream>>>(a);
+    if (c.cylinders) rollout_kernel<true><<<blocks, 32 * wpb, smem, stream>>>(a);
+    else rollout_kernel<false><<<blocks, 32 * wpb, smem, stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;
     int host_cnt[8];
     if (cudaMemcpyAsync(host_cnt, counters, sizeof(host_cnt), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||

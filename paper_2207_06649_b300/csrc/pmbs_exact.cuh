@@ -29,12 +29,47 @@ __device__ __forceinline__ void quat_to_R_exact(float w, float x, float y, float
     R[6] = xm(2.f, xs(xz, wy)); R[7] = xm(2.f, xa(yz, wx)); R[8] = xs(1.f, xm(2.f, xa(xx, yy)));
 }
 
-// AABB half width along world axis k: (|R_k0| h0 + |R_k1| h1) + |R_k2| h2.
-__device__ __forceinline__ float aabb_half_exact(const float* Rrow, float h0, float h1, float h2) {
-    return xa(xa(xm(fabsf(Rrow[0]), h0), xm(fabsf(Rrow[1]), h1)), xm(fabsf(Rrow[2]), h2));
+// Cylinders: a half-extent row (r, -r, h) marks a cylinder of radius r and half height h
+// about its body z axis.  Its contact, footprint and heightmap shape is the right prism
+// over the regular 16-gon inscribed in its circle: cap vertex k at angle k pi/8 in the
+// body xy plane, side face s with outward normal at angle (2s + 1) pi/16 and apothem
+// r cos(pi/16), cap edges of half length r sin(pi/16).  Direction tables (cos, sin) of
+// the vertex directions k = 0..7 and side normals s = 0..7 (k + 8, s + 8: negated), the
+// closed forms rounded to binary32.
+__constant__ float kGonC[8] = {1.f, 0.923879504f, 0.707106769f, 0.382683426f, 0.f, -0.382683426f, -0.707106769f,
+                               -0.923879504f};
+__constant__ float kGonS[8] = {0.f, 0.382683426f, 0.707106769f, 0.923879504f, 1.f, 0.923879504f, 0.707106769f,
+                               0.382683426f};
+__constant__ float kGonFC[8] = {0.980785251f, 0.831469595f, 0.555570245f, 0.195090324f, -0.195090324f,
+                                -0.555570245f, -0.831469595f, -0.980785251f};
+__constant__ float kGonFS[8] = {0.195090324f, 0.555570245f, 0.831469595f, 0.980785251f, 0.980785251f,
+                                0.831469595f, 0.555570245f, 0.195090324f};
+constexpr float kGonApo = 0.980785251f;       // cos(pi/16)
+constexpr float kGonHalfEdge = 0.195090324f;  // sin(pi/16)
+
+// Radial support of the unit 16-gon along the body-plane direction (p0, p1):
+// max_k |c_k p0 + s_k p1| over the eight vertex directions.
+__device__ __forceinline__ float gon_support_exact(float p0, float p1) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) m = fmaxf(m, fabsf(xa(xm(kGonC[k], p0), xm(kGonS[k], p1))));
+    return m;
 }
 
-// Footprint: centre, unit axes u, v = perp(u), support half widths su, sv.
+// AABB half width along world axis k: (|R_k0| h0 + |R_k1| h1) + |R_k2| h2 (a cylinder's
+// bounding box: h1 taken as |h1| = r).
+__device__ __forceinline__ float aabb_half_exact(const float* Rrow, float h0, float h1, float h2) {
+    return xa(xa(xm(fabsf(Rrow[0]), h0), xm(fabsf(Rrow[1]), fabsf(h1))), xm(fabsf(Rrow[2]), h2));
+}
+
+// Vertical half extent (support along z) of a box or cylinder.
+__device__ __forceinline__ float vertical_half_exact(const float* R, float h0, float h1, float h2) {
+    if (h1 < 0.f) return xa(xm(gon_support_exact(R[6], R[7]), h0), xm(fabsf(R[8]), h2));
+    return aabb_half_exact(R + 6, h0, h1, h2);
+}
+
+// Footprint: centre, unit axes u, v = perp(u), support half widths su, sv (the rectangle
+// bounding the body's projection along u and v).
 struct Foot {
     float cx, cy, ux, uy, vx, vy, su, sv;
 };
@@ -56,6 +91,14 @@ __device__ __forceinline__ Foot footprint_exact(float cx, float cy, const float*
     f.uy = xd(ey, len);
     f.vx = -f.uy;
     f.vy = f.ux;
+    if (h1 < 0.f) {
+        // cylinder: r times the 16-gon support of (u.x_b, u.y_b), plus h |u.z_b|
+        f.su = xa(xm(gon_support_exact(xdot2(R[0], R[3], f.ux, f.uy), xdot2(R[1], R[4], f.ux, f.uy)), h0),
+                  xm(fabsf(xdot2(R[2], R[5], f.ux, f.uy)), h2));
+        f.sv = xa(xm(gon_support_exact(xdot2(R[0], R[3], f.vx, f.vy), xdot2(R[1], R[4], f.vx, f.vy)), h0),
+                  xm(fabsf(xdot2(R[2], R[5], f.vx, f.vy)), h2));
+        return f;
+    }
     f.su = xa(xa(xm(fabsf(xdot2(R[0], R[3], f.ux, f.uy)), h0), xm(fabsf(xdot2(R[1], R[4], f.ux, f.uy)), h1)),
               xm(fabsf(xdot2(R[2], R[5], f.ux, f.uy)), h2));
     f.sv = xa(xa(xm(fabsf(xdot2(R[0], R[3], f.vx, f.vy)), h0), xm(fabsf(xdot2(R[1], R[4], f.vx, f.vy)), h1)),

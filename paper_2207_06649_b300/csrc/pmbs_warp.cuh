@@ -232,8 +232,10 @@ __device__ __forceinline__ CBox load_cbox(const WarpMem& W, int i) {
 #pragma unroll
     for (int k = 0; k < 9; k++) b.R[k] = W.R()[k * NB + i];
     b.h[0] = W.h()[i];
-    b.h[1] = W.h()[NB + i];
+    const float h1 = W.h()[NB + i];  // negative: a cylinder of radius h0
+    b.h[1] = fabsf(h1);
     b.h[2] = W.h()[2 * NB + i];
+    b.cyl = h1 < 0.f;
     return b;
 }
 
@@ -436,7 +438,9 @@ __device__ __forceinline__ int emit_chunk(const WarpMem& W, const Grp& g, const 
 // most four points sharing a normal.  Manifolds are emitted in candidate order until the
 // manifold or point capacity would be exceeded; that manifold and every later one are
 // dropped.  Writes M, P to scal[3], scal[4] and the box-box manifold count to scal[7],
-// plane manifolds to scal[8]; returns true on overflow.
+// plane manifolds to scal[8]; returns true on overflow.  kCyl compiles the cylinder
+// contact paths in (batches without cylinders run the instantiation without them).
+template <bool kCyl>
 __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool on, const SimConst& C, float Px,
                                             float Py, NarrowStats& st) {
     const int npairs = on ? W.scal()[0] : 0, nplane = on ? W.scal()[1] : 0, npush = on ? W.scal()[2] : 0;
@@ -456,7 +460,8 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
             B = pr >> 8;
             const CBox a = load_cbox(W, A), b = load_cbox(W, B);
             sat++;
-            const int kd = collide_box_box(a, b, C.margin, cm, clipv);
+            const int kd = (kCyl && (a.cyl || b.cyl)) ? collide_convex(a, b, C.margin, cm, clipv)
+                                                      : collide_box_box(a, b, C.margin, cm, clipv);
             if (kd == 1) face++;
             if (kd == 2) edge++;
             mu = sqrtf(W.bw()[A].w * W.bw()[B].w);
@@ -477,7 +482,8 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
         if (c < nplane && !E.stop) {
             B = W.plane()[c];
             const CBox b = load_cbox(W, B);
-            collide_box_plane(b, C.margin, cm);
+            if (kCyl && b.cyl) collide_cyl_plane(b, C.margin, cm);
+            else collide_box_plane(b, C.margin, cm);
             mu = sqrtf(W.bw()[B].w * C.table_mu);
             cB = b.c;
         }
@@ -495,7 +501,8 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
         if (c < npush && !E.stop) {
             A = W.pusher()[c];
             const CBox a = load_cbox(W, A);
-            collide_capsule_box(a, Px, Py, C.pz0, C.pz1, C.pr, C.margin, cm);
+            if (kCyl && a.cyl) collide_capsule_cyl(a, Px, Py, C.pz0, C.pz1, C.pr, C.margin, cm);
+            else collide_capsule_box(a, Px, Py, C.pz0, C.pz1, C.pr, C.margin, cm);
             mu = sqrtf(W.bw()[A].w * C.pusher_mu);
             cA = a.c;
         }

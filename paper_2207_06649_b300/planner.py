@@ -32,8 +32,9 @@ def ucb_virtual(q, n, n_virt, n_parent, n_parent_virt, c):
 
 
 def footprints(state13, half):
-    """Top-down footprint per box: centre, unit axis u (horizontal part of the box's x axis,
-    or y axis when x is vertical), v = perp(u), support half widths along u and v."""
+    """Top-down footprint per box or cylinder: centre, unit axis u (horizontal part of the
+    body's x axis, or y axis when x is vertical), v = perp(u), support half widths along u
+    and v."""
     st = np.asarray(state13, np.float64)
     h = np.asarray(half, np.float64)
     w, x, y, z = st[:, 3], st[:, 4], st[:, 5], st[:, 6]
@@ -52,8 +53,18 @@ def footprints(state13, half):
     e[small] = R[small, :2, 1]
     u = e / np.linalg.norm(e, axis=1, keepdims=True)
     v = np.stack([-u[:, 1], u[:, 0]], 1)
-    su = (np.abs(np.einsum("ikj,ik->ij", R[:, :2, :], u)) * h).sum(1)
-    sv = (np.abs(np.einsum("ikj,ik->ij", R[:, :2, :], v)) * h).sum(1)
+    pu = np.einsum("ikj,ik->ij", R[:, :2, :], u)   # u on the body axes
+    pv = np.einsum("ikj,ik->ij", R[:, :2, :], v)
+    su = (np.abs(pu) * np.abs(h)).sum(1)
+    sv = (np.abs(pv) * np.abs(h)).sum(1)
+    cyl = h[:, 1] < 0
+    if cyl.any():
+        # a cylinder (row (r, -r, h)): r times the 16-gon's radial support plus h |.z_b|
+        ang = np.arange(8) * np.pi / 8
+        c, s = np.cos(ang), np.sin(ang)
+        for sup, pp in ((su, pu), (sv, pv)):
+            rad = np.abs(pp[cyl, 0:1] * c + pp[cyl, 1:2] * s).max(1)
+            sup[cyl] = rad * h[cyl, 0] + np.abs(pp[cyl, 2]) * h[cyl, 2]
     return st[:, :2], u, v, su, sv
 
 

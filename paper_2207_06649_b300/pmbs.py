@@ -50,7 +50,7 @@ class pmbs_config(C.Structure):
                 ("smem_points", C.c_int),
                 ("smem_manifolds", C.c_int), ("watchdog_ms", C.c_float),
                 ("max_initial_penetration", C.c_float), ("warm_start", C.c_int),
-                ("warm_tolerance", C.c_float)]
+                ("warm_tolerance", C.c_float), ("cylinders", C.c_int)]
 
 
 class PmbsError(RuntimeError):

@@ -1,0 +1,354 @@
+"""Cylinders (16-gon prisms) on the GPU, through the C ABI, against the FP64 oracle.
+
+Bit-exact on identical FP32 snapshots: broadphase lists, footprint grasp decisions,
+sampled pushes, start checks, heightmaps and heightmap grasp decisions.  Tolerances:
+one substep of cylinder clutter within 1e-4 m / 1e-3 rad; non-chaotic cylinder scenes
+after 240 substeps within 1e-3 m / 1e-2 rad; impulse ratios that fix the cylinder's
+inertia within 1e-4 of the closed form.  The mixed workload runs bit-identically
+across launch shapes and alone versus in a batch, box-only batches keep the box-only
+solver, and the 4096-scene cylinder workload runs in one launch with sampled parity.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import _geom as G
+
+pytestmark = pytest.mark.gpu
+APO = math.cos(math.pi / 16)
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2207_06649_b300 import pmbs
+    e = pmbs.Engine(device=0, mem_budget_bytes=4 << 30)
+    yield e
+    e.close()
+
+
+def _sg():
+    from paper_2207_06649_b300 import scenegen
+    return scenegen
+
+
+def _cyl(r, h):
+    return np.array([r, -r, h], np.float32)
+
+
+def _with_cylinders(half, rng, frac=0.4):
+    half = np.array(half, np.float32)
+    m = rng.uniform(size=len(half)) < frac
+    r = np.minimum(half[:, 0], half[:, 1])
+    half[m, 0] = r[m]
+    half[m, 1] = -r[m]
+    return half
+
+
+def _snapshots(seed, n_envs, n_lo=2, n_hi=40, tilt=0.3):
+    sg = _sg()
+    rng = np.random.default_rng(seed)
+    sts, hs, off = [], [], [0]
+    for _ in range(n_envs):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        pose, vel, half = sg.random_state_snapshot(rng, n, spread=0.02 + 0.004 * n, tilt=tilt)
+        sts.append(np.concatenate([pose, vel], 1))
+        hs.append(_with_cylinders(half, rng))
+        off.append(off[-1] + n)
+    return np.array(off, np.int32), np.concatenate(sts).astype(np.float32), np.concatenate(hs)
+
+
+def _clutter(seed, n_envs, n_lo=3, n_hi=25, squeeze=1.0, frac=0.4):
+    sg = _sg()
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _ in range(n_envs):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        sc = sg.make_scene(rng, n, half_lo=0.01, half_hi=0.035, yaw_hi=math.pi / 2,
+                           density_scale=rng.uniform(0.3, 0.6), cyl_frac=frac, target_cylinder=True)
+        sc.pose[:, :2] *= squeeze
+        parts.append(sc)
+    return sg.concat(parts)
+
+
+def _bits(a, b):
+    return np.array_equal(np.ascontiguousarray(a, np.float32).view(np.uint32),
+                          np.ascontiguousarray(b, np.float32).view(np.uint32))
+
+
+# ------------------------------------------------------------------ bit-exact predicates
+def test_cylinder_pairs_bit_exact(eng, orc):
+    off, st, h = _snapshots(11, 96)
+    assert _sg().is_cylinder(h).mean() > 0.3
+    pxy = np.random.default_rng(3).uniform(-0.05, 0.05, size=(len(off) - 1, 2)).astype(np.float32)
+    got = eng.eval_pairs(off, st, h, pusher_xy=pxy)
+    for e in range(len(off) - 1):
+        a, b = off[e], off[e + 1]
+        bb, pl, pu, _ = orc.pairs(st[a:b], h[a:b], pusher_xy=pxy[e], f32=True)
+        assert np.array_equal(got[e][0], bb) and np.array_equal(got[e][1], pl) and np.array_equal(got[e][2], pu)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_cylinder_grasp_samples_and_starts_bit_exact(eng, orc, seed):
+    sc = _clutter(500 + seed, 128)
+    st = _sg().state13(sc)
+    rng = np.random.default_rng(seed)
+    st[:, :2] += rng.normal(scale=0.002, size=(len(st), 2)).astype(np.float32)
+    ne = sc.n_scenes
+    rows = lambda e: slice(sc.box_offset[e], sc.box_offset[e + 1])
+    tgt = np.zeros(ne, np.int32)   # the target is a cylinder in every scene
+    got = eng.eval_grasp(sc.box_offset, st, sc.half, tgt)
+    want = [orc.grasp(st[rows(e)], sc.half[rows(e)], 0, f32=True) for e in range(ne)]
+    assert got.tolist() == want and 0 < sum(want) < ne
+    seeds = rng.integers(0, 2 ** 63, size=ne, dtype=np.uint64)
+    att, push = eng.eval_sample(sc.box_offset, st, sc.half, seeds, 2)
+    for e in range(ne):
+        wa, wp = orc.sample_push(st[rows(e)], sc.half[rows(e)], int(seeds[e]), 2, f32=True)
+        assert att[e] == wa
+        if wa >= 0:
+            assert _bits(push[e], wp)
+    starts = np.stack([st[sc.box_offset[e] + rng.integers(0, sc.box_offset[e + 1] - sc.box_offset[e]), :2]
+                       + rng.normal(scale=0.03, size=2) for e in range(ne)]).astype(np.float32)
+    got = eng.eval_start_blocked(sc.box_offset, st, sc.half, starts)
+    want = [orc.start_blocked(st[rows(e)], sc.half[rows(e)], starts[e, 0], starts[e, 1], f32=True) for e in range(ne)]
+    assert got.tolist() == want and 0 < sum(want) < ne
+
+
+@pytest.mark.parametrize("tilt", [0.0, 0.7])
+def test_cylinder_heightmaps_bit_exact(eng, orc, tilt):
+    off, st, h = _snapshots(21 + int(tilt * 10), 40, tilt=tilt)
+    got = eng.render_heightmaps(off, st, h)
+    for e in range(len(off) - 1):
+        a, b = off[e], off[e + 1]
+        assert _bits(got[e], orc.heightmap(st[a:b], h[a:b], f32=True)), f"env {e}"
+    assert (got > 0).any()
+
+
+@pytest.mark.parametrize("depth", [0.005, 0.03])
+def test_cylinder_target_heightmap_grasp_bit_exact(eng, orc, depth):
+    sc = _clutter(600 + int(depth * 1000), 96)
+    st = _sg().state13(sc)
+    st[:, :2] += np.random.default_rng(1).normal(scale=0.002, size=(len(st), 2)).astype(np.float32)
+    tgt = np.zeros(sc.n_scenes, np.int32)
+    got = eng.eval_grasp_heightmap(sc.box_offset, st, sc.half, tgt, depth=depth)
+    want = [orc.grasp_heightmap(st[sc.box_offset[e]:sc.box_offset[e + 1]], sc.half[sc.box_offset[e]:sc.box_offset[e + 1]],
+                                0, depth=depth, f32=True) for e in range(sc.n_scenes)]
+    assert got.tolist() == want and 0 < sum(want) < len(want)
+
+
+# ------------------------------------------------------------------ trajectories
+def _angle_err(qa, qb):
+    return 2 * np.arccos(np.abs(np.sum(qa * qb, axis=-1)).clip(0, 1))
+
+
+def _run(eng, sc, pushes, count):
+    ids = eng.load(sc)
+    b = eng.rollout_pushes(ids, pushes, 1)
+    eng.step(b, count)
+    st, steps = eng.query_states(b)
+    eng.release_batch(b)
+    eng.free_scenes(ids)
+    return st.astype(np.float64), steps
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_cylinder_clutter_one_substep(orc, seed):
+    from paper_2207_06649_b300 import pmbs
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30, max_initial_penetration=0.01)
+    sg = _sg()
+    sc = _clutter(700 + seed, 64, 3, 30, squeeze=0.95)
+    rng = np.random.default_rng(seed)
+    pushes = np.stack([sg._random_valid_push(rng, sc, e) for e in range(sc.n_scenes)])
+    st, steps = _run(eng, sc, pushes, 1)
+    eng.close()
+    s0 = sg.state13(sc)
+    for e in range(sc.n_scenes):
+        a, b = sc.box_offset[e], sc.box_offset[e + 1]
+        ref, _, _ = orc.run_substeps(s0[a:b], sc.half[a:b], sc.mass[a:b], sc.mu[a:b], push=pushes[e].astype(float), count=1)
+        assert steps[e] == 1
+        assert np.abs(st[a:b, :3] - ref[:, :3]).max() <= 1e-4
+        assert _angle_err(st[a:b, 3:7], ref[:, 3:7]).max() <= 1e-3
+
+
+def _env(rows, halves, mass=0.1, mu=0.5):
+    sg = _sg()
+    st = np.stack(rows).astype(np.float32)
+    n = len(rows)
+    return sg.Scenes(np.array([0, n], np.int32), st[:, :7].copy(), st[:, 7:].copy(), np.array(halves, np.float32),
+                     np.full(n, mass, np.float32), np.full(n, mu, np.float32), np.array([0], np.int32))
+
+
+def _qmul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return (w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+            w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2)
+
+
+@pytest.mark.parametrize("case", ["rest", "slide", "push_corner", "push_side", "on_box", "stack", "lying"])
+def test_cylinder_non_chaotic_240_substeps(eng, orc, case):
+    far = np.array([[0.19, 0.19, 0.19, 0.19]], np.float32)
+    r, h = 0.02, 0.03
+    c = _cyl(r, h)
+    push = far
+    if case == "rest":
+        sc = _env([G.box_row(0.05, -0.02, h)], [c])
+    elif case == "slide":
+        sc = _env([G.box_row(0, 0, h, v=(0.3, 0.2, 0))], [c])
+    elif case == "push_corner":
+        sc = _env([G.box_row(0, 0, h)], [c])
+        push = np.array([[-0.05, 0.0, 0.05, 0.0]], np.float32)
+    elif case == "push_side":
+        sc = _env([G.box_row(0, 0, h, q=G.yaw_q(math.pi / 16))], [c])
+        push = np.array([[-0.05, 0.0, 0.05, 0.0]], np.float32)
+    elif case == "on_box":
+        sc = _env([G.box_row(0, 0, 0.02), G.box_row(0.004, -0.003, 0.04 + h)], [[0.03, 0.03, 0.02], c])
+    elif case == "stack":
+        sc = _env([G.box_row(0, 0, h), G.box_row(0.002, -0.001, 3 * h)], [c, _cyl(0.018, h)])
+    else:
+        q = _qmul(G.quat_from_rotvec([0, math.pi / 2, 0]), G.quat_from_rotvec([0, 0, -math.pi / 16]))
+        sc = _env([G.box_row(0, 0, r * APO, q=q)], [c])
+    st, steps = _run(eng, sc, push, 240)
+    ref, _, _ = orc.run_substeps(_sg().state13(sc), sc.half, sc.mass, sc.mu, push=push[0].astype(float), count=240)
+    assert steps[0] == 240
+    assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-3
+    assert _angle_err(st[:, 3:7], ref[:, 3:7]).max() <= 1e-2
+
+
+def _first_impulse(eng, sc, push, nmax=120):
+    ids = eng.load(sc)
+    b = eng.rollout_pushes(ids, push, 1)
+    prev, _ = eng.query_states(b)
+    for _ in range(nmax):
+        eng.step(b, 1)
+        cur, _ = eng.query_states(b)
+        if np.abs(cur[-1, 7:10] - prev[-1, 7:10]).max() > 1e-7:
+            eng.release_batch(b)
+            eng.free_scenes(ids)
+            return prev.astype(np.float64), cur.astype(np.float64)
+        prev = cur
+    raise AssertionError("no contact")
+
+
+def test_cylinder_inertia_impulse_ratios():
+    """The oracle's inertia pins on the GPU: dw_z / dv_x = -delta m / I_d for a pusher at
+    axial offset delta on a lying cylinder, and 2 sin(psi) / r for a box face striking an
+    upright cylinder's corner edge at yaw psi (g = 0, mu = 0)."""
+    from paper_2207_06649_b300 import pmbs
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30, gravity=(0.0, 0.0, 0.0), pusher_mu=0.0)
+    r, h, m, delta = 0.02, 0.03, 0.1, 0.012
+    q = _qmul(G.quat_from_rotvec([-math.pi / 2, 0, 0]), G.quat_from_rotvec([0, 0, math.pi / 16]))
+    sc = _env([G.box_row(0, 0, 0.1, q=q)], [_cyl(r, h)], mass=m, mu=0.0)
+    x0 = -(r * APO + 0.01 + 0.003)
+    a, b = _first_impulse(eng, sc, np.array([[x0, delta, x0 + 0.1, delta]], np.float32))
+    dv, dw = b[0, 7:10] - a[0, 7:10], b[0, 10:13] - a[0, 10:13]
+    want = -delta * m / (m * (3 * r * r + 4 * h * h) / 12)
+    assert abs(dw[2] / dv[0] - want) < 1e-4 * abs(want)
+    psi = 0.03
+    sg = _sg()
+    rows = np.stack([G.box_row(-(r + 0.02 + 0.003), 0, 0.1, v=(0.2, 0, 0)), G.box_row(0, 0, 0.1, q=G.yaw_q(psi))])
+    sc = sg.Scenes(np.array([0, 2], np.int32), rows[:, :7].astype(np.float32), rows[:, 7:].astype(np.float32),
+                   np.stack([np.array([0.02, 0.05, 0.05], np.float32), _cyl(r, h)]), np.array([5.0, 0.1], np.float32),
+                   np.zeros(2, np.float32), np.array([1], np.int32))
+    a, b = _first_impulse(eng, sc, np.array([[0.19, 0.19, 0.19, 0.19]], np.float32))
+    eng.close()
+    dv, dw = b[1, 7:10] - a[1, 7:10], b[1, 10:13] - a[1, 10:13]
+    yaw = 2 * math.atan2(a[1, 6], a[1, 3])
+    assert abs(dw[2] / dv[0] - 2 * math.sin(yaw) / r) < 1e-4 * (2 * math.sin(yaw) / r)
+
+
+# ------------------------------------------------------------------ workloads
+def test_cylinder_workload_invariance_and_agreement(eng, orc):
+    """96 scenes of the cylinder workload: bit-identical across launch shapes and alone
+    versus in the batch; costs agree with the oracle's rollouts for >= 85 % of the
+    environments; grasp decisions on the GPU's final states are bit-exact."""
+    sg = _sg()
+    scenes, pushes, seeds = sg.config_cylinders(seed=9, n_envs=96, workers=1)
+    assert sg.is_cylinder(scenes.half).mean() > 0.25
+    ids = eng.load(scenes)
+    outs = []
+    for G_, wpb, ms in [(32, 2, 0), (32, 4, 8), (16, 2, 8), (8, 1, 0)]:
+        eng.set_launch_shape(G_, wpb, -1, ms)
+        outs.append(eng.rollout(ids, pushes, depth=2, seeds=seeds))
+    eng.set_launch_shape(0, 0, -1, -1)
+    for o in outs[1:]:
+        assert np.array_equal(o["cost"], outs[0]["cost"])
+        assert _bits(o["state"], outs[0]["state"])
+    out = outs[0]
+    for e in (0, 17, 50):
+        alone = eng.rollout(ids[e:e + 1], pushes[e:e + 1], depth=2, seeds=seeds[e:e + 1])
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        assert alone["cost"][0] == out["cost"][e] and _bits(alone["state"], out["state"][a:z])
+    eng.free_scenes(ids)
+    ref = orc.rollout(scenes.box_offset, sg.state13(scenes), scenes.half, scenes.mass, scenes.mu, scenes.target,
+                      pushes, depth=2, seeds=seeds, threads=8)
+    agree = np.mean(out["cost"] == ref.cost)
+    print(f"cylinder workload: cost agreement {agree:.3f}")
+    assert agree >= 0.85
+    for e in range(scenes.n_scenes):
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        if out["flags"][e] & 6 or out["cost"][e] > 2:
+            continue
+        assert orc.grasp(out["state"][a:z], scenes.half[a:z], int(scenes.target[e]), f32=True)
+
+
+def test_box_batches_keep_the_box_solver(eng):
+    """A box-only batch in a context that also holds cylinder scenes runs the box-only
+    solver: its results equal a fresh context's bit for bit."""
+    from paper_2207_06649_b300 import pmbs
+    sg = _sg()
+    boxes, pushes, seeds = sg.config_uneven(seed=31, n_envs=48, n_lo=5, n_hi=25, workers=1)
+    cyls, _, _ = sg.config_cylinders(seed=32, n_envs=8, workers=1)
+    cid = eng.load(cyls)
+    bid = eng.load(boxes)
+    out = eng.rollout(bid, pushes, depth=2, seeds=seeds)
+    eng.free_scenes(bid)
+    eng.free_scenes(cid)
+    fresh = pmbs.Engine(device=0, mem_budget_bytes=1 << 30)
+    ids = fresh.load(boxes)
+    ref = fresh.rollout(ids, pushes, depth=2, seeds=seeds)
+    fresh.close()
+    assert np.array_equal(out["cost"], ref["cost"]) and _bits(out["state"], ref["state"])
+
+
+def test_cylinder_scene_validation(eng):
+    from paper_2207_06649_b300 import pmbs
+    sg = _sg()
+    bad = _env([G.box_row(0, 0, 0.03)], [[0.02, -0.01, 0.03]])   # radii disagree
+    with pytest.raises(pmbs.PmbsError):
+        eng.load(bad)
+    deep = _env([G.box_row(0, 0, 0.03), G.box_row(0.035, 0, 0.03)], [_cyl(0.02, 0.03), _cyl(0.02, 0.03)])
+    with pytest.raises(pmbs.PmbsError):
+        eng.load(deep)    # 5 mm overlap
+    ok = _env([G.box_row(0, 0, 0.03), G.box_row(0.0415, 0, 0.03)], [_cyl(0.02, 0.03), _cyl(0.02, 0.03)])
+    eng.free_scenes(eng.load(ok))
+
+
+def test_cylinder_4096_env_launch_sampled_parity(eng, orc):
+    """The 4096-scene cylinder workload in one launch: sampled environments after one
+    substep within 1e-4 m of the oracle; the full rollout's sampled grasp decisions
+    bit-exact and sampled environments equal when re-run alone."""
+    sg = _sg()
+    scenes, pushes, seeds = sg.config_cylinders(seed=5, n_envs=4096)
+    ids = eng.load(scenes)
+    b = eng.rollout_pushes(ids, pushes, 1)
+    eng.step(b, 1)
+    st1, _ = eng.query_states(b)
+    eng.release_batch(b)
+    s0 = sg.state13(scenes)
+    sample = np.random.default_rng(0).choice(4096, size=16, replace=False)
+    for e in sample:
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        ref, _, _ = orc.run_substeps(s0[a:z], scenes.half[a:z], scenes.mass[a:z], scenes.mu[a:z],
+                                     push=pushes[e].astype(float), count=1)
+        assert np.abs(st1[a:z, :3] - ref[:, :3]).max() <= 1e-4
+    out = eng.rollout(ids, pushes, depth=3, seeds=seeds)
+    assert ((out["flags"] & 2) == 0).mean() > 0.9
+    for e in sample:
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        c = out["cost"][e]
+        if c <= 3 and not out["flags"][e] & 6:
+            assert orc.grasp(out["state"][a:z], scenes.half[a:z], int(scenes.target[e]), f32=True)
+        alone = eng.rollout(ids[e:e + 1], pushes[e:e + 1], depth=3, seeds=seeds[e:e + 1])
+        assert alone["cost"][0] == c and _bits(alone["state"], out["state"][a:z])
+    eng.free_scenes(ids)
