@@ -36,9 +36,9 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": "4ab5247526ad84d7", "bytes_per_launch": 101632880,
-           "note": "ncu dram bytes (read 19.54 MB + write 47.78 MB) of a one-push launch of the same "
-                   "4096 scenes in the 32,2,0 launch shape, scaled by env-steps (983,040 -> 1,484,160)"}
+TRAFFIC = {"source_sha": "3124ae216c4b90ac", "bytes_per_launch": 128350000,
+           "note": "ncu dram bytes (read 21.70 MB + write 106.65 MB) of one launch of the benchmark "
+                   "workload itself (4096 scenes, depth 3) in the 32,4,0 launch shape, single-pass capture"}
 
 
 def measured_hbm_gbs():
@@ -51,17 +51,28 @@ def measured_hbm_gbs():
         return 6400.0
 
 
+def _code_only(src: bytes) -> bytes:
+    """Source with // comments and blank lines removed (comment edits change no kernel)."""
+    out = []
+    for line in src.decode().splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            out.append(code)
+    return "\n".join(out).encode()
+
+
 def kernel_source_sha():
     """Hash of the rollout kernel's device code: the three device headers and the marked
-    rollout section of the engine source (host code and other kernels excluded)."""
+    rollout section of the engine source (host code and other kernels excluded), with
+    comments stripped."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_06649_b300", "csrc")
     for f in ("pmbs_exact.cuh", "pmbs_collide.cuh", "pmbs_warp.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, f), "rb").read()))
     eng = open(os.path.join(csrc, "pmbs_engine.cu"), "rb").read()
     a = eng.index(b"// ---- rollout device code begins")
     b = eng.index(b"// ---- rollout device code ends")
-    h.update(eng[a:b])
+    h.update(_code_only(eng[a:b]))
     return h.hexdigest()[:16]
 
 
@@ -79,6 +90,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch shape")
     ap.add_argument("--no-heightmaps", action="store_true")
+    ap.add_argument("--cylinders", type=int, default=1, help="also time the cylinder workload (0 = skip)")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'lanes,warps_per_block,smem_manifolds' instead of autotuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="served-load run length (0 = skip)")
@@ -413,6 +425,39 @@ def run_ours(args):
                       "frac": (out_bytes + in_bytes) / hm_s / 1e9 / hbm if hbm else None,
                       "kernel": "heightmap_kernel"}
 
+    # the same workload with cylinders (30 % of the objects, every target): the rollout
+    # kernel built with the cylinder contact paths, autotuned, timed like the main line
+    cylinders = None
+    if args.cylinders and ws == 1:
+        cs, cp, cd = sg.config_cylinders(seed=args.seed + 2, n_envs=args.envs)
+        cids = eng.load(cs)
+        if not args.no_autotune:
+            ctuned = eng.autotune(cids, cp, args.depth, cd, substeps=240)
+        c_steps = None
+        cms = []
+        for i in range(args.warmup + args.steps):
+            cb = eng.rollout_pushes(cids, cp, args.depth, cd)
+            flush.zero_()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record()
+            eng.step(cb, 0)
+            c1.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                cms.append(c0.elapsed_time(c1))
+            if c_steps is None:
+                c_steps = int(eng.query_states(cb)[1].sum())
+            eng.release_batch(cb)
+        eng.free_scenes(cids)
+        cms_mean = float(np.mean(cms))
+        cylinders = {"workload": f"{args.envs} scenes x U{{5..40}} objects, 30 % cylinders (16-gon prisms), "
+                                 f"cylinder targets, depth {args.depth} x 240 substeps",
+                     "cylinder_fraction": float(sg.is_cylinder(cs.half).mean()),
+                     "env_steps_per_step": c_steps, "ms_per_step": cms_mean,
+                     "value": c_steps / (cms_mean / 1e3), "unit": "env-steps/s",
+                     "launch_shape": ctuned if not args.no_autotune else "default",
+                     "kernel": "rollout_kernel (cylinder contact paths compiled in)"}
+
     serving = None
     if args.serve_seconds > 0 and ws == 1:
         pool_sc, pool_pu, _ = sg.config_uneven(seed=args.seed + 7, n_envs=512)
@@ -466,6 +511,7 @@ def run_ours(args):
         "e2e": e2e,
         "serving": serving,
         "heightmaps": heightmaps,
+        "cylinders": cylinders,
         "planning": planning,
         # per timed step: the batch set-up kernel and the rollout launch(es) of the tiling
         "gpu_launches": args.steps * (1 + rollout_launches),

@@ -5,7 +5,8 @@
 // library's reading: box-plane vertex contacts, box-box separating-axis test over 15 axes
 // with reference-face clipping (at most four points) or one edge-edge point, and a
 // capsule pusher against a box by closest points at the ends of the overlapping height
-// range.  Separation d < 0 means penetration; contacts are kept while d < margin.
+// range; cylinders (16-gon prisms) take the general convex form of the same rules.
+// Separation d < 0 means penetration; contacts are kept while d < margin.
 #pragma once
 #include <cstdint>
 
@@ -447,11 +448,14 @@ __device__ __forceinline__ float3 cyl_vertex(const CBox& b, int k, float sz) {
     gon_vdir(k & 15, c, s);
     return b.c + plane_vec(b, c * b.h[0], s * b.h[0]) + b.ax(2) * (sz * b.h[2]);
 }
+// Radial support of the unit 16-gon along (p0, p1): the largest |c_k p0 + s_k p1| over
+// the vertex directions.  By the 16-gon's symmetry, with a >= b the magnitudes of the
+// components, it is the largest of a, cos(pi/8) a + sin(pi/8) b and (a + b) / sqrt 2 --
+// the vertex directions 0, pi/8 and pi/4 that bracket the first octant.
 __device__ __forceinline__ float gon_sup(float p0, float p1) {
-    float m = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; k++) m = fmaxf(m, fabsf(kGonC[k] * p0 + kGonS[k] * p1));
-    return m;
+    const float u = fabsf(p0), v = fabsf(p1);
+    const float a = fmaxf(u, v), b = fminf(u, v);
+    return fmaxf(a, fmaxf(0.923879504f * a + 0.382683426f * b, 0.707106769f * a + 0.707106769f * b));
 }
 __device__ __forceinline__ float support(const CBox& b, float3 L) {
     if (b.cyl) return gon_sup(dot3(b.ax(0), L), dot3(b.ax(1), L)) * b.h[0] + fabsf(dot3(b.ax(2), L)) * b.h[2];

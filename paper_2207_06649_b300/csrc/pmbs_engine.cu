@@ -599,13 +599,12 @@ __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_env
                 const float dx = __fsub_rn(xc, sc[b][0]), dy = __fsub_rn(yc, sc[b][1]);
                 float s_lo = -INFINITY, s_hi = INFINITY;
                 bool hit = true;
-                const int ns = sns[b];
-                for (int k = 0; k < ns && hit; k++) {
+                auto clip = [&](int k) {
                     const float a = __fmaf_rn(sw[b][k][0], dx, __fmul_rn(sw[b][k][1], dy));
                     const float bk = sw[b][k][2];
                     if (bk == 0.f) {
                         if (!(fabsf(a) <= sw[b][k][3])) hit = false;
-                        continue;
+                        return;
                     }
                     const float r = srb[b][k];
                     float t0 = __fmaf_rn(-a, r, -shr[b][k]), t1 = __fmaf_rn(-a, r, shr[b][k]);
@@ -616,6 +615,12 @@ __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_env
                     }
                     if (t0 > s_lo) s_lo = t0;
                     if (t1 < s_hi) s_hi = t1;
+                };
+                if (sns[b] == 3) {
+#pragma unroll
+                    for (int k = 0; k < 3; k++) clip(k);
+                } else {
+                    for (int k = 0; k < 9 && hit; k++) clip(k);
                 }
                 if (hit && s_lo <= s_hi) {
                     const float z = __fadd_rn(sc[b][2], s_hi);
