@@ -352,3 +352,63 @@ def test_cylinder_4096_env_launch_sampled_parity(eng, orc):
         alone = eng.rollout(ids[e:e + 1], pushes[e:e + 1], depth=3, seeds=seeds[e:e + 1])
         assert alone["cost"][0] == c and _bits(alone["state"], out["state"][a:z])
     eng.free_scenes(ids)
+
+
+# ------------------------------------------------------------------ other modes
+def test_cylinders_with_warm_start_match_the_oracle(orc):
+    """Warm-started solve on cylinder scenes (a two-cylinder stack, a cylinder on a box,
+    a pushed cylinder) against the oracle with the same option."""
+    from paper_2207_06649_b300 import pmbs
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30, warm_start=1)
+    r, h = 0.02, 0.03
+    cases = [
+        (_env([G.box_row(0, 0, h), G.box_row(0.002, -0.001, 3 * h)], [_cyl(r, h), _cyl(0.018, h)]), None),
+        (_env([G.box_row(0, 0, 0.02), G.box_row(0.004, -0.003, 0.04 + h)], [[0.03, 0.03, 0.02], _cyl(r, h)]), None),
+        (_env([G.box_row(0, 0, h)], [_cyl(r, h)]), np.array([[-0.05, 0.0, 0.05, 0.0]], np.float32)),
+    ]
+    for sc, push in cases:
+        push = np.array([[0.19, 0.19, 0.19, 0.19]], np.float32) if push is None else push
+        st, _ = _run(eng, sc, push, 240)
+        ref, _, _ = orc.run_substeps(_sg().state13(sc), sc.half, sc.mass, sc.mu, push=push[0].astype(float), count=240,
+                                     prm=orc.params(warm_start=1))
+        assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-3
+    eng.close()
+
+
+def test_cylinder_batches_served_alone_and_in_a_mix(eng):
+    """Cylinder and box requests through the server: each result equals the same request
+    run alone, bit for bit."""
+    from paper_2207_06649_b300 import pmbs
+    sg = _sg()
+    cs, cp, cd = sg.config_cylinders(seed=41, n_envs=64, workers=1)
+    bs, bp, bd = sg.config_uneven(seed=42, n_envs=64, n_lo=5, n_hi=25, workers=1)
+    cid, bid = eng.load(cs), eng.load(bs)
+    alone_c = eng.rollout(cid, cp, depth=2, seeds=cd)
+    alone_b = eng.rollout(bid, bp, depth=2, seeds=bd)
+    srv = pmbs.Server(eng, n_streams=4, max_inflight=8)
+    tickets = [srv.submit(cid, cp, 2, cd), srv.submit(bid, bp, 2, bd), srv.submit(cid[:16], cp[:16], 2, cd[:16])]
+    res = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert np.array_equal(res[0]["cost"], alone_c["cost"]) and np.array_equal(res[0]["steps"], alone_c["steps"])
+    assert np.array_equal(res[1]["cost"], alone_b["cost"]) and np.array_equal(res[1]["steps"], alone_b["steps"])
+    assert np.array_equal(res[2]["cost"], alone_c["cost"][:16])
+    eng.free_scenes(cid)
+    eng.free_scenes(bid)
+
+
+def test_cylinder_batch_heightmaps(eng, orc):
+    """Heightmaps of a finished cylinder batch's final states equal the snapshot entry
+    point and the oracle's binary32 twin."""
+    sg = _sg()
+    scenes, pushes, seeds = sg.config_cylinders(seed=43, n_envs=24, workers=1)
+    ids = eng.load(scenes)
+    b = eng.rollout_pushes(ids, pushes, 2, seeds)
+    eng.step(b, 0)
+    hm = eng.query_heightmaps(b)
+    st, _ = eng.query_states(b)
+    eng.release_batch(b)
+    eng.free_scenes(ids)
+    assert _bits(hm, eng.render_heightmaps(scenes.box_offset, st, scenes.half))
+    for e in (0, 11, 23):
+        a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
+        assert _bits(hm[e], orc.heightmap(st[a:z], scenes.half[a:z], f32=True))

@@ -66,3 +66,35 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     st = lib.pmbs_rollout_noalloc(ctypes.byref(big), null, 1, null, null, null, null, null, 1, null, null, null,
                                   null)
     assert st == pmbs.PMBS_E_INVALID
+
+
+def test_noalloc_with_cylinders_matches_context_rollout():
+    """cfg.cylinders = 1 runs the solver with the cylinder contact paths: the cylinder
+    workload's results equal the context entry point's."""
+    import torch
+    from paper_2207_06649_b300 import pmbs, scenegen as sg
+    lib = pmbs.load()
+    scenes, pushes, seeds = sg.config_cylinders(seed=23, n_envs=64, workers=1)
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30)
+    ids = eng.load(scenes)
+    ref = eng.rollout(ids, pushes, depth=2, seeds=seeds)
+    eng.close()
+    dev = torch.device("cuda", 0)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    rec = np.concatenate([scenes.pose, scenes.vel, scenes.half, scenes.mass[:, None], scenes.mu[:, None]],
+                         1).astype(np.float32)
+    B, n = rec.shape[0], scenes.n_scenes
+    d_state = torch.full((B, 13), float("nan"), device=dev)
+    d_cost = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    d_rew = torch.full((n,), -1.0, device=dev)
+    d_flags = torch.full((n,), 255, dtype=torch.uint8, device=dev)
+    cfg = pmbs.default_config(device=0, cylinders=1)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = [to(scenes.box_offset), to(rec), to(scenes.target), to(pushes.astype(np.float32)), to(seeds.view(np.int64))]
+    st = lib.pmbs_rollout_noalloc(ctypes.byref(cfg), stream, n, *[_ptr(a) for a in args], 2, _ptr(d_state),
+                                  _ptr(d_cost), _ptr(d_rew), _ptr(d_flags))
+    torch.cuda.synchronize()
+    assert st == pmbs.PMBS_OK
+    assert np.array_equal(d_cost.cpu().numpy(), ref["cost"])
+    assert np.array_equal(d_flags.cpu().numpy(), ref["flags"])
+    assert np.array_equal(d_state.cpu().numpy().view(np.uint32), ref["state"].view(np.uint32))
