@@ -36,8 +36,8 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": "3124ae216c4b90ac", "bytes_per_launch": 128350000,
-           "note": "ncu dram bytes (read 21.70 MB + write 106.65 MB) of one launch of the benchmark "
+TRAFFIC = {"source_sha": "2d98e3f5ff4ac933", "bytes_per_launch": 152570000,
+           "note": "ncu dram bytes (read 21.56 MB + write 131.01 MB) of one launch of the benchmark "
                    "workload itself (4096 scenes, depth 3) in the 32,4,0 launch shape, single-pass capture"}
 
 

@@ -553,7 +553,7 @@ __device__ __forceinline__ int clip_side32(const float3* in, int n, float3* out,
 }
 
 // Face contact between convex bodies: reference face f of ref (outward normal nref).
-__device__ __noinline__ int face_contact_convex(const CBox& ref, int f, float3 nref, const CBox& inc, float margin,
+__device__ __forceinline__ int face_contact_convex(const CBox& ref, int f, float3 nref, const CBox& inc, float margin,
                                                 CManifold& M, int& clip_verts) {
     // reference face: centre and side planes (origin fc)
     float3 fc;
@@ -694,7 +694,7 @@ __device__ __forceinline__ void support_edge(const CBox& b, int j, float3 L, flo
 
 // Convex pair with a cylinder (A = lower index).  Returns 0 none, 1 face, 2 edge; the
 // separation of the chosen axis in *sep_out when given.
-__device__ __noinline__ int collide_convex(const CBox& A, const CBox& B, float margin, CManifold& M, int& clip_verts,
+__device__ __forceinline__ int collide_convex(const CBox& A, const CBox& B, float margin, CManifold& M, int& clip_verts,
                                            float* sep_out = nullptr) {
     M.np = 0;
     const float3 D = B.c - A.c;
@@ -785,40 +785,114 @@ __device__ __noinline__ int collide_convex(const CBox& A, const CBox& B, float m
     return 2;
 }
 
+// Offset from the centre of a cylinder's vertex v (v < 16: bottom cap vertex v, else top
+// cap vertex v - 16).
+__device__ __forceinline__ float3 cyl_offset(const CBox& b, int v) {
+    float c, s;
+    gon_vdir(v & 15, c, s);
+    return plane_vec(b, c * b.h[0], s * b.h[0]) + b.ax(2) * ((v < 16 ? -1.f : 1.f) * b.h[2]);
+}
+
 // Cylinder against the plane z = 0 (A = plane, B = cylinder): its 32 vertices (bottom cap
 // k = 0..15, then top) below the margin; four or fewer kept deepest first (ties by vertex
-// index), more reduced to four as for face contacts.  p = offset from the centre.
-__device__ __noinline__ void collide_cyl_plane(const CBox& b, float margin, CManifold& M) {
+// index), more reduced to four as for face contacts (normal +z, so the areas are the z
+// components of the cross products).  p = offset from the centre.  The candidates are a
+// bit mask and every vertex is recomputed when needed, so nothing leaves registers; a cap
+// whose lowest vertex is clear of the margin by more than 1e-6 m (far beyond the
+// rounding of that bound) is skipped.  Loops run over vertex indices uniformly across the
+// warp, so the direction-table reads are broadcasts.
+__device__ __forceinline__ void collide_cyl_plane(const CBox& b, float margin, CManifold& M) {
     M.np = 0;
     M.n = f3(0.f, 0.f, 1.f);
-    float3 B[32];
-    float kd[32];
-    int nk = 0;
-    for (int v = 0; v < 32; v++) {
-        const float3 r = cyl_vertex(b, v & 15, v < 16 ? -1.f : 1.f) - b.c;
-        const float d = b.c.z + r.z;
+    const float rad = gon_sup(b.R[6], b.R[7]) * b.h[0], ax = b.R[8] * b.h[2];
+    const bool bot = b.c.z - ax - rad < margin + 1e-6f, top = b.c.z + ax - rad < margin + 1e-6f;
+    const int v0 = bot ? 0 : 16, v1 = top ? 32 : 16;
+    unsigned cand = 0u;
+    int nk = 0, i1 = -1;
+    float d1 = 0.f;
+    for (int v = v0; v < v1; v++) {
+        const float d = b.c.z + cyl_offset(b, v).z;
         if (d < margin) {
-            B[nk] = r;
-            kd[nk] = d;
+            cand |= 1u << v;
             nk++;
+            if (i1 < 0 || d < d1) {
+                d1 = d;
+                i1 = v;
+            }
         }
     }
-    if (nk > 4) {
-        M.np = reduce_points(B, kd, nk, M.n, M);
+    if (nk == 0) return;
+    if (nk <= 4) {
+        // stable insertion by depth, candidates in vertex order
+        for (int v = v0; v < v1; v++) {
+            if (!(cand >> v & 1u)) continue;
+            const float3 r = cyl_offset(b, v);
+            const float d = b.c.z + r.z;
+            int k = M.np;
+            while (k > 0 && d < M.d[k - 1]) {
+                M.d[k] = M.d[k - 1];
+                M.p[k] = M.p[k - 1];
+                k--;
+            }
+            M.d[k] = d;
+            M.p[k] = r;
+            M.np++;
+        }
         return;
     }
-    // stable insertion by depth (candidates arrive in vertex order)
-    for (int i = 0; i < nk; i++) {
-        int k = M.np;
-        while (k > 0 && kd[i] < M.d[k - 1]) {
-            M.d[k] = M.d[k - 1];
-            M.p[k] = M.p[k - 1];
-            k--;
+    const float3 p1 = cyl_offset(b, i1);
+    unsigned left = cand & ~(1u << i1);
+    int i2 = -1;
+    float b2 = -1.f;
+    for (int v = v0; v < v1; v++) {
+        if (!(left >> v & 1u)) continue;
+        const float3 e = cyl_offset(b, v) - p1;
+        const float l = dot3(e, e);
+        if (i2 < 0 || l > b2) {
+            b2 = l;
+            i2 = v;
         }
-        M.d[k] = kd[i];
-        M.p[k] = B[i];
-        M.np++;
     }
+    left &= ~(1u << i2);
+    const float3 p2 = cyl_offset(b, i2);
+    const float3 e2 = p2 - p1;
+    auto area = [](float3 e, float3 f) { return e.x * f.y - e.y * f.x; };
+    int i3 = -1;
+    float b3 = -1.f;
+    for (int v = v0; v < v1; v++) {
+        if (!(left >> v & 1u)) continue;
+        const float a = fabsf(area(e2, cyl_offset(b, v) - p1));
+        if (i3 < 0 || a > b3) {
+            b3 = a;
+            i3 = v;
+        }
+    }
+    left &= ~(1u << i3);
+    const float3 p3 = cyl_offset(b, i3);
+    const float sgn = area(e2, p3 - p1) < 0.f ? -1.f : 1.f;
+    int i4 = -1;
+    float b4 = 0.f;
+    for (int v = v0; v < v1; v++) {
+        if (!(left >> v & 1u)) continue;
+        const float3 q = cyl_offset(b, v);
+        float a = -sgn * area(e2, q - p1);
+        a = fmaxf(a, -sgn * area(p3 - p2, q - p2));
+        a = fmaxf(a, -sgn * area(p1 - p3, q - p3));
+        if (i4 < 0 || a > b4) {
+            b4 = a;
+            i4 = v;
+        }
+    }
+    const float3 p4 = cyl_offset(b, i4);
+    M.p[0] = p1;
+    M.d[0] = b.c.z + p1.z;
+    M.p[1] = p2;
+    M.d[1] = b.c.z + p2.z;
+    M.p[2] = p3;
+    M.d[2] = b.c.z + p3.z;
+    M.p[3] = p4;
+    M.d[3] = b.c.z + p4.z;
+    M.np = 4;
 }
 
 // Vertical capsule against a cylinder (A = cylinder, B = pusher): as against a box, with
@@ -826,7 +900,7 @@ __device__ __noinline__ void collide_cyl_plane(const CBox& b, float margin, CMan
 // closest point to S's body-plane coordinates -- S's own when inside, else the nearest
 // point of the nearest edge, earliest on ties -- with the axial coordinate clamped);
 // inside the prism the depth is the smallest distance to a face.
-__device__ __noinline__ void collide_capsule_cyl(const CBox& b, float px, float py, float z0, float z1, float rp,
+__device__ __forceinline__ void collide_capsule_cyl(const CBox& b, float px, float py, float z0, float z1, float rp,
                                                  float margin, CManifold& M) {
     M.np = 0;
     const float ez = gon_sup(b.R[6], b.R[7]) * b.h[0] + fabsf(b.R[8]) * b.h[2];

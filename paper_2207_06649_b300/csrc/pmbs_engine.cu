@@ -367,10 +367,11 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
     }
 }
 
-// 128 threads (up to four warps) per block and a register budget for two blocks per SM:
-// the solver keeps its working set in registers without spilling.
+// 128 threads (up to four warps) per block and a register budget for three blocks per SM
+// (two with the cylinder contact paths, whose general separating-axis test and clipping
+// stay in registers): the solver keeps its working set in registers without spilling.
 template <bool kCyl>
-__global__ void __launch_bounds__(128, 3) rollout_kernel(const __grid_constant__ RolloutArgs a) {
+__global__ void __launch_bounds__(128, kCyl ? 2 : 3) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const Grp g(a.G, lane);
     const int per_warp = 32 / a.G;
