@@ -334,6 +334,7 @@ def run_ours(args):
     env_steps = int(steps.sum())
     ev = eng.query_events(batches[0])
     flops_per_launch = flops.algorithmic_flops(ev, pmbs.EVENT_NAMES)
+    flops_phases = flops.flops_by_phase(ev, pmbs.EVENT_NAMES)
     boxes = scenes.counts()
     for b in batches:
         eng.release_batch(b)
@@ -503,7 +504,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "rollout_kernel", "kernel_ms": kernel_s * 1e3,
-                     "flops_per_launch": flops_per_launch,
+                     "flops_per_launch": flops_per_launch, "flops_by_phase": flops_phases,
                      "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "fma_probe_tflops": peak_fma,
                      "hbm_achieved_gbs": state_bytes / kernel_s / 1e9},

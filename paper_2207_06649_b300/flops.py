@@ -51,3 +51,17 @@ def algorithmic_flops(events, names) -> float:
 def fp32_peak_tflops(sms: int, clock_mhz: float) -> float:
     """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 (FMA) x clock."""
     return sms * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+PHASES = {
+    "per_body": ("box_steps",),
+    "narrowphase": ("sat", "face", "clip_verts", "edge", "plane", "pusher"),
+    "contact_prep": ("points", "bb_points", "manifolds"),
+    "contact_solve": ("pgs_points", "pgs_bb_points"),
+}
+
+
+def flops_by_phase(events, names) -> dict:
+    """Algorithmic flops of an events array split by phase of the substep."""
+    ev = dict(zip(names, np.asarray(events, np.float64).reshape(-1, len(names)).sum(0)))
+    return {ph: float(sum(FLOPS_PER_EVENT[k] * ev.get(k, 0.0) for k in keys)) for ph, keys in PHASES.items()}
