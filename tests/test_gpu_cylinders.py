@@ -412,3 +412,33 @@ def test_cylinder_batch_heightmaps(eng, orc):
     for e in (0, 11, 23):
         a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
         assert _bits(hm[e], orc.heightmap(st[a:z], scenes.half[a:z], f32=True))
+
+
+def test_cylinder_special_contacts_one_and_ten_substeps(orc):
+    """Contact kinds one at a time against the oracle after 1 and 10 substeps (g on):
+    crossed lying cylinders meeting edge to edge, a small cap on a large cap, a lying
+    cylinder's side on a box face, a tilted cylinder's rim on a box."""
+    from paper_2207_06649_b300 import pmbs
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30, max_initial_penetration=0.01)
+    r, h = 0.02, 0.04
+    qx = tuple(G.quat_from_rotvec([0, math.pi / 2, 0]))
+    qy = tuple(G.quat_from_rotvec([-math.pi / 2, 0, 0]))
+    cases = [
+        ([G.box_row(0, 0, r, q=qx), G.box_row(0.003, -0.002, 3 * r + 2e-4, q=qy)], [_cyl(r, h), _cyl(r, h)]),
+        ([G.box_row(0, 0, 0.03), G.box_row(0.004, 0.002, 0.06 + 0.02 - 1e-4)], [_cyl(0.03, 0.03), _cyl(0.015, 0.02)]),
+        ([G.box_row(0, 0, 0.02), G.box_row(0.005, 0, 0.04 + r * APO - 1e-4,
+                                           q=tuple(G.quat_from_rotvec([0, math.pi / 2, 0]) * 1.0))],
+         [np.array([0.05, 0.05, 0.02], np.float32), _cyl(r, h)]),
+        ([G.box_row(0, 0, 0.02), G.box_row(0.01, 0, 0.04 + 0.03, q=tuple(G.quat_from_rotvec([0.3, 0.2, 0])))],
+         [np.array([0.05, 0.05, 0.02], np.float32), _cyl(0.02, 0.025)]),
+    ]
+    far = np.array([[0.19, 0.19, 0.19, 0.19]], np.float32)
+    for rows, halves in cases:
+        sc = _env(rows, halves)
+        s0 = _sg().state13(sc)
+        for count in (1, 10):
+            st, _ = _run(eng, sc, far, count)
+            ref, _, _ = orc.run_substeps(s0, sc.half, sc.mass, sc.mu, push=far[0].astype(float), count=count)
+            assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-4 * count
+            assert _angle_err(st[:, 3:7], ref[:, 3:7]).max() <= 1e-3 * count
+    eng.close()

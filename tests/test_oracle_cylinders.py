@@ -293,3 +293,20 @@ def test_heightmap_grasp_of_cylinder_target(orc):
         half.append(np.array([0.008, 0.012, 0.04], np.float32))
     assert not orc.grasp_heightmap(np.stack(st), np.stack(half), 0, f32=False)
     assert sg.is_cylinder(np.stack(half)).tolist() == [True] + [False] * 8
+
+
+def test_crossed_cylinder_edges_meet_at_one_point(orc):
+    """Two lying cylinders crossing at right angles, the lower with a corner edge up and
+    the upper with one down: edge-edge axis (the two cylinder axes, id 200), separation =
+    the gap, one point midway between the edges above their crossing."""
+    r, h, gap = 0.02, 0.04, 4e-4
+    qA = G.quat_from_rotvec([0, math.pi / 2, 0])    # axis along x, corner 8 up
+    qB = G.quat_from_rotvec([-math.pi / 2, 0, 0])   # axis along y, corner 4 down
+    sA = G.box_row(0, 0, 0, q=tuple(qA))
+    sB = G.box_row(0.003, -0.002, 2 * r + gap, q=tuple(qB))
+    res = orc.box_box(sA, cyl(r, h), sB, cyl(r, h))
+    assert res["axis"] == 200
+    assert np.allclose(res["n"], [0, 0, 1], atol=1e-9)
+    assert abs(res["sep"] - gap) < 1e-8
+    assert len(res["pts"]) == 1
+    assert np.allclose(res["pts"][0], [0.003, 0.0, r + gap / 2], atol=1e-8)
