@@ -118,8 +118,8 @@ typedef struct {
     float warm_tolerance;       /* 2e-3 m: match distance for warm starting */
     int cylinders;              /* pmbs_rollout_noalloc only: 1 = the records may hold cylinders
                                    (runs the solver built with the cylinder contact paths);
-                                   0 (default) = boxes only, cylinder rows are then simulated
-                                   as nothing sensible and must not be passed.  The other
+                                   0 (default) = boxes only: an environment with a cylinder
+                                   row is refused like one with a bad box count.  The other
                                    entry points decide from the loaded scenes. */
 } pmbs_config;
 
@@ -388,8 +388,9 @@ void pmbs_server_destroy(pmbs_server* server);
  * kernel's shared-memory limit); make that first call before any stream capture.  The
  * call synchronises cuda_stream and returns PMBS_OK, PMBS_E_INVALID (bad argument,
  * cfg->warm_start set (its caches need memory), or
- * an environment with a box count outside 1..max_boxes_per_env or a target out of range:
- * such environments are not simulated and their outputs are undefined), PMBS_E_TIMEOUT
+ * an environment with a box count outside 1..max_boxes_per_env, a target out of range,
+ * a cylinder row (r, -r, h) while cfg->cylinders is 0, or a cylinder row whose radii
+ * differ: such environments are not simulated and their outputs are undefined), PMBS_E_TIMEOUT
  * or PMBS_E_CUDA.  Every call shares the one array and starts by clearing what must start
  * at zero; calls whose GPU work overlaps (several threads or streams at once) race on it
  * and must be serialised by the caller.  It allocates no device memory. */

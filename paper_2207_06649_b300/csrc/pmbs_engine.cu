@@ -2663,9 +2663,10 @@ std::mutex g_noalloc_mu;
 // Environment e owns records box_offset[e] .. box_offset[e+1]-1 (18 floats each: state13,
 // half extents, mass, mu).  Environments with a box count outside [1, max_boxes] or a
 // target out of range are not simulated; counters[1] records that.
-__global__ void __launch_bounds__(1024) noalloc_setup_kernel(int n_envs, int max_boxes, const int32_t* box_offset,
-                                                             const float* records, const int32_t* target,
-                                                             EnvIn* env, int* order, EnvProg* prog, int* counters,
+__global__ void __launch_bounds__(1024) noalloc_setup_kernel(int n_envs, int max_boxes, int allow_cyl,
+                                                             const int32_t* box_offset, const float* records,
+                                                             const int32_t* target, EnvIn* env, int* order,
+                                                             EnvProg* prog, int* counters,
                                                              unsigned long long* events, int32_t* steps) {
     __shared__ int hist[kMaxBoxes + 2];
     const int t = threadIdx.x;
@@ -2678,7 +2679,13 @@ __global__ void __launch_bounds__(1024) noalloc_setup_kernel(int n_envs, int max
         const int tg = target[e];
         EnvProg p;
         memset(&p, 0, sizeof(p));
-        if (n < 1 || n > max_boxes || tg < 0 || tg >= n) {
+        bool bad = n < 1 || n > max_boxes || tg < 0 || tg >= n;
+        // a cylinder row is (r, -r, h); without the cylinder solver it is refused too
+        for (int i = 0; !bad && i < n; i++) {
+            const float* h = records + (size_t)kRecFloats * (b0 + i) + 13;
+            if (h[1] < 0.f) bad = !allow_cyl || h[1] != -h[0];
+        }
+        if (bad) {
             atomicOr(counters + 1, 1);
             p.done = 1;  // not simulated
             n = 0;
@@ -2785,7 +2792,8 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
                                              max_warps / per_block}));
     if (max_warps < per_block) return PMBS_E_INVALID;
 
-    noalloc_setup_kernel<<<1, 1024, 0, stream>>>(n_envs, nb, d_box_offset, d_records, d_target, env, order, prog,
+    noalloc_setup_kernel<<<1, 1024, 0, stream>>>(n_envs, nb, c.cylinders ? 1 : 0, d_box_offset, d_records, d_target, env,
+                                                 order, prog,
                                                  counters, events, steps);
     if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;
     RolloutArgs a;

@@ -98,3 +98,39 @@ def test_noalloc_with_cylinders_matches_context_rollout():
     assert np.array_equal(d_cost.cpu().numpy(), ref["cost"])
     assert np.array_equal(d_flags.cpu().numpy(), ref["flags"])
     assert np.array_equal(d_state.cpu().numpy().view(np.uint32), ref["state"].view(np.uint32))
+
+
+def test_noalloc_refuses_cylinder_rows_without_the_cylinder_solver():
+    """cfg.cylinders = 0 with a cylinder row, or a cylinder row whose radii differ, makes
+    that environment invalid: the call returns PMBS_E_INVALID and the other environments
+    are simulated as usual."""
+    import torch
+    from paper_2207_06649_b300 import pmbs, scenegen as sg
+    lib = pmbs.load()
+    scenes, pushes, seeds = sg.config_uneven(seed=25, n_envs=8, n_lo=5, n_hi=10, workers=1)
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30)
+    ref = eng.rollout(eng.load(scenes), pushes, depth=1)
+    eng.close()
+    dev = torch.device("cuda", 0)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    half = scenes.half.copy()
+    a0 = scenes.box_offset[3]
+    half[a0] = (0.02, -0.02, 0.02)   # env 3 holds a cylinder
+    rec = np.concatenate([scenes.pose, scenes.vel, half, scenes.mass[:, None], scenes.mu[:, None]], 1).astype(np.float32)
+    B, n = rec.shape[0], scenes.n_scenes
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for cyl_flag, row in ((0, (0.02, -0.02, 0.02)), (1, (0.02, -0.01, 0.02))):
+        rec[a0, 13:16] = row
+        d_state = torch.zeros((B, 13), device=dev)
+        d_cost = torch.zeros((n,), dtype=torch.int32, device=dev)
+        d_rew = torch.zeros((n,), device=dev)
+        d_flags = torch.zeros((n,), dtype=torch.uint8, device=dev)
+        cfg = pmbs.default_config(device=0, cylinders=cyl_flag)
+        args = [to(scenes.box_offset), to(rec), to(scenes.target), to(pushes.astype(np.float32)), to(seeds.view(np.int64))]
+        st = lib.pmbs_rollout_noalloc(ctypes.byref(cfg), stream, n, *[_ptr(a) for a in args], 1, _ptr(d_state),
+                                      _ptr(d_cost), _ptr(d_rew), _ptr(d_flags))
+        torch.cuda.synchronize()
+        assert st == pmbs.PMBS_E_INVALID
+        got = d_cost.cpu().numpy()
+        ok = np.arange(n) != 3
+        assert np.array_equal(got[ok], ref["cost"][ok])
