@@ -147,8 +147,8 @@ const char* pmbs_last_error(const pmbs_ctx* ctx);
  * selected states into environments; a scene here is such a state).  CSR over boxes:
  * scene s owns rows box_offset[s] .. box_offset[s+1]-1 of pose [B][7] (x y z qw qx qy
  * qz), vel [B][6] (linear, angular; NULL = at rest), half_ext [B][3], mass [B], mu [B];
- * target[s] is the local index of its target box.  A half_ext row (r, -r, h) is an
- * upright-in-its-frame cylinder of radius r and half height h about its body z axis
+ * target[s] is the local index of its target box.  A half_ext row (r, -r, h) is a
+ * cylinder of radius r and half height h whose axis is its body z axis
  * (contact geometry: the right prism over the regular 16-gon inscribed in its circle;
  * inertia: the solid cylinder's); this convention holds in every entry point that takes
  * half extents.  Writes one id per scene to out_scene_ids.  Validation: finite values,
