@@ -442,3 +442,31 @@ def test_cylinder_special_contacts_one_and_ten_substeps(orc):
             assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-4 * count
             assert _angle_err(st[:, 3:7], ref[:, 3:7]).max() <= 1e-3 * count
     eng.close()
+
+
+def test_cylinder_edge_cases_one_substep(orc):
+    """A 64-object scene (every other object a cylinder), a flat disc (h = r / 10) resting
+    on the table and a needle (r = 2 mm, h = 4 cm) leaning on a box: one substep within
+    1e-4 m of the oracle, and the 64-object scene's heightmap bit-exact."""
+    from paper_2207_06649_b300 import pmbs
+    sg = _sg()
+    eng = pmbs.Engine(device=0, mem_budget_bytes=1 << 30, max_initial_penetration=0.01)
+    rng = np.random.default_rng(77)
+    big = sg.make_scene(rng, 64, half_lo=0.008, half_hi=0.016, region_half=0.19)
+    assert big.counts()[0] == 64
+    half = big.half.copy()
+    half[1::2, 0] = np.minimum(half[1::2, 0], half[1::2, 1])
+    half[1::2, 1] = -half[1::2, 0]
+    big = sg.Scenes(big.box_offset, big.pose, big.vel, half, big.mass, big.mu, big.target)
+    disc = _env([G.box_row(0.01, 0.0, 0.002)], [_cyl(0.02, 0.002)])
+    needle = _env([G.box_row(0, 0, 0.02), G.box_row(0.035, 0.0, 0.045, q=tuple(G.quat_from_rotvec([0, -0.6, 0])))],
+                  [np.array([0.02, 0.02, 0.02], np.float32), _cyl(0.002, 0.04)])
+    far = np.array([[0.19, 0.19, 0.19, 0.19]], np.float32)
+    for sc in (big, disc, needle):
+        st, _ = _run(eng, sc, far, 1)
+        ref, _, _ = orc.run_substeps(_sg().state13(sc), sc.half, sc.mass, sc.mu, push=far[0].astype(float), count=1)
+        assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-4
+    s0 = sg.state13(big)
+    hm = eng.render_heightmaps(big.box_offset, s0, big.half)
+    assert _bits(hm[0], orc.heightmap(s0, big.half, f32=True))
+    eng.close()
