@@ -4,14 +4,17 @@
 // baseline of the benchmark do.
 //
 // What it computes (Sec. III-A, Sec. IV-B, Sec. IV-C "Batch Simulation"): each
-// environment holds boxes on a table plane (z = 0) and a kinematic vertical capsule
-// pusher that executes straight push actions a^p = (x_s, y_s, x_e, y_e).  The
+// environment holds boxes and cylinders (right prisms over a 16-gon, with the solid
+// cylinder's inertia) on a table plane (z = 0) and a kinematic vertical capsule pusher
+// that executes straight push actions a^p = (x_s, y_s, x_e, y_e).  The
 // transition function is only described in the paper as quasi-static motion with
 // friction and collisions (Sec. III-A, transition function), so every physics rule
 // here is a stated reading, written once in plain sequential form:
 //   substep = pusher kinematics, gravity, AABB broadphase, narrowphase (box-plane
 //   vertices, box-box separating-axis test with face clipping or edge-edge point,
-//   capsule-box closest points), contact preparation, greedy manifold colouring,
+//   capsule-box closest points; pairs with a cylinder through the general convex
+//   separating-axis test, cylinder-plane vertices, capsule-cylinder closest points),
+//   contact preparation, greedy manifold colouring,
 //   projected Gauss-Seidel with disk-clamped Coulomb friction, semi-implicit Euler.
 // After each push: workspace bounds, grasp-clearance test standing in for the grasp
 // classifier (Sec. IV-B), cost and discounted reward gamma^(k-1) (Sec. III-A, Sec. V-A
