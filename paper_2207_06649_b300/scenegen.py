@@ -1,8 +1,9 @@
 """Seeded synthetic inputs for the batched push-rollout engine.
 
 These generators stand in for the paper's evaluation scenes (Sec. V-A: 20 clutter
-cases that are not available here).  They produce boxes resting on a table plane at
-non-overlapping, seeded positions and straight push actions a^p = (x_s, y_s, x_e, y_e)
+cases that are not available here).  They produce boxes (and, on request, upright
+cylinders) resting on a table plane at non-overlapping, seeded positions and straight
+push actions a^p = (x_s, y_s, x_e, y_e)
 (Sec. III-A, action space).  The module is input data only: it holds none of the
 engine's physics, contact, grasp or sampling arithmetic, and both the CUDA path and
 the CPU oracle consume its output.
