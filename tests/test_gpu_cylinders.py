@@ -470,3 +470,27 @@ def test_cylinder_edge_cases_one_substep(orc):
     hm = eng.render_heightmaps(big.box_offset, s0, big.half)
     assert _bits(hm[0], orc.heightmap(s0, big.half, f32=True))
     eng.close()
+
+
+def test_cylinder_graph_stepping_equals_one_launch(eng):
+    """The substep loop captured as a CUDA graph (one launch per push, and launches of 97
+    substeps through resumed stepping) gives the one persistent launch's results bit for
+    bit on the cylinder workload."""
+    sg = _sg()
+    scenes, pushes, seeds = sg.config_cylinders(seed=47, n_envs=64, workers=1)
+    ids = eng.load(scenes)
+    ref = eng.rollout(ids, pushes, depth=2, seeds=seeds)
+    b = eng.rollout_pushes(ids, pushes, 2, seeds)
+    eng.step_graph(b, 240)
+    r = eng.query_cost(b)
+    st, steps = eng.query_states(b)
+    eng.release_batch(b)
+    assert np.array_equal(r["cost"], ref["cost"]) and np.array_equal(steps, ref["steps"])
+    assert _bits(st, ref["state"])
+    b = eng.rollout_pushes(ids, pushes, 2, seeds)
+    while not eng.step(b, 97):
+        pass
+    st, steps = eng.query_states(b)
+    eng.release_batch(b)
+    assert _bits(st, ref["state"])
+    eng.free_scenes(ids)
