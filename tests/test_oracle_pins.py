@@ -707,3 +707,32 @@ def test_warm_start_conserves_momentum_in_impacts(orc):
     p1 = (m[:, None] * out[:, 7:10]).sum(0)
     assert np.abs(out[:, 7:10] - st[:, 7:10]).max() > 0.05      # they did collide
     assert np.abs(p1 - p0).max() <= 1e-12
+
+
+def test_pusher_box_contact_closed_form(orc):
+    """Capsule pusher (radius 0.01 m, z in [0.01, 0.20]) beside an upright box: the two
+    contact points sit on the box face at the ends of the overlapping height range
+    [0.01, 2 h_z], separation = centre distance - h_x - r, normal from the box to the
+    pusher; a pusher level with a box corner meets it at the corner edge."""
+    hx, hy, hz, rp = 0.03, 0.02, 0.025, 0.01
+    half = np.array([[hx, hy, hz]], np.float32)
+    st = G.box_row(0, 0, hz)[None]
+    gap = 4e-4
+    px = -(hx + rp + gap)
+    info, nrm, pts = orc.contacts(st, half, np.ones(1, np.float32), np.full(1, 0.5, np.float32),
+                                  push=np.array([px, 0.0, px + 0.1, 0.0]), s=0)
+    m = [k for k in range(len(info)) if info[k, 1] == -2][0]
+    assert info[m, 2] == 2
+    assert np.allclose(nrm[m], [-1, 0, 0], atol=1e-12)
+    zs = np.sort(pts[m, :2, 2])
+    assert np.allclose(zs, [0.01, 2 * hz], atol=1e-7)
+    assert np.allclose(pts[m, :2, 0], -hx, atol=1e-7) and np.allclose(pts[m, :2, 3], gap, atol=1e-7)
+    # diagonal approach to the (-x, -y) corner edge: distance to the edge minus the radius
+    d = rp + gap
+    p = np.array([-hx, -hy]) - d * np.array([1, 1]) / math.sqrt(2)
+    info, nrm, pts = orc.contacts(st, half, np.ones(1, np.float32), np.full(1, 0.5, np.float32),
+                                  push=np.array([p[0], p[1], p[0] + 0.1, p[1]]), s=0)
+    m = [k for k in range(len(info)) if info[k, 1] == -2][0]
+    assert np.allclose(pts[m, :info[m, 2], 3], gap, atol=1e-7)
+    assert np.allclose(nrm[m], [-1 / math.sqrt(2), -1 / math.sqrt(2), 0], atol=1e-7)
+    assert np.allclose(pts[m, :info[m, 2], :2], [-hx, -hy], atol=1e-7)
