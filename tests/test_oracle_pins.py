@@ -736,3 +736,21 @@ def test_pusher_box_contact_closed_form(orc):
     assert np.allclose(pts[m, :info[m, 2], 3], gap, atol=1e-7)
     assert np.allclose(nrm[m], [-1 / math.sqrt(2), -1 / math.sqrt(2), 0], atol=1e-7)
     assert np.allclose(pts[m, :info[m, 2], :2], [-hx, -hy], atol=1e-7)
+
+
+def test_speculative_contact_closes_the_gap_exactly(orc):
+    """A separated contact (gap d < margin) allows an approach speed of d/dt and no more:
+    a box falling at 0.5 m/s onto the table from d = 0.8 mm (0.5 m/s x dt = 2.1 mm would
+    overshoot by 1.3 mm) lands within the Gauss-Seidel residual of z = h_z after one
+    substep with v_z = -d/dt to 1 %, never penetrates by more than 1 um, and rests."""
+    h, m, mu = one_box((0.02, 0.02, 0.02), 0.1, 0.5)
+    d0 = 8e-4
+    st = G.box_row(0.01, -0.01, 0.02 + d0, v=(0.0, 0.0, -0.5))[None]
+    st1, _, _ = orc.run_substeps(st, h, m, mu, count=1)
+    assert -1e-6 <= st1[0, 2] - 0.02 <= 1e-3 * d0
+    assert abs(st1[0, 9] / (-d0 / DT) - 1) < 1e-2
+    cur = st1
+    for k in range(1, 40):
+        cur, _, _ = orc.run_substeps(cur, h, m, mu, s0=k, count=1)
+        assert cur[0, 2] - 0.02 >= -1e-6
+    assert abs(cur[0, 9]) < 1e-4
