@@ -178,10 +178,14 @@ def _single_env(rows, halves, mass=0.1, mu=0.5):
                      np.full(n, mass, np.float32), np.full(n, mu, np.float32), np.array([0], np.int32))
 
 
-@pytest.mark.parametrize("case", ["rest", "slide", "push", "stack", "tilted"])
+@pytest.mark.parametrize("case", ["rest", "slide", "push", "stack", "tilted", "drop"])
 def test_non_chaotic_240_substeps(eng, orc, case):
     far = np.array([[0.19, 0.19, 0.19, 0.19]], np.float32)   # zero-length push: pusher inactive
-    if case == "rest":
+    if case == "drop":
+        # falls 5 mm onto the table at 0.3 m/s (speculative contact, then rest)
+        sc = _single_env([(0.02, 0.01, 0.025, (1, 0, 0, 0), (0.0, 0.0, -0.3))], [[0.02, 0.03, 0.02]])
+        push = far
+    elif case == "rest":
         sc = _single_env([(0.05, -0.02, 0.015)], [[0.02, 0.03, 0.015]])
         push = far
     elif case == "slide":
