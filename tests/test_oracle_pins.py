@@ -374,6 +374,45 @@ def test_footprint_of_upright_box_is_its_rectangle(orc):
         assert np.allclose(fp[6:8], h[:2], atol=1e-7)
 
 
+@pytest.mark.parametrize("f32", [False, True])
+def test_footprint_of_tilted_box_bounds_its_corners(orc, f32):
+    """Sec. IV-B footprints under any 3-D rotation: u is the horizontal part of the box's
+    x axis (of its y axis when x is vertical), v = perp(u), and the support half widths
+    su, sv equal the largest projection of the 8 corners (scipy rotation, independent of
+    the oracle's quaternion algebra) on u and v.  A dropped or misplaced third term
+    |(R e_2)_xy . u| h_2, or a transposed rotation, moves su or sv by up to h_2."""
+    rng = np.random.default_rng(11)
+    cases = [G.quat_from_rotvec(rng.normal(size=3) * rng.uniform(0.2, 2.0)) for _ in range(40)]
+    # the box's x axis vertical (rotation about y by -90 degrees, then a yaw about the world
+    # z axis): u falls back to the horizontal part of its y axis
+    for yaw in (0.0, 0.7, -2.1):
+        q_tilt = np.array([math.cos(-math.pi / 4), 0.0, math.sin(-math.pi / 4), 0.0])
+        w1, x1, y1, z1 = G.yaw_q(yaw)
+        w2, x2, y2, z2 = q_tilt
+        cases.append(np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                               w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2]))
+    tol = 2e-7 if f32 else 1e-9
+    n_fallback = 0
+    for q in cases:
+        h = rng.uniform(0.01, 0.04, 3)
+        row = G.box_row(0.03, -0.07, 0.05, q=tuple(q))
+        st = row[None].astype(np.float32)
+        hh = h[None].astype(np.float32)
+        cx, cy, ux, uy, vx, vy, su, sv = orc.footprints(st, hh, f32=f32)[0]
+        Rm = G.rotmat(st[0, 3:7].astype(np.float64))
+        ax = Rm[:2, 0] if np.hypot(*Rm[:2, 0]) > 1e-6 else Rm[:2, 1]
+        n_fallback += np.hypot(*Rm[:2, 0]) <= 1e-6
+        ax = ax / np.linalg.norm(ax)
+        assert np.allclose([cx, cy], st[0, :2], atol=0)
+        assert np.allclose([ux, uy], ax, atol=tol * 10)
+        assert np.allclose([vx, vy], [-ax[1], ax[0]], atol=tol * 10)
+        V = G.vertices(st[0].astype(np.float64), hh[0].astype(np.float64))
+        d = V[:, :2] - st[0, :2].astype(np.float64)
+        assert abs(su - np.abs(d @ ax).max()) <= tol * 10 + 1e-12
+        assert abs(sv - np.abs(d @ np.array([-ax[1], ax[0]])).max()) <= tol * 10 + 1e-12
+    assert n_fallback == 3
+
+
 def _raster_overlap(rect, foot, cell=1e-4):
     """Cells of a 0.1 mm grid whose centres are inside both rectangles.
     rect/foot = (cx, cy, ux, uy, hu, hv) with v = perp(u)."""
