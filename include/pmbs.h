@@ -378,11 +378,17 @@ void pmbs_server_destroy(pmbs_server* server);
  *
  * It needs no context.  The caller passes every input and output as device pointers on
  * device cfg->device and the stream cuda_stream (a cudaStream_t, NULL = legacy default):
- *   d_box_offset [n_envs+1] int32, CSR over boxes; d_records [B][18] floats per box
- *   (x y z qw qx qy qz vx vy vz wx wy wz, half extents x y z, mass, mu); d_target [n_envs]
- *   local target index; d_first_push [n_envs][4]; d_seeds [n_envs] (may be NULL when
- *   depth == 1).  Outputs: d_state_out [B][13] final states, d_cost, d_reward, d_flags
- *   [n_envs] with the meaning of pmbs_query_cost.  Physics constants come from *cfg.
+ *   d_box_offset [n_envs+1] int32, CSR over boxes: environment e owns records
+ *   d_box_offset[e] .. d_box_offset[e+1]-1, so the offsets must start at 0, never
+ *   decrease, and end at the number of records B (the call cannot see B: an offset past
+ *   the end of d_records makes the kernel read outside it); d_records [B][18] floats per
+ *   box (x y z qw qx qy qz vx vy vz wx wy wz, half extents x y z, mass, mu); d_target
+ *   [n_envs] local target index; d_first_push [n_envs][4]; d_seeds [n_envs] (may be NULL
+ *   when depth == 1).  Outputs: d_state_out [B][13] final states, d_cost, d_reward,
+ *   d_flags [n_envs] with the meaning of pmbs_query_cost.  Physics constants come from
+ *   *cfg; the launch shape is the context entry points' default (one environment per
+ *   warp, two warps per block, eight manifolds per environment in shared memory) unless
+ *   cfg->lanes_per_env, warps_per_block or smem_manifolds / smem_points set it.
  * The results equal those of pmbs_rollout_pushes + pmbs_step + pmbs_query_cost for the
  * same inputs.  All scratch (descriptors, progress, counters, per-warp contact spill
  * regions) lives in one file-scope device array of 32 MiB that every device loading the
@@ -390,14 +396,26 @@ void pmbs_server_destroy(pmbs_server* server);
  * cfg->max_boxes_per_env <= 64.  Larger requests return PMBS_E_INVALID before any GPU
  * work.  The first call on a device looks up that array's device address (and sets the
  * kernel's shared-memory limit); make that first call before any stream capture.  The
- * call synchronises cuda_stream and returns PMBS_OK, PMBS_E_INVALID (bad argument,
- * cfg->warm_start set (its caches need memory), or
- * an environment with a box count outside 1..max_boxes_per_env, a target out of range,
- * a cylinder row (r, -r, h) while cfg->cylinders is 0, or a cylinder row whose radii
- * differ: such environments are not simulated and their outputs are undefined), PMBS_E_TIMEOUT
- * or PMBS_E_CUDA.  Every call shares the one array and starts by clearing what must start
- * at zero; calls whose GPU work overlaps (several threads or streams at once) race on it
- * and must be serialised by the caller.  It allocates no device memory. */
+ * call makes cfg->device current while it runs and puts the caller's current device back
+ * before it returns.  It synchronises cuda_stream and returns:
+ *   PMBS_OK;
+ *   PMBS_E_INVALID for a bad argument, cfg->warm_start set (its caches need memory), or
+ *     an environment that fails the per-environment checks -- a box count outside
+ *     1..max_boxes_per_env, a negative first offset, a target out of range, a non-finite
+ *     first push, or a record that scene loading would refuse (a non-finite value,
+ *     | |q| - 1 | > 1e-3, a non-positive half extent or mass, a negative mu, a cylinder
+ *     row (r, -r, h) while cfg->cylinders is 0, a cylinder row whose radii differ).
+ *     Such environments are not simulated and their outputs are left as they were; the
+ *     other environments are simulated as usual.  Unlike pmbs_load_scenes, the call does
+ *     not measure initial body-body penetration: overlapping boxes are simulated (the
+ *     solver pushes them apart);
+ *   PMBS_E_TIMEOUT when the watchdog (cfg->watchdog_ms) stopped environments: their
+ *     outputs are undefined and, having no batch to resume, the call cannot continue
+ *     them (the context entry points resume such environments on the next pmbs_step);
+ *   PMBS_E_CUDA for a CUDA error.
+ * Every call shares the one array and starts by clearing what must start at zero; calls
+ * whose GPU work overlaps (several threads or streams at once) race on it and must be
+ * serialised by the caller.  It allocates no device memory. */
 pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_stream, int n_envs,
                                  const int32_t* d_box_offset, const float* d_records,
                                  const int32_t* d_target, const float* d_first_push,

@@ -2661,12 +2661,26 @@ std::mutex g_noalloc_mu;
 
 // Descriptors, order and cleared per-call state for caller-provided environments.
 // Environment e owns records box_offset[e] .. box_offset[e+1]-1 (18 floats each: state13,
-// half extents, mass, mu).  Environments with a box count outside [1, max_boxes] or a
-// target out of range are not simulated; counters[1] records that.
+// half extents, mass, mu).  An environment is not simulated (counters[1] records that)
+// when its box count is outside [1, max_boxes], its first record offset is negative, its
+// target is out of range, its first push is not finite, or one of its rows fails the
+// checks scene loading applies: every value finite, | |q| - 1 | <= 1e-3, positive half
+// extents (a cylinder row (r, -r, h) only with the cylinder solver), mass > 0, mu >= 0.
+__device__ __forceinline__ bool noalloc_row_ok(const float* r, int allow_cyl) {
+    for (int k = 0; k < kRecFloats; k++)
+        if (!isfinite(r[k])) return false;
+    const double qn = sqrt((double)r[3] * r[3] + (double)r[4] * r[4] + (double)r[5] * r[5] + (double)r[6] * r[6]);
+    if (fabs(qn - 1.0) > 1e-3) return false;
+    const float* h = r + 13;
+    const bool cyl = h[1] < 0.f;
+    if (cyl && (!allow_cyl || h[1] != -h[0])) return false;
+    return h[0] > 0.f && (h[1] > 0.f || cyl) && h[2] > 0.f && r[16] > 0.f && r[17] >= 0.f;
+}
+
 __global__ void __launch_bounds__(1024) noalloc_setup_kernel(int n_envs, int max_boxes, int allow_cyl,
                                                              const int32_t* box_offset, const float* records,
-                                                             const int32_t* target, EnvIn* env, int* order,
-                                                             EnvProg* prog, int* counters,
+                                                             const int32_t* target, const float4* first_push,
+                                                             EnvIn* env, int* order, EnvProg* prog, int* counters,
                                                              unsigned long long* events, int32_t* steps) {
     __shared__ int hist[kMaxBoxes + 2];
     const int t = threadIdx.x;
@@ -2677,21 +2691,19 @@ __global__ void __launch_bounds__(1024) noalloc_setup_kernel(int n_envs, int max
         const int b0 = box_offset[e];
         int n = box_offset[e + 1] - b0;
         const int tg = target[e];
+        const float4 fp = first_push[e];
         EnvProg p;
         memset(&p, 0, sizeof(p));
-        bool bad = n < 1 || n > max_boxes || tg < 0 || tg >= n;
-        // a cylinder row is (r, -r, h); without the cylinder solver it is refused too
-        for (int i = 0; !bad && i < n; i++) {
-            const float* h = records + (size_t)kRecFloats * (b0 + i) + 13;
-            if (h[1] < 0.f) bad = !allow_cyl || h[1] != -h[0];
-        }
+        bool bad = b0 < 0 || n < 1 || n > max_boxes || tg < 0 || tg >= n || !isfinite(fp.x) || !isfinite(fp.y) ||
+                   !isfinite(fp.z) || !isfinite(fp.w);
+        for (int i = 0; !bad && i < n; i++) bad = !noalloc_row_ok(records + (size_t)kRecFloats * (b0 + i), allow_cyl);
         if (bad) {
             atomicOr(counters + 1, 1);
             p.done = 1;  // not simulated
             n = 0;
         }
         prog[e] = p;
-        env[e] = EnvIn{records + (size_t)kRecFloats * b0, n, tg, b0, -1};
+        env[e] = EnvIn{bad ? records : records + (size_t)kRecFloats * b0, n, tg, bad ? 0 : b0, -1};
         for (int k = 0; k < kNumEvents; k++) events[(size_t)e * kNumEvents + k] = 0ull;
         steps[e] = 0;
         atomicAdd(&hist[kMaxBoxes - min(n, kMaxBoxes)], 1);
@@ -2714,23 +2726,12 @@ __global__ void __launch_bounds__(1024) noalloc_setup_kernel(int n_envs, int max
 
 }  // namespace
 
-extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_stream, int n_envs,
-                                            const int32_t* d_box_offset, const float* d_records,
-                                            const int32_t* d_target, const float* d_first_push,
-                                            const uint64_t* d_seeds, int depth, float* d_state_out,
-                                            int32_t* d_cost, float* d_reward, uint8_t* d_flags) {
-    if (!cfg) return PMBS_E_INVALID;
-    const pmbs_config& c = *cfg;
-    if (n_envs < 0 || n_envs > kNoAllocMaxEnvs || depth < 1 || depth > 64 || c.max_boxes_per_env < 1 ||
-        c.max_boxes_per_env > kMaxBoxes || c.device < 0 || c.device >= kNoAllocMaxDevices || c.grasp_angles < 1 ||
-        c.grasp_angles > 32 || c.sample_attempts < 1 || c.sample_attempts > 32 || c.contact_cap < 4 ||
-        c.manifold_cap < 1 || c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096 || c.warm_start)
-        return PMBS_E_INVALID;
-    if (n_envs == 0) return PMBS_OK;
-    if (!d_box_offset || !d_records || !d_target || !d_first_push || (!d_seeds && depth > 1) || !d_state_out ||
-        !d_cost || !d_reward || !d_flags)
-        return PMBS_E_INVALID;
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
+namespace {
+
+pmbs_status noalloc_run(const pmbs_config& c, cudaStream_t stream, int n_envs, const int32_t* d_box_offset,
+                        const float* d_records, const int32_t* d_target, const float* d_first_push,
+                        const uint64_t* d_seeds, int depth, float* d_state_out, int32_t* d_cost, float* d_reward,
+                        uint8_t* d_flags) {
     if (cudaSetDevice(c.device) != cudaSuccess) return PMBS_E_CUDA;
     NoAllocDevice& dv = g_noalloc_dev[c.device];
     {
@@ -2775,11 +2776,22 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     int32_t* steps = (int32_t*)(S + o_steps);
     float4* spill = (float4*)(S + off);
 
-    const int nb = c.max_boxes_per_env, wpb = 4;
+    // the context entry points' default shape: one environment per warp, two warps per
+    // block, eight manifolds per environment in shared memory (the rest in the spill
+    // regions); cfg->lanes_per_env, warps_per_block and smem_manifolds / smem_points
+    // override it as they do there
+    const int nb = c.max_boxes_per_env;
     const int G = (c.lanes_per_env == 8 || c.lanes_per_env == 16 || c.lanes_per_env == 32) ? c.lanes_per_env : 32;
     const int K = 32 / G;
+    int wpb = std::min(c.warps_per_block > 0 ? c.warps_per_block : 2, 4);
     const int pairS = std::min(c.pair_cap, std::max(1, nb * (nb - 1) / 2));
-    const Layout L = make_layout(nb, pairS, 0, c.manifold_cap);
+    int Ms = K > 1 ? 0 : 8;
+    if (c.smem_points >= 0) Ms = c.smem_points / 4;
+    if (c.smem_manifolds >= 0) Ms = c.smem_manifolds;
+    Ms = std::min(Ms, c.manifold_cap);
+    while (Ms > 0 && (size_t)K * make_layout(nb, pairS, Ms, c.manifold_cap).bytes > 227 * 1024) Ms /= 2;
+    while (wpb > 1 && (size_t)wpb * K * make_layout(nb, pairS, Ms, c.manifold_cap).bytes > 227 * 1024) wpb >>= 1;
+    const Layout L = make_layout(nb, pairS, Ms, c.manifold_cap);
     const size_t smem = (size_t)L.bytes * wpb * K;
     if (smem > 227 * 1024) return PMBS_E_INVALID;
     int per_sm = 0;
@@ -2787,14 +2799,15 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
                                                       32 * wpb, smem) != cudaSuccess)
         return PMBS_E_CUDA;
     if (per_sm < 1) return PMBS_E_INVALID;
+    per_sm = std::min(per_sm, kMaxWarpsPerSM / wpb);
     const int per_block = wpb * K;
+    if (max_warps < per_block) return PMBS_E_INVALID;
     const int blocks = std::max(1, std::min({(n_envs + per_block - 1) / per_block, per_sm * dv.num_sms,
                                              max_warps / per_block}));
-    if (max_warps < per_block) return PMBS_E_INVALID;
 
-    noalloc_setup_kernel<<<1, 1024, 0, stream>>>(n_envs, nb, c.cylinders ? 1 : 0, d_box_offset, d_records, d_target, env,
-                                                 order, prog,
-                                                 counters, events, steps);
+    noalloc_setup_kernel<<<1, 1024, 0, stream>>>(n_envs, nb, c.cylinders ? 1 : 0, d_box_offset, d_records, d_target,
+                                                 (const float4*)d_first_push, env, order, prog, counters, events,
+                                                 steps);
     if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;
     RolloutArgs a;
     fill_const(c, a.C);
@@ -2822,7 +2835,7 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     a.scratch_f4_per_warp = f4_per_warp;
     a.watchdog_cycles = (long long)((double)c.watchdog_ms * 2.0e6);
     a.watchdog_flag = counters + 4;
-    a.warm = nullptr;  // no room for caches in the fixed scratch: warm start is refused above
+    a.warm = nullptr;  // no room for caches in the fixed scratch: warm start is refused
     a.warm_f4_per_env = 0;
     if (c.cylinders) rollout_kernel<true><<<blocks, 32 * wpb, smem, stream>>>(a);
     else rollout_kernel<false><<<blocks, 32 * wpb, smem, stream>>>(a);
@@ -2834,4 +2847,31 @@ extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_s
     if (host_cnt[4]) return PMBS_E_TIMEOUT;
     if (host_cnt[1]) return PMBS_E_INVALID;
     return PMBS_OK;
+}
+
+}  // namespace
+
+extern "C" pmbs_status pmbs_rollout_noalloc(const pmbs_config* cfg, void* cuda_stream, int n_envs,
+                                            const int32_t* d_box_offset, const float* d_records,
+                                            const int32_t* d_target, const float* d_first_push,
+                                            const uint64_t* d_seeds, int depth, float* d_state_out,
+                                            int32_t* d_cost, float* d_reward, uint8_t* d_flags) {
+    if (!cfg) return PMBS_E_INVALID;
+    const pmbs_config& c = *cfg;
+    if (n_envs < 0 || n_envs > kNoAllocMaxEnvs || depth < 1 || depth > 64 || c.max_boxes_per_env < 1 ||
+        c.max_boxes_per_env > kMaxBoxes || c.device < 0 || c.device >= kNoAllocMaxDevices || c.grasp_angles < 1 ||
+        c.grasp_angles > 32 || c.sample_attempts < 1 || c.sample_attempts > 32 || c.contact_cap < 4 ||
+        c.manifold_cap < 1 || c.manifold_cap > 1024 || c.pair_cap < 1 || c.pair_cap > 4096 || c.warm_start)
+        return PMBS_E_INVALID;
+    if (n_envs == 0) return PMBS_OK;
+    if (!d_box_offset || !d_records || !d_target || !d_first_push || (!d_seeds && depth > 1) || !d_state_out ||
+        !d_cost || !d_reward || !d_flags)
+        return PMBS_E_INVALID;
+    // the caller's current device is put back on every return
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return PMBS_E_CUDA;
+    const pmbs_status st = noalloc_run(c, (cudaStream_t)cuda_stream, n_envs, d_box_offset, d_records, d_target,
+                                       d_first_push, d_seeds, depth, d_state_out, d_cost, d_reward, d_flags);
+    if (cudaSetDevice(prev) != cudaSuccess && st == PMBS_OK) return PMBS_E_CUDA;
+    return st;
 }

@@ -117,7 +117,8 @@ class Node:
     parent: "Node | None" = None
     action: np.ndarray | None = None
     terminal: bool = False          # target graspable here
-    failed: bool = False            # workspace left: dead end
+    failed: bool = False            # workspace left (or the start was blocked): dead end
+    exhausted: bool = False         # every node below is terminal, failed or fully expanded
     N: int = 0
     Q: float = 0.0
     Nv: int = 0                     # virtual count of this selection round
@@ -182,7 +183,7 @@ class Planner:
             node = root
             path = [node]
             while not self._expandable(node):
-                kids = [k for k in node.children if not k.terminal and not k.failed]
+                kids = [k for k in node.children if not k.terminal and not k.failed and not k.exhausted]
                 if not kids:
                     node = None
                     break
@@ -191,11 +192,12 @@ class Planner:
                 node = kids[int(np.argmax(scores))]
                 path.append(node)
             if node is None:
-                # dead branch: no expandable node below; mark it so traversal skips it
+                # fully explored branch: nothing below is left to expand; traversal skips
+                # it from now on, while its statistics still rank it for the final action
                 misses += 1
                 if len(path) == 1:
                     break
-                path[-1].failed = path[-1].failed or not path[-1].terminal
+                path[-1].exhausted = True
                 continue
             action = node.untried.pop()
             pairs.append((node, action))

@@ -2,8 +2,22 @@
 
 Bit-exact: broadphase pair lists, grasp decisions, start-pose checks and sampled pushes on
 identical FP32 snapshots (the oracle's binary32 twins).  Tolerances: state after one
-substep within 1e-4 m / 1e-3 rad; non-chaotic scenes after 240 substeps within
-1e-3 m / 1e-2 rad; tiny-config cost agreement >= 90 %.
+substep within 1e-4 m / 1e-3 rad, linear velocity within V_TOL and angular velocity within
+W_TOL; non-chaotic scenes after 240 substeps within 1e-3 m / 1e-2 rad; tiny-config cost
+agreement >= 90 %.
+
+Velocity bounds after one substep, from FP32 rounding (Sec. III-A transition: the solve's
+output is the new velocity).  The largest velocity a substep produces is about 0.5 m/s
+(the Baumgarte target 0.2 / dt x 1 cm of initial overlap in the squeezed clutter; the
+pusher moves at 0.1 m/s, gravity adds 0.04 m/s).  A body takes part in at most about 1000
+dependent row updates per substep (10 iterations x up to ~8 manifolds x 4 points x 3
+rows), each rounding at 2^-24 relative with a few operations per update; a random walk of
+those errors stays below 0.5 x 6e-8 x sqrt(1000) x 4 = 4e-6 m/s, so V_TOL = 1e-5 m/s.
+Angular velocity carries that error through a lever arm: an impulse that changes a box's
+velocity by dv, applied at a point of its surface, changes its spin about body axis i by
+at most 3 dv / sqrt(h_j^2 + h_k^2) (inertia m (h_j^2 + h_k^2) / 3, lever arm at most
+sqrt(h_j^2 + h_k^2)); with half extents >= 0.01 m that is 212 dv per m/s, so
+W_TOL = 212 x 1e-5 = 2.1e-3 rad/s, rounded up to 3e-3.
 """
 import math
 
@@ -13,6 +27,9 @@ import pytest
 from tests import _geom as G
 
 pytestmark = pytest.mark.gpu
+
+V_TOL = 1e-5   # m/s after one substep (derivation in the module docstring)
+W_TOL = 3e-3   # rad/s after one substep
 
 
 @pytest.fixture(scope="module")
@@ -153,21 +170,36 @@ def _run_gpu_substeps(eng, sc, pushes, count, depth=1, seeds=None):
     return st, steps
 
 
+def _state_errors(got, ref):
+    """Per-body position, rotation, linear and angular velocity errors."""
+    return (np.abs(got[:, :3] - ref[:, :3]).max(1), _angle_err(got[:, 3:7].astype(float), ref[:, 3:7]),
+            np.abs(got[:, 7:10] - ref[:, 7:10]).max(1), np.abs(got[:, 10:13] - ref[:, 10:13]).max(1))
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_one_substep_state_parity(eng_overlap, orc, seed):
+    """All 13 state numbers of every box after one substep of 64 clutter scenes (3-30
+    boxes, squeezed into contact): position, rotation, and the solve's direct output, the
+    linear and angular velocity."""
     sg = _sg()
     sc = _clutter_batch(400 + seed, 64, 3, 30, squeeze=0.95)
     rng = np.random.default_rng(seed)
     pushes = np.stack([sg._random_valid_push(rng, sc, e) for e in range(sc.n_scenes)])
     st, steps = _run_gpu_substeps(eng_overlap, sc, pushes, 1)
     s0 = sg.state13(sc)
+    worst = np.zeros(4)
     for e in range(sc.n_scenes):
         a, b = sc.box_offset[e], sc.box_offset[e + 1]
         ref, _, _ = orc.run_substeps(s0[a:b], sc.half[a:b], sc.mass[a:b], sc.mu[a:b], push=pushes[e].astype(float),
                                      count=1)
         assert steps[e] == 1
-        assert np.abs(st[a:b, :3] - ref[:, :3]).max() <= 1e-4
-        assert _angle_err(st[a:b, 3:7].astype(float), ref[:, 3:7]).max() <= 1e-3
+        ex, eq, ev, ew = _state_errors(st[a:b], ref)
+        worst = np.maximum(worst, [ex.max(), eq.max(), ev.max(), ew.max()])
+        assert ex.max() <= 1e-4 and eq.max() <= 1e-3, f"env {e}"
+        assert ev.max() <= V_TOL, f"env {e}: linear velocity error {ev.max():.3e} m/s"
+        assert ew.max() <= W_TOL, f"env {e}: angular velocity error {ew.max():.3e} rad/s"
+    print(f"one substep, seed {seed}: max error x {worst[0]:.2e} m, rotation {worst[1]:.2e} rad, "
+          f"v {worst[2]:.2e} m/s, w {worst[3]:.2e} rad/s")
 
 
 def _single_env(rows, halves, mass=0.1, mu=0.5):
@@ -211,8 +243,12 @@ def test_non_chaotic_240_substeps(eng, orc, case):
 
 
 def test_tiny_config_cost_agreement(eng, orc):
+    """The tiny workload (16 pushes through a 5-box scene, depth 1) over 8 seeds: long
+    multi-contact trajectories are chaotic (FP32 and FP64 diverge), so parity is stated as
+    the cost-to-go agreement rate (>= 90 %) and reported with the distribution of the
+    end-state error; decisions taken on the GPU's own final states are bit-exact."""
     sg = _sg()
-    agree, total, errs = 0, 0, []
+    agree, total, errs, env_errs = 0, 0, [], []
     for seed in range(1, 9):
         sc, pushes = sg.config_tiny(seed=seed)
         ids = eng.load(sc)
@@ -223,7 +259,11 @@ def test_tiny_config_cost_agreement(eng, orc):
                           depth=1, threads=8)
         agree += int(np.sum(out["cost"] == ref.cost))
         total += len(pushes)
-        errs.append(np.abs(out["state"][:, :3] - ref.state[:, :3]).max())
+        d = np.abs(out["state"][:, :3] - ref.state[:, :3]).max(1)
+        errs.append(d.max())
+        for e in range(len(pushes)):
+            if not out["flags"][e] & 2:
+                env_errs.append(d[envs.box_offset[e]:envs.box_offset[e + 1]].max())
         # flags that do not depend on the trajectory agree exactly
         assert np.array_equal(out["flags"] & 2, ref.flags & 2)
         # decisions on the GPU's own final states are bit-exact with the binary32 twin
@@ -232,7 +272,10 @@ def test_tiny_config_cost_agreement(eng, orc):
             if out["flags"][e] & 6:
                 continue
             assert orc.grasp(out["state"][a:b], envs.half[a:b], 0, f32=True) == (out["cost"][e] == 1)
-    print(f"tiny config: cost agreement {agree}/{total}, max end-state error {max(errs):.2e} m")
+    q = np.percentile(env_errs, [50, 90, 99, 100])
+    print(f"tiny config: cost agreement {agree}/{total} ({100.0 * agree / total:.1f} %); end-state position "
+          f"error over {len(env_errs)} simulated envs (max over boxes, m): p50 {q[0]:.2e} p90 {q[1]:.2e} "
+          f"p99 {q[2]:.2e} max {q[3]:.2e}; envs within 1e-3 m: {np.mean(np.array(env_errs) <= 1e-3) * 100:.1f} %")
     assert agree >= 0.9 * total
 
 
@@ -330,7 +373,9 @@ def test_max_size_scene_runs(eng, orc):
     push = sg._random_valid_push(rng, sc, 0)[None]
     st, steps = _run_gpu_substeps(eng, sc, push, 1)
     ref, _, _ = orc.run_substeps(sg.state13(sc), sc.half, sc.mass, sc.mu, push=push[0].astype(float), count=1)
-    assert np.abs(st[:, :3] - ref[:, :3]).max() <= 1e-4
+    ex, eq, ev, ew = _state_errors(st, ref)
+    assert ex.max() <= 1e-4 and eq.max() <= 1e-3
+    assert ev.max() <= V_TOL and ew.max() <= W_TOL
 
 
 def test_child_states_equal_state_after_first_push(eng):
@@ -387,7 +432,9 @@ def test_uneven_4096_env_launch_sampled_parity(eng, orc):
         a, z = scenes.box_offset[e], scenes.box_offset[e + 1]
         ref, _, _ = orc.run_substeps(s0[a:z], scenes.half[a:z], scenes.mass[a:z], scenes.mu[a:z],
                                      push=pushes[e].astype(float), count=1)
-        assert np.abs(st1[a:z, :3] - ref[:, :3]).max() <= 1e-4
+        ex, eq, ev, ew = _state_errors(st1[a:z], ref)
+        assert ex.max() <= 1e-4 and eq.max() <= 1e-3
+        assert ev.max() <= V_TOL and ew.max() <= W_TOL
     out = eng.rollout(ids, pushes, depth=3, seeds=seeds)
     assert ((out["flags"] & 2) == 0).mean() > 0.95
     for e in sample:
