@@ -90,6 +90,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="time the default launch shape")
     ap.add_argument("--no-heightmaps", action="store_true")
+    ap.add_argument("--no-phases", action="store_true", help="skip the per-phase cycle split")
     ap.add_argument("--cylinders", type=int, default=1, help="also time the cylinder workload (0 = skip)")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'lanes,warps_per_block,smem_manifolds' instead of autotuning")
@@ -366,6 +367,25 @@ def run_ours(args):
     elapsed, total_env_steps = multigpu.reduce_job(elapsed, env_steps * args.steps, device=dev)
     value = total_env_steps / elapsed
 
+    # per-phase split of the warps' cycles (library phase timers, one untimed launch of the
+    # same batch in the same launch shape)
+    phase = None
+    if not args.no_phases:
+        teng = pmbs.Engine(device=local, mem_budget_bytes=int(args.arena_gb * 2 ** 30), max_envs=max(args.envs, 1),
+                           stream=pmbs.C.c_void_p(stream.cuda_stream), phase_timers=1)
+        if tuned is not None:
+            teng.set_launch_shape(tuned["lanes_per_env"], tuned["warps_per_block"], -1, tuned["smem_manifolds"])
+        tids = teng.load(scenes)
+        tb = teng.rollout_pushes(tids, pushes, args.depth, seeds)
+        teng.step(tb, 0)
+        cyc = teng.query_phase_cycles(tb).astype(np.float64)
+        teng.release_batch(tb)
+        teng.close()
+        tot = cyc.sum(0)
+        phase = {"cycles_share": {n: float(v / tot.sum()) for n, v in zip(pmbs.PHASE_NAMES, tot)},
+                 "cycles_per_env_step": float(tot.sum() / max(env_steps, 1)),
+                 "source": "pmbs_query_phase_cycles on one untimed launch of the same batch (phase_timers=1)"}
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -484,6 +504,14 @@ def run_ours(args):
     max_mhz = clocks["sm_max_mhz"] or 2032.0
     peak = flops.fp32_peak_tflops(sms, max_mhz)
     achieved = flops_per_launch / kernel_s / 1e12
+    solve = None
+    if phase is not None:
+        # the contact solve's own rate: its algorithmic flops over the share of the launch
+        # its warps spent in it
+        sh = phase["cycles_share"]["contact_solve"]
+        rate = flops_phases["contact_solve"] / (kernel_s * sh) / 1e12
+        solve = {"achieved": rate, "frac": rate / peak, "cycles_share": sh,
+                 "flops_per_launch": flops_phases["contact_solve"]}
     sha = kernel_source_sha()
     default_workload = (args.envs, args.depth, args.seed) == (4096, 3, 3)
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["source_sha"] == sha and default_workload else None
@@ -507,7 +535,9 @@ def run_ours(args):
                      "flops_per_launch": flops_per_launch, "flops_by_phase": flops_phases,
                      "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "fma_probe_tflops": peak_fma,
-                     "hbm_achieved_gbs": state_bytes / kernel_s / 1e9},
+                     "hbm_achieved_gbs": state_bytes / kernel_s / 1e9,
+                     "contact_solve": solve},
+        "phases": phase,
         "clocks": clocks,
         "e2e": e2e,
         "serving": serving,

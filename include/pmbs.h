@@ -67,6 +67,12 @@ enum {
 /* Event counters per environment (pmbs_query_events), in this order. */
 #define PMBS_NUM_EVENTS 18
 
+/* Phase timers per environment (pmbs_query_phase_cycles), in this order: push set-up
+ * (footprints, start check, contour sampler), gravity + frames + broadphase,
+ * narrowphase, contact preparation, colouring, contact solve (with the optional warm
+ * start), integration, end of push (workspace and grasp tests, child state). */
+#define PMBS_NUM_PHASES 8
+
 typedef struct {
     int device;                 /* CUDA device ordinal */
     int max_envs;               /* largest batch accepted by one pmbs_rollout_pushes */
@@ -121,6 +127,12 @@ typedef struct {
                                    0 (default) = boxes only: an environment with a cylinder
                                    row is refused like one with a bad box count.  The other
                                    entry points decide from the loaded scenes. */
+    int phase_timers;           /* 0 (default); 1 = every environment accumulates the SM clock
+                                   cycles its warp (or lane group) spends in each phase of
+                                   PMBS_NUM_PHASES, read with pmbs_query_phase_cycles.  Costs
+                                   a clock read and a shared-memory add per phase and
+                                   substep; off, one uniform branch per phase.  Ignored by
+                                   pmbs_rollout_noalloc. */
 } pmbs_config;
 
 /* Fill *cfg with the defaults listed above.  Never fails. */
@@ -241,6 +253,24 @@ pmbs_status pmbs_query_states(pmbs_ctx* ctx, int64_t batch, float* out_states,
  * clipped vertices, colours, box-box contact points, PGS point visits between two boxes)
  * used to count the algorithmic flops of a launch. */
 pmbs_status pmbs_query_events(pmbs_ctx* ctx, int64_t batch, uint64_t* out_events);
+
+/* Status word of the bounds-checked build (libpmbs_checked.so, compiled with
+ * -DPMBS_BOUNDS_CHECK=1): out[0] = number of out-of-range indices met by the rollout
+ * kernel on ctx's device since the last reset (shared-memory arrays, contact manifolds,
+ * environments, state rows, warm-start records), out[1..3] = the first one's array id,
+ * index and capacity.  Such an access was redirected to a sink and the kernel carried on
+ * (no trap).  reset != 0 clears the word afterwards.  Synchronises the context's stream.
+ * The release library returns PMBS_E_INVALID and zeros. */
+pmbs_status pmbs_check_status(pmbs_ctx* ctx, uint32_t* out, int reset);
+
+/* Per-phase SM clock cycles of every environment of a batch, [n_envs][PMBS_NUM_PHASES]
+ * (order above), summed over its pushes and substeps and over every launch so far; all
+ * zero unless the context was created with cfg->phase_timers = 1.  An environment's
+ * phases add up to the cycles its warp spent on it outside fetching and loading it; the
+ * cycles count while other warps share the SM, so they measure latency under the launch's
+ * load, not issue slots.  Synchronises the context's stream.  Unknown batch or NULL
+ * output -> PMBS_E_INVALID. */
+pmbs_status pmbs_query_phase_cycles(pmbs_ctx* ctx, int64_t batch, uint64_t* out_cycles);
 
 /* Number of environments and boxes in the batch. */
 pmbs_status pmbs_batch_info(pmbs_ctx* ctx, int64_t batch, int32_t* out_n_envs,

@@ -83,6 +83,8 @@ struct RolloutArgs {
     int* watchdog_flag;
     float4* warm;               // warm-start caches, warm_f4_per_env per environment (or null)
     size_t warm_f4_per_env;
+    unsigned long long* phase;  // [n_envs][kNumPhases] cycles when C.timers (else unused)
+    long long n_rows;           // rows of state and child (the bounds-checked build checks row indices)
 };
 
 // ------------------------------------------------------------------ device: environments
@@ -152,9 +154,10 @@ __device__ __forceinline__ void store_state(const WarpMem& W, int n, float* dst,
 // warp's collectives).  Returns true on a cap overflow.
 template <bool kCyl>
 __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, int n_env, bool on, const Pusher& pu,
-                                        int s, const Grp& g, float4* warm, int& warm_n) {
+                                        int s, const Grp& g, float4* warm, int& warm_n, PhaseClock& pc) {
     const SimConst& C = a.C;
     const int n = on ? n_env : 0;
+    const bool tm = C.timers != 0, rec = on && g.gl == 0;
     const int done = s < pu.moving ? s : pu.moving;
     const float travel = (C.pspeed * C.dt) * (float)done;
     const float Px = pu.sx + pu.dx * travel, Py = pu.sy + pu.dy * travel;
@@ -169,12 +172,13 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
     frames_and_aabb(W, n, g, C.margin);
     __syncwarp();
     bool ovf = broadphase(W, n, g, C.pair_cap, on && pu.active, Px, Py, C);
+    pc.mark(tm, W, PH_BROADPHASE, rec);
     {
         NarrowStats st{0, 0, 0, 0, 0, 0, 0};
         ovf |= narrowphase<kCyl>(W, g, on, C, Px, Py, st);
         // count now, so that nothing of the narrowphase stays live through the solve
         if (on && g.gl == 0) {
-            unsigned long long* ev = W.ev().ptr();
+            const SArr<unsigned long long> ev = W.ev();
             ev[EV_SUBSTEPS] += 1;
             ev[EV_BOX_STEPS] += n;
             ev[EV_PAIR_TESTS] += n * (n - 1) / 2;
@@ -189,8 +193,11 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
             ev[EV_BB_POINTS] += st.bb_points;
         }
     }
+    pc.mark(tm, W, PH_NARROWPHASE, rec);
     prepare(W, g, on, C);
+    pc.mark(tm, W, PH_PREP, rec);
     ovf |= colour_manifolds(W, n, g, on);
+    pc.mark(tm, W, PH_COLOUR, rec);
     if (C.warm && a.warm) warm_start(W, g, on, C, warm, warm_n);
     int bb_visits = 0;
     const int visits = pgs(W, g, on, C.iters, V, bb_visits);
@@ -198,10 +205,12 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
         const int m = warm_save(W, g, on, warm);
         if (on) warm_n = m;
     }
+    pc.mark(tm, W, PH_SOLVE, rec);
     integrate(W, n, g, C.dt);
+    pc.mark(tm, W, PH_INTEGRATE, rec);
     const int v_all = g.sum(visits), v_bb = g.sum(bb_visits);
     if (on && g.gl == 0) {
-        unsigned long long* ev = W.ev().ptr();
+        const SArr<unsigned long long> ev = W.ev();
         ev[EV_PGS_MAN] += (unsigned long long)C.iters * W.scal()[6];
         ev[EV_PGS_PTS] += v_all;
         ev[EV_COLOURS] += W.scal()[5];
@@ -227,6 +236,8 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
     int budget = 0;
     long long t_start = 0;
     bool ovf = false, timed_out = false;
+    const bool tm = C.timers != 0;
+    PhaseClock pc;
     for (;;) {
         // 1. fetch
         const bool need = e < 0 && !exhausted;
@@ -237,8 +248,17 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
         if (need) {
             if (slot < a.n_envs) {
                 e = a.order[slot];
+#if PMBS_BOUNDS_CHECK
+                if (!check_index(CHK_ENV, e, a.n_envs)) e = 0;
+#endif
                 ei = a.env[e];
                 pg = a.prog[e];
+#if PMBS_BOUNDS_CHECK
+                // every state and child row of the environment lies inside the batch
+                if (!check_index(CHK_STATE_ROW, ei.box_off, a.n_rows) ||
+                    !check_index(CHK_STATE_ROW, (long long)ei.box_off + ei.n - 1, a.n_rows))
+                    pg.done = 1;
+#endif
                 if (pg.done) e = -1;
                 else fresh = true;
             } else {
@@ -256,13 +276,16 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
             ovf = false;
             timed_out = false;
             t_start = clock64();
-            if (g.gl == 0)
+            if (g.gl == 0) {
                 for (int k = 0; k < kNumEvents; k++) W.ev()[k] = 0ull;
+                for (int k = 0; k < kNumPhases; k++) W.ph()[k] = 0ull;
+            }
         }
         const bool active = e >= 0;
         if (!__any_sync(kFull, active || !exhausted)) break;
         // 2. push set-up: the first push's start check, or a sampled push
         const bool setup = active && !pg.push_ready;
+        pc.start(tm);
         if (__any_sync(kFull, setup)) {
             compute_footprints(W, setup ? ei.n : 0, g);
             const bool first = setup && pg.k == 1;
@@ -296,11 +319,12 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
                 pg.push_ready = 1;
             }
         }
+        pc.mark(tm, W, PH_PUSH_SETUP, setup && g.gl == 0);
         // 3. one substep
         const bool run = active && !pg.done && pg.s < C.substeps && budget > 0;
         const Pusher pu = make_pusher(C, pg.push, pg.noop != 0);
         ovf |= substep<kCyl>(a, W, ei.n, run, pu, pg.s, g, a.warm ? a.warm + (size_t)(e < 0 ? 0 : e) * a.warm_f4_per_env : nullptr,
-                       pg.pad[0]);
+                       pg.pad[0], pc);
         // bounded run time per environment and launch (the shuffle runs in every lane)
         const bool late = g.bcast((int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
         if (run) {
@@ -343,6 +367,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
                 }
             }
         }
+        pc.mark(tm, W, PH_PUSH_END, endp && g.gl == 0);
         // 5. retire: write the environment back and free the slot
         const bool fin = active && (pg.done || budget <= 0 || timed_out);
         if (fin) {
@@ -352,6 +377,10 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
                 a.prog[e] = pg;
                 unsigned long long* ev = a.events + (size_t)e * kNumEvents;
                 for (int k = 0; k < kNumEvents; k++) ev[k] += W.ev()[k];
+                if (tm) {
+                    unsigned long long* ph = a.phase + (size_t)e * kNumPhases;
+                    for (int k = 0; k < kNumPhases; k++) ph[k] += W.ph()[k];
+                }
                 a.steps[e] = pg.steps;
                 if (pg.done) {
                     a.cost[e] = pg.cost;
@@ -883,6 +912,7 @@ struct Batch {
     uint8_t* flags = nullptr;
     int32_t* steps = nullptr;
     unsigned long long* events = nullptr;
+    unsigned long long* phase = nullptr;  // per-phase cycles (cfg.phase_timers)
     float4* warm = nullptr;         // warm-start caches (cfg.warm_start), one per environment
     bool finished = false;
     int G = 32, wpb = 4, Ms = 0;
@@ -968,6 +998,7 @@ void fill_const(const pmbs_config& c, SimConst& C) {
     C.Pcap = c.contact_cap;
     C.Mcap = c.manifold_cap;
     C.pair_cap = c.pair_cap;
+    C.timers = c.phase_timers ? 1 : 0;
     for (int k = 0; k < 32; k++) {
         const double th = k < c.grasp_angles ? k * M_PI / c.grasp_angles : 0.0;
         C.gcos[k] = (float)std::cos(th);
@@ -1167,7 +1198,8 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
                  o_state = take(sizeof(float) * 13 * std::max(boxes, (size_t)1)),
                  o_child = take(sizeof(float) * 13 * std::max(boxes, (size_t)1)), o_cost = take(sizeof(int32_t) * ne),
                  o_rew = take(sizeof(float) * ne), o_flags = take(ne), o_steps = take(sizeof(int32_t) * ne),
-                 o_ev = take(sizeof(unsigned long long) * kNumEvents * ne);
+                 o_ev = take(sizeof(unsigned long long) * kNumEvents * ne),
+                 o_ph = take(sizeof(unsigned long long) * kNumPhases * ne);
     const size_t warm_f4 = (size_t)kWarmF4 * ctx->cfg.manifold_cap;
     const size_t o_warm = ctx->cfg.warm_start ? take(sizeof(float4) * warm_f4 * ne) : 0;
     b.off = ctx->arena.alloc(sz);
@@ -1188,6 +1220,7 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
     b.flags = (uint8_t*)(base + o_flags);
     b.steps = (int32_t*)(base + o_steps);
     b.events = (unsigned long long*)(base + o_ev);
+    b.phase = (unsigned long long*)(base + o_ph);
     b.warm = ctx->cfg.warm_start ? (float4*)(base + o_warm) : nullptr;
     auto bail = [&](const char* what, cudaError_t e) {
         ctx->arena.release(b.off, b.bytes);
@@ -1196,6 +1229,7 @@ pmbs_status rollout_common(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, 
     cudaError_t e = cudaMemsetAsync(base + o_cnt, 0, sizeof(int) * 8, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.prog, 0, sizeof(EnvProg) * ne, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.events, 0, sizeof(unsigned long long) * kNumEvents * ne, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.phase, 0, sizeof(unsigned long long) * kNumPhases * ne, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.steps, 0, sizeof(int32_t) * ne, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.seeds, 0, sizeof(uint64_t) * ne, ctx->stream);
     if (n_envs > 0 && e == cudaSuccess) {
@@ -1306,6 +1340,8 @@ pmbs_status launch_rollout_once(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaS
     a.watchdog_flag = b.counters + 4;
     a.warm = b.warm;
     a.warm_f4_per_env = (size_t)kWarmF4 * c.manifold_cap;
+    a.phase = b.phase;
+    a.n_rows = (long long)b.state_boxes;
     CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), stream));
     if (b.cyl) rollout_kernel<true><<<blocks, threads, smem, stream>>>(a);
     else rollout_kernel<false><<<blocks, threads, smem, stream>>>(a);
@@ -1999,6 +2035,20 @@ pmbs_status pmbs_query_events(pmbs_ctx* ctx, int64_t batch, uint64_t* out_events
     return PMBS_OK;
 }
 
+pmbs_status pmbs_query_phase_cycles(pmbs_ctx* ctx, int64_t batch, uint64_t* out_cycles) {
+    if (!ctx) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    Batch* b = find_batch(ctx, batch);
+    if (!b || !out_cycles) return fail(ctx, PMBS_E_INVALID, "unknown batch or null output");
+    if (b->n_envs == 0) return PMBS_OK;
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaMemcpyAsync(out_cycles, b->phase, sizeof(uint64_t) * kNumPhases * b->n_envs, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return PMBS_OK;
+}
+
 pmbs_status pmbs_batch_info(pmbs_ctx* ctx, int64_t batch, int32_t* out_n_envs, int32_t* out_n_boxes) {
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -2239,6 +2289,26 @@ pmbs_status pmbs_set_launch_shape(pmbs_ctx* ctx, int lanes_per_env, int warps_pe
     ctx->fixed_Ps = smem_points;
     ctx->fixed_Ms = smem_manifolds;
     return PMBS_OK;
+}
+
+pmbs_status pmbs_check_status(pmbs_ctx* ctx, uint32_t* out, int reset) {
+    if (!ctx || !out) return PMBS_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    for (int k = 0; k < 4; k++) out[k] = 0u;
+#if PMBS_BOUNDS_CHECK
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyFromSymbol(out, g_check_status, sizeof(uint32_t) * 4));
+    if (reset) {
+        const uint32_t zero[4] = {0u, 0u, 0u, 0u};
+        CU(cudaMemcpyToSymbol(g_check_status, zero, sizeof(zero)));
+    }
+    return PMBS_OK;
+#else
+    (void)reset;
+    return fail(ctx, PMBS_E_INVALID, "library built without bounds checks (build with PMBS_BOUNDS_CHECK=1)");
+#endif
 }
 
 pmbs_status pmbs_fp32_peak(pmbs_ctx* ctx, double* out_tflops) {
@@ -2837,6 +2907,9 @@ pmbs_status noalloc_run(const pmbs_config& c, cudaStream_t stream, int n_envs, c
     a.watchdog_flag = counters + 4;
     a.warm = nullptr;  // no room for caches in the fixed scratch: warm start is refused
     a.warm_f4_per_env = 0;
+    a.C.timers = 0;    // phase timers have no output here
+    a.phase = nullptr;
+    a.n_rows = LLONG_MAX;  // the record count is the caller's (not passed)
     if (c.cylinders) rollout_kernel<true><<<blocks, 32 * wpb, smem, stream>>>(a);
     else rollout_kernel<false><<<blocks, 32 * wpb, smem, stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;

@@ -27,6 +27,12 @@ enum {
     EV_POINTS, EV_MANIFOLDS, EV_PGS_MAN, EV_PGS_PTS, EV_PUSH_EVALS, EV_SAMPLE_ATTEMPTS,
     EV_CLIP_VERTS, EV_COLOURS, EV_BB_POINTS, EV_PGS_BB_POINTS
 };
+// Phase timers (SimConst::timers): SM clock cycles an environment's group spends in each
+// part of its work, summed over its substeps and pushes.
+constexpr int kNumPhases = 8;
+enum {
+    PH_PUSH_SETUP = 0, PH_BROADPHASE, PH_NARROWPHASE, PH_PREP, PH_COLOUR, PH_SOLVE, PH_INTEGRATE, PH_PUSH_END
+};
 enum { FLAG_GRASP1 = 1, FLAG_INVALID_START = 2, FLAG_OUT_OF_WS = 4, FLAG_OVERFLOW = 8, FLAG_NOOP = 16 };
 
 // Physical and algorithmic constants of a launch.
@@ -40,6 +46,7 @@ struct SimConst {
     int warm;         // carry contact impulses over substeps
     float warm_tol2;  // squared match distance
     int Pcap, Mcap, pair_cap;
+    int timers;       // accumulate per-phase clock cycles (off: one uniform branch per phase)
     float gcos[32], gsin[32];
 };
 
@@ -88,7 +95,7 @@ __host__ __device__ inline Layout make_layout(int NB, int pairS, int Ms, int Mca
     L.o_mask = o; o += 4 * NB;
     L.o_scal = o; o += 4 * 16;
     o = align_up(o, 8);
-    L.o_ev = o; o += 8 * kNumEvents;  // event counters of the running environment (8-byte aligned)
+    L.o_ev = o; o += 8 * (kNumEvents + kNumPhases);  // event counters and phase cycles of the running environment (8-byte aligned)
     L.o_mAB = o; o += 2 * Mcap;
     L.o_order = o; o += 2 * Mcap;
     L.o_cstart = o; o += 2 * (kMaxColours + 2);
@@ -108,44 +115,96 @@ __host__ __device__ inline int scratch_f4_per_warp(int Mcap) { return kConFields
 // The block's dynamic shared memory; every kernel that binds warp regions uses it.
 extern __shared__ __align__(16) unsigned char pmbs_smem[];
 
+// Bounds-checked build (compiled with -DPMBS_BOUNDS_CHECK=1 into a library of its own):
+// every shared-memory array index, every contact manifold index and every global row or
+// environment index of the rollout kernel is checked against its capacity.  An index out
+// of range is recorded in a status word -- violations, then the first one's array id,
+// index and capacity -- and the access is redirected to a sink (a load reads the sink, a
+// store lands there), so the kernel carries on and ends normally: no trap, no fault.
+#ifndef PMBS_BOUNDS_CHECK
+#define PMBS_BOUNDS_CHECK 0
+#endif
+#if PMBS_BOUNDS_CHECK
+enum {
+    CHK_BV = 1, CHK_BW, CHK_BI0, CHK_BI1, CHK_X, CHK_Q, CHK_H, CHK_IB, CHK_R, CHK_LO, CHK_HI, CHK_MASK, CHK_SCAL,
+    CHK_EV, CHK_PH, CHK_MAB, CHK_ORDER, CHK_CSTART, CHK_PAIRS, CHK_MCOL, CHK_PLANE, CHK_PUSHER, CHK_MANIFOLD,
+    CHK_STATE_ROW, CHK_ENV, CHK_WARM
+};
+__device__ unsigned int g_check_status[4];
+__device__ float4 g_check_sink[8];
+__device__ __noinline__ void check_fail(uint32_t id, long long i, long long cap) {
+    if (atomicAdd(&g_check_status[0], 1u) == 0u) {
+        g_check_status[1] = id;
+        g_check_status[2] = (unsigned int)i;
+        g_check_status[3] = (unsigned int)cap;
+    }
+}
+// true when 0 <= i < cap; otherwise records the violation
+__device__ __forceinline__ bool check_index(uint32_t id, long long i, long long cap) {
+    if (i >= 0 && i < cap) return true;
+    check_fail(id, i, cap);
+    return false;
+}
+#endif
+
 // An array in the block's dynamic shared memory held as a 32-bit byte offset: one
 // register per array, and accesses compile to shared-memory loads and stores.
 template <class T>
 struct SArr {
     uint32_t off;
+#if PMBS_BOUNDS_CHECK
+    uint32_t cap, id;
+    __device__ __forceinline__ T& operator[](int i) const {
+        if (!check_index(id, i, cap)) return *reinterpret_cast<T*>(g_check_sink);
+        return reinterpret_cast<T*>(pmbs_smem + off)[i];
+    }
+#else
     __device__ __forceinline__ T& operator[](int i) const { return reinterpret_cast<T*>(pmbs_smem + off)[i]; }
-    __device__ __forceinline__ T* ptr() const { return reinterpret_cast<T*>(pmbs_smem + off); }
+#endif
 };
+
+#if PMBS_BOUNDS_CHECK
+#define PMBS_SARR(o, n, tag) {base + (uint32_t)(o), (uint32_t)(n), (uint32_t)(tag)}
+#else
+#define PMBS_SARR(o, n, tag) {base + (uint32_t)(o)}
+#endif
 
 // One warp's region: its byte offset in the block's dynamic shared memory, the launch's
 // layout (a kernel parameter, so field offsets are read from the parameter bank instead
-// of being held in registers) and the warp's global contact scratch.
+// of being held in registers) and the warp's global contact scratch.  Capacities (used by
+// the bounds-checked build only) are those of make_layout.
 struct WarpMem {
     uint32_t base;
     const Layout* L;
     float4* con_g;
-    __device__ __forceinline__ SArr<float4> bv() const { return {base + (uint32_t)L->o_bv}; }    // v, 1/m
-    __device__ __forceinline__ SArr<float4> bw() const { return {base + (uint32_t)L->o_bw}; }    // w, mu
-    __device__ __forceinline__ SArr<float4> bI0() const { return {base + (uint32_t)L->o_bI0}; }  // I^-1 00 01 02 11
-    __device__ __forceinline__ SArr<float4> bI1() const { return {base + (uint32_t)L->o_bI1}; }  // I^-1 12 22
-    __device__ __forceinline__ SArr<float> x() const { return {base + (uint32_t)L->o_x}; }  // SoA, stride NB
-    __device__ __forceinline__ SArr<float> q() const { return {base + (uint32_t)L->o_q}; }  // 4 rows
-    __device__ __forceinline__ SArr<float> h() const { return {base + (uint32_t)L->o_h}; }
-    __device__ __forceinline__ SArr<float> ib() const { return {base + (uint32_t)L->o_ib}; }
-    __device__ __forceinline__ SArr<float> R() const { return {base + (uint32_t)L->o_R}; }  // 9 rows
-    __device__ __forceinline__ SArr<float> lo() const { return {base + (uint32_t)L->o_lo}; }
-    __device__ __forceinline__ SArr<float> hi() const { return {base + (uint32_t)L->o_hi}; }
-    __device__ __forceinline__ SArr<uint32_t> mask() const { return {base + (uint32_t)L->o_mask}; }
-    __device__ __forceinline__ SArr<int> scal() const { return {base + (uint32_t)L->o_scal}; }
+    __device__ __forceinline__ SArr<float4> bv() const { return PMBS_SARR(L->o_bv, L->NB, CHK_BV); }     // v, 1/m
+    __device__ __forceinline__ SArr<float4> bw() const { return PMBS_SARR(L->o_bw, L->NB, CHK_BW); }     // w, mu
+    __device__ __forceinline__ SArr<float4> bI0() const { return PMBS_SARR(L->o_bI0, L->NB, CHK_BI0); }  // I^-1 00 01 02 11
+    __device__ __forceinline__ SArr<float4> bI1() const { return PMBS_SARR(L->o_bI1, L->NB, CHK_BI1); }  // I^-1 12 22
+    __device__ __forceinline__ SArr<float> x() const { return PMBS_SARR(L->o_x, 3 * L->NB, CHK_X); }  // SoA, stride NB
+    __device__ __forceinline__ SArr<float> q() const { return PMBS_SARR(L->o_q, 4 * L->NB, CHK_Q); }  // 4 rows
+    __device__ __forceinline__ SArr<float> h() const { return PMBS_SARR(L->o_h, 3 * L->NB, CHK_H); }
+    __device__ __forceinline__ SArr<float> ib() const { return PMBS_SARR(L->o_ib, 3 * L->NB, CHK_IB); }
+    __device__ __forceinline__ SArr<float> R() const { return PMBS_SARR(L->o_R, 9 * L->NB, CHK_R); }  // 9 rows
+    __device__ __forceinline__ SArr<float> lo() const { return PMBS_SARR(L->o_lo, 3 * L->NB, CHK_LO); }
+    __device__ __forceinline__ SArr<float> hi() const { return PMBS_SARR(L->o_hi, 3 * L->NB, CHK_HI); }
+    __device__ __forceinline__ SArr<uint32_t> mask() const { return PMBS_SARR(L->o_mask, L->NB, CHK_MASK); }
+    __device__ __forceinline__ SArr<int> scal() const { return PMBS_SARR(L->o_scal, 16, CHK_SCAL); }
     // event counters, written by the group's first lane only
-    __device__ __forceinline__ SArr<unsigned long long> ev() const { return {base + (uint32_t)L->o_ev}; }
-    __device__ __forceinline__ SArr<uint16_t> mAB() const { return {base + (uint32_t)L->o_mAB}; }
-    __device__ __forceinline__ SArr<uint16_t> order() const { return {base + (uint32_t)L->o_order}; }
-    __device__ __forceinline__ SArr<uint16_t> cstart() const { return {base + (uint32_t)L->o_cstart}; }
-    __device__ __forceinline__ SArr<uint16_t> pairs() const { return {base + (uint32_t)L->o_pairs}; }
-    __device__ __forceinline__ SArr<uint8_t> mcol() const { return {base + (uint32_t)L->o_mcol}; }
-    __device__ __forceinline__ SArr<uint8_t> plane() const { return {base + (uint32_t)L->o_plane}; }
-    __device__ __forceinline__ SArr<uint8_t> pusher() const { return {base + (uint32_t)L->o_pusher}; }
+    __device__ __forceinline__ SArr<unsigned long long> ev() const { return PMBS_SARR(L->o_ev, kNumEvents, CHK_EV); }
+    // phase cycle counters (kNumPhases), after the event counters
+    __device__ __forceinline__ SArr<unsigned long long> ph() const {
+        return PMBS_SARR(L->o_ev + 8 * kNumEvents, kNumPhases, CHK_PH);
+    }
+    __device__ __forceinline__ SArr<uint16_t> mAB() const { return PMBS_SARR(L->o_mAB, L->Mcap, CHK_MAB); }
+    __device__ __forceinline__ SArr<uint16_t> order() const { return PMBS_SARR(L->o_order, L->Mcap, CHK_ORDER); }
+    __device__ __forceinline__ SArr<uint16_t> cstart() const {
+        return PMBS_SARR(L->o_cstart, kMaxColours + 2, CHK_CSTART);
+    }
+    __device__ __forceinline__ SArr<uint16_t> pairs() const { return PMBS_SARR(L->o_pairs, L->pairS, CHK_PAIRS); }
+    __device__ __forceinline__ SArr<uint8_t> mcol() const { return PMBS_SARR(L->o_mcol, L->Mcap, CHK_MCOL); }
+    __device__ __forceinline__ SArr<uint8_t> plane() const { return PMBS_SARR(L->o_plane, L->NB, CHK_PLANE); }
+    __device__ __forceinline__ SArr<uint8_t> pusher() const { return PMBS_SARR(L->o_pusher, L->NB, CHK_PUSHER); }
     // contacts: shared memory below Ms, global scratch above
     __device__ __forceinline__ float4* con_s() const { return reinterpret_cast<float4*>(pmbs_smem + base + L->o_con); }
     __device__ __forceinline__ int NB() const { return L->NB; }
@@ -174,6 +233,13 @@ struct CRef {
 
 __device__ __forceinline__ CRef cref(const WarpMem& W, int m) {
     CRef r;
+#if PMBS_BOUNDS_CHECK
+    if (!check_index(CHK_MANIFOLD, m, W.Mcap())) {
+        r.p = g_check_sink;  // every field of a bad manifold index lands on the sink
+        r.stride = 0;
+        return r;
+    }
+#endif
     if (m < W.Ms()) {
         r.p = W.con_s() + m;
         r.stride = W.Ms();
@@ -220,6 +286,23 @@ struct Grp {
     }
     __device__ __forceinline__ int bcast(int v, int src) const { return __shfl_sync(kFull, v, src, G); }
     __device__ __forceinline__ float bcast(float v, int src) const { return __shfl_sync(kFull, v, src, G); }
+};
+
+// Phase clock of a group: on a mark, the group's first lane adds the cycles since the
+// previous mark to phase k of its environment (when `rec`).  en = SimConst::timers, a
+// launch-uniform value, so a launch without timers pays one branch per mark.
+struct PhaseClock {
+    long long t = 0;
+    __device__ __forceinline__ void start(bool en) {
+        if (en) t = clock64();
+    }
+    __device__ __forceinline__ void mark(bool en, const WarpMem& W, int k, bool rec) {
+        if (en) {
+            const long long now = clock64();
+            if (rec) W.ph()[k] += (unsigned long long)(now - t);
+            t = now;
+        }
+    }
 };
 
 // Warp-uniform loop bound: the largest per-group bound.
@@ -774,7 +857,7 @@ constexpr int kWarmF4 = 9;
 
 __device__ __forceinline__ float3 key_local(const WarpMem& W, int kb, float3 r) {
     const int NB = W.NB();
-    const float* R = W.R().ptr();
+    const SArr<float> R = W.R();
     return f3(R[kb] * r.x + R[3 * NB + kb] * r.y + R[6 * NB + kb] * r.z,
               R[NB + kb] * r.x + R[4 * NB + kb] * r.y + R[7 * NB + kb] * r.z,
               R[2 * NB + kb] * r.x + R[5 * NB + kb] * r.y + R[8 * NB + kb] * r.z);
@@ -787,6 +870,9 @@ __device__ __forceinline__ float3 key_local(const WarpMem& W, int kb, float3 r) 
 __device__ __forceinline__ void warm_start(const WarpMem& W, const Grp& g, bool on, const SimConst& C,
                                            const float4* cache, int Mold) {
     const int M = on ? W.scal()[3] : 0;
+#if PMBS_BOUNDS_CHECK
+    if (!check_index(CHK_WARM, Mold, W.Mcap() + 1)) Mold = 0;
+#endif
     for (int m = g.gl; m < M; m += g.G) {
         if (W.mcol()[m] == 255) continue;
         const CRef r = cref(W, m);
@@ -875,7 +961,10 @@ __device__ __forceinline__ void warm_start(const WarpMem& W, const Grp& g, bool 
 // the next substep's contacts will be compared in after their own update).  Returns the
 // number of records (manifolds dropped by the colour cap are recorded with no points).
 __device__ __forceinline__ int warm_save(const WarpMem& W, const Grp& g, bool on, float4* cache) {
-    const int M = on ? W.scal()[3] : 0;
+    int M = on ? W.scal()[3] : 0;
+#if PMBS_BOUNDS_CHECK
+    if (!check_index(CHK_WARM, M, W.Mcap() + 1)) M = 0;
+#endif
     for (int m = g.gl; m < M; m += g.G) {
         const CRef r = cref(W, m);
         const float4 h1 = r.f(1), h2 = r.f(2);
@@ -930,7 +1019,7 @@ __device__ __forceinline__ void compute_footprints(const WarpMem& W, int n, cons
         float R[9];
         quat_to_R_exact(W.q()[i], W.q()[NB + i], W.q()[2 * NB + i], W.q()[3 * NB + i], R);
         const Foot f = footprint_exact(W.x()[i], W.x()[NB + i], R, W.h()[i], W.h()[NB + i], W.h()[2 * NB + i]);
-        float* o = W.R().ptr();
+        const SArr<float> o = W.R();
         o[0 * NB + i] = f.cx;
         o[1 * NB + i] = f.cy;
         o[2 * NB + i] = f.ux;
@@ -945,7 +1034,7 @@ __device__ __forceinline__ void compute_footprints(const WarpMem& W, int n, cons
 
 __device__ __forceinline__ Foot load_foot(const WarpMem& W, int i) {
     const int NB = W.NB();
-    const float* o = W.R().ptr();
+    const SArr<float> o = W.R();
     Foot f;
     f.cx = o[i];
     f.cy = o[NB + i];

@@ -22,13 +22,17 @@ NUM_EVENTS = 18
 EVENT_NAMES = ["substeps", "box_steps", "pair_tests", "sat", "face", "edge", "plane",
                "pusher", "points", "manifolds", "pgs_manifolds", "pgs_points",
                "push_evals", "sample_attempts", "clip_verts", "colours", "bb_points", "pgs_bb_points"]
+NUM_PHASES = 8
+PHASE_NAMES = ["push_setup", "broadphase", "narrowphase", "contact_prep", "colouring", "contact_solve",
+               "integrate", "push_end"]
 
 EXPORTED = ["pmbs_default_config", "pmbs_create", "pmbs_create_with_arena", "pmbs_destroy",
             "pmbs_last_error", "pmbs_load_scenes", "pmbs_free_scenes", "pmbs_rollout_pushes",
             "pmbs_rollout_pushes_device", "pmbs_step", "pmbs_query_cost", "pmbs_query_cost_device",
-            "pmbs_query_states", "pmbs_query_events", "pmbs_batch_info", "pmbs_release_batch",
+            "pmbs_query_states", "pmbs_query_events", "pmbs_query_phase_cycles", "pmbs_batch_info", "pmbs_release_batch",
             "pmbs_eval_pairs", "pmbs_eval_grasp", "pmbs_eval_sample", "pmbs_eval_start_blocked",
-            "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_rollout_noalloc",
+            "pmbs_launch_shape", "pmbs_set_launch_shape", "pmbs_fp32_peak", "pmbs_check_status",
+            "pmbs_rollout_noalloc",
             "pmbs_step_graph", "pmbs_autotune", "pmbs_server_create", "pmbs_server_submit",
             "pmbs_server_wait", "pmbs_server_stats", "pmbs_server_cancel", "pmbs_server_destroy",
             "pmbs_render_heightmaps", "pmbs_render_heightmaps_device", "pmbs_query_heightmaps",
@@ -50,7 +54,7 @@ class pmbs_config(C.Structure):
                 ("smem_points", C.c_int),
                 ("smem_manifolds", C.c_int), ("watchdog_ms", C.c_float),
                 ("max_initial_penetration", C.c_float), ("warm_start", C.c_int),
-                ("warm_tolerance", C.c_float), ("cylinders", C.c_int)]
+                ("warm_tolerance", C.c_float), ("cylinders", C.c_int), ("phase_timers", C.c_int)]
 
 
 class PmbsError(RuntimeError):
@@ -59,19 +63,20 @@ class PmbsError(RuntimeError):
         self.status = status
 
 
-_lib = None
+_libs = {}
 
 
-def load(build_if_missing: bool = True):
-    """Load libpmbs.so (building it if the sources are newer and nvcc is present)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if build_if_missing and _build.stale() and os.path.exists(_build.NVCC):
-        _build.build()
-    if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libpmbs.so not built at {LIB_PATH}; run paper_2207_06649_b300/build.py")
-    L = C.CDLL(LIB_PATH)
+def load(build_if_missing: bool = True, checked: bool = False):
+    """Load libpmbs.so, or with checked=True its bounds-checked twin libpmbs_checked.so
+    (building it if the sources are newer and nvcc is present)."""
+    if checked in _libs:
+        return _libs[checked]
+    path = _build.LIB_CHECKED if checked else LIB_PATH
+    if build_if_missing and _build.stale(checked) and os.path.exists(_build.NVCC):
+        _build.build(checked=checked)
+    if not os.path.exists(path):
+        raise ImportError(f"{os.path.basename(path)} not built at {path}; run paper_2207_06649_b300/build.py")
+    L = C.CDLL(path)
     vp, i32, i64, P = C.c_void_p, C.c_int, C.c_int64, C.POINTER
     sig = {
         "pmbs_default_config": ([P(pmbs_config)], None),
@@ -90,6 +95,7 @@ def load(build_if_missing: bool = True):
         "pmbs_query_cost_device": ([vp, i64, vp, vp, vp], i32),
         "pmbs_query_states": ([vp, i64, vp, vp], i32),
         "pmbs_query_events": ([vp, i64, vp], i32),
+        "pmbs_query_phase_cycles": ([vp, i64, vp], i32),
         "pmbs_batch_info": ([vp, i64, vp, vp], i32),
         "pmbs_release_batch": ([vp, i64], i32),
         "pmbs_eval_pairs": ([vp, i32] + [vp] * 10, i32),
@@ -99,6 +105,7 @@ def load(build_if_missing: bool = True):
         "pmbs_launch_shape": ([vp, i32, vp, vp, vp, vp, vp], i32),
         "pmbs_set_launch_shape": ([vp, i32, i32, i32, i32], i32),
         "pmbs_fp32_peak": ([vp, P(C.c_double)], i32),
+        "pmbs_check_status": ([vp, vp, i32], i32),
         "pmbs_rollout_noalloc": ([P(pmbs_config), vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp], i32),
         "pmbs_server_create": ([vp, i32, i32, P(vp)], i32),
         "pmbs_server_submit": ([vp, i32, vp, vp, i32, vp, P(C.c_int64)], i32),
@@ -115,7 +122,7 @@ def load(build_if_missing: bool = True):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = res
-    _lib = L
+    _libs[checked] = L
     return L
 
 
@@ -150,8 +157,11 @@ def current_stream_handle():
 class Engine:
     """A pmbs context with numpy-array methods (one C call each)."""
 
-    def __init__(self, cfg: pmbs_config | None = None, stream=None, arena=None, **overrides):
-        self.lib = load()
+    def __init__(self, cfg: pmbs_config | None = None, stream=None, arena=None, checked: bool = False,
+                 **overrides):
+        """checked=True runs every call on the bounds-checked library (same results,
+        slower; read its status word with check_status)."""
+        self.lib = load(checked=checked)
         self.cfg = cfg or default_config(**overrides)
         self.ctx = C.c_void_p()
         if arena is not None:
@@ -279,6 +289,20 @@ class Engine:
         self._check(self.lib.pmbs_query_events(self.ctx, batch, _p(ev)), "pmbs_query_events")
         return ev
 
+    def check_status(self, reset=True):
+        """Bounds-checked library only: (violations, first array id, index, capacity)."""
+        out = np.zeros(4, np.uint32)
+        self._check(self.lib.pmbs_check_status(self.ctx, _p(out), 1 if reset else 0), "pmbs_check_status")
+        return tuple(int(v) for v in out)
+
+    def query_phase_cycles(self, batch):
+        """[n_envs, NUM_PHASES] SM clock cycles per phase (PHASE_NAMES order); zeros unless
+        the engine was created with phase_timers=1."""
+        ne, _ = self.batch_info(batch)
+        ph = np.zeros((ne, NUM_PHASES), np.uint64)
+        self._check(self.lib.pmbs_query_phase_cycles(self.ctx, batch, _p(ph)), "pmbs_query_phase_cycles")
+        return ph
+
     def release_batch(self, batch):
         self._check(self.lib.pmbs_release_batch(self.ctx, batch), "pmbs_release_batch")
 
@@ -399,6 +423,8 @@ class Engine:
         st, steps = self.query_states(b)
         out["state"], out["steps"] = st, steps
         out["events"] = self.query_events(b)
+        if self.cfg.phase_timers:
+            out["phase_cycles"] = self.query_phase_cycles(b)
         self.release_batch(b)
         return out
 

@@ -16,9 +16,11 @@ def _declared():
     return sorted(set(re.findall(r"\b(pmbs_[a-z0-9_]+)\s*\(", src)))
 
 
-def test_library_exports_every_declared_symbol():
+@pytest.mark.parametrize("checked", [False, True])
+def test_library_exports_every_declared_symbol(checked):
+    """Both the release library and its bounds-checked twin export every call."""
     from paper_2207_06649_b300 import pmbs
-    lib = pmbs.load()
+    lib = pmbs.load(checked=checked)
     names = _declared()
     assert len(names) >= 20
     for n in names:

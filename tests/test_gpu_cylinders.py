@@ -138,7 +138,7 @@ def test_cylinder_target_heightmap_grasp_bit_exact(eng, orc, depth):
 
 # ------------------------------------------------------------------ trajectories
 def _angle_err(qa, qb):
-    return 2 * np.arccos(np.abs(np.sum(qa * qb, axis=-1)).clip(0, 1))
+    return G.rotation_angle_between(qa, qb)
 
 
 def _run(eng, sc, pushes, count):

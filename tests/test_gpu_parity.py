@@ -156,8 +156,7 @@ def test_start_checks_bit_exact(eng, orc):
 
 # ------------------------------------------------------------------ trajectories
 def _angle_err(qa, qb):
-    d = np.abs(np.sum(qa * qb, axis=-1)).clip(0, 1)
-    return 2 * np.arccos(d)
+    return G.rotation_angle_between(qa, qb)
 
 
 def _run_gpu_substeps(eng, sc, pushes, count, depth=1, seeds=None):
