@@ -95,10 +95,10 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'lanes,warps_per_block,smem_manifolds' instead of autotuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="served-load run length (0 = skip)")
-    ap.add_argument("--plan-seeds", type=int, default=1, help="planning episodes per method (0 = skip)")
+    ap.add_argument("--plan-seeds", type=int, default=10, help="planning scenes per method (0 = skip)")
     ap.add_argument("--arena-gb", type=float, default=8.0, help="device arena of the timed engine")
     ap.add_argument("--plan-tmax", type=float, default=2.0, help="PMBS planning budget per action (s)")
-    ap.add_argument("--serial-budgets", default="2,8", help="serial MCTS budgets per action (s)")
+    ap.add_argument("--serial-budgets", default="1,4", help="serial MCTS budgets per action (s), ascending")
     ap.add_argument("--plan-c", default="1.4", help="UCB exploration constants of the planning run")
     ap.add_argument("--planning-study", action="store_true",
                     help="only the planning episodes (--plan-seeds, --plan-c, budgets); one JSON line")
@@ -255,23 +255,50 @@ def serving_run(pmbs, sg, dev_index, seconds, rate, seed=5, planners=64, pool=No
             "peak_arena_gb": st["peak_bytes"] / 2 ** 30}
 
 
+def hard_planning_scenes(pmbs, sg, eng, count, max_seed=200):
+    """Planning scenes whose target no single push frees: the target starts not graspable
+    and none of the root's expansion candidates (16 contour points around every box
+    within 0.1 m of the target) makes it graspable after one push (one batched depth-1
+    rollout on the engine).  Returns [(seed, scene, candidates)], seeds in order."""
+    from paper_2207_06649_b300 import planner as P
+    out, rejected = [], {"graspable_at_start": 0, "one_push": 0}
+    for sd in range(max_seed):
+        if len(out) >= count:
+            break
+        sc = sg.config_planning(sd)
+        st = sg.state13(sc)
+        be = P.GpuBackend(eng, sc.half, sc.mass, sc.mu)
+        if be.graspable(st, sc.half, 0):
+            rejected["graspable_at_start"] += 1
+            continue
+        cand = P.contour_candidates(st, sc.half, 0)
+        h = be.load_state(st, sc.half, 0)
+        r = be.rollout(np.full(len(cand), h, np.int32), cand, 1, np.zeros(len(cand), np.uint64))
+        be.release([h] + list(r["child_handles"]))
+        if np.any(r["cost"] == 1):
+            rejected["one_push"] += 1
+            continue
+        out.append((sd, sc, len(cand)))
+    return out, rejected
+
+
 def planning_run(pmbs, sg, local, seeds, tmax, serial_budgets, n_envs=512, c=1.4, max_actions=16):
-    """Full planning episodes (buried target in 30-box clutter): PMBS with n_envs rollouts
-    per iteration vs serial MCTS (one rollout per iteration) on the same engine, each
-    given a planning budget per action; reports actions to retrieval (pushes + grasp),
-    completion within max_actions and planning seconds per action."""
+    """Full planning episodes on buried-target 30-box scenes that no single push solves:
+    PMBS with n_envs rollouts per iteration vs serial MCTS (one rollout per iteration) on
+    the same engine, each given a planning budget per action; reports actions to
+    retrieval (pushes + grasp) with their distribution, completion within max_actions,
+    planning seconds per action, and the serial budget at which serial MCTS first
+    matches PMBS's mean actions (equal solution cost)."""
     from paper_2207_06649_b300 import planner as P
     eng = pmbs.Engine(device=local, mem_budget_bytes=4 << 30)
+    scenes, rejected = hard_planning_scenes(pmbs, sg, eng, seeds)
     methods = [("pmbs", n_envs, tmax)] + [("serial", 1, b) for b in serial_budgets]
     res = {}
     for name, ne, budget in methods:
-        acts, done, plan = [], 0, []
-        for sd in range(seeds):
-            sc = sg.config_planning(sd)
+        acts, done, plan, iters = [], 0, [], []
+        for sd, sc, _ in scenes:
             be = P.GpuBackend(eng, sc.half, sc.mass, sc.mu)
             st = sg.state13(sc)
-            if be.graspable(st, sc.half, 0):
-                continue
             ep = P.run_episode(be, st, sc.half, 0,
                                lambda: P.Planner(be, sc.half, 0, n_envs=ne, c=c, t_max=budget, seed=sd),
                                max_actions=max_actions)
@@ -280,11 +307,24 @@ def planning_run(pmbs, sg, local, seeds, tmax, serial_budgets, n_envs=512, c=1.4
             plan.extend(ep["plan_s"])
         key = f"{name}_{budget:g}s" if name == "serial" else f"pmbs_{ne}envs_{budget:g}s"
         res[key] = {"episodes": len(acts), "actions_mean": float(np.mean(acts)) if acts else None,
+                    "actions": [int(a) for a in acts],
                     "completion": done / max(1, len(acts)),
                     "plan_s_per_action": float(np.mean(plan)) if plan else None,
                     "plan_s_total_mean": float(np.sum(plan) / max(1, len(acts)))}
     eng.close()
-    return res
+    pm = res[f"pmbs_{n_envs}envs_{tmax:g}s"]
+    equal = None
+    for b in serial_budgets:
+        r = res[f"serial_{b:g}s"]
+        if r["actions_mean"] is not None and pm["actions_mean"] is not None and \
+                r["actions_mean"] <= pm["actions_mean"] + 1e-9:
+            equal = {"serial_budget_s": b, "serial_plan_s_total_mean": r["plan_s_total_mean"],
+                     "pmbs_plan_s_total_mean": pm["plan_s_total_mean"],
+                     "speedup": r["plan_s_total_mean"] / max(pm["plan_s_total_mean"], 1e-9)}
+            break
+    return {"scenes": [sd for sd, _, _ in scenes], "rejected": rejected,
+            "root_candidates": [k for _, _, k in scenes], "by_method": res,
+            "equal_cost": equal if equal else "no serial budget reached PMBS's mean actions"}
 
 
 def run_ours(args):
@@ -483,19 +523,22 @@ def run_ours(args):
     if args.serve_seconds > 0 and ws == 1:
         pool_sc, pool_pu, _ = sg.config_uneven(seed=args.seed + 7, n_envs=512)
         seng = pmbs.Engine(device=local, mem_budget_bytes=16 << 30, max_envs=4096)
-        full = serving_run(pmbs, sg, local, args.serve_seconds, 200.0, pool=(pool_sc, pool_pu), eng=seng)
+        sweep = [serving_run(pmbs, sg, local, args.serve_seconds, rate, seed=5 + i, pool=(pool_sc, pool_pu), eng=seng)
+                 for i, rate in enumerate((50.0, 100.0, 150.0, 200.0))]
+        full = sweep[-1]
         # sustainable rate: what the device completed under overload, with 20 % headroom
         rate = max(1.0, 0.8 * (full["achieved_batches_per_s"] or 1.0))
-        sus = serving_run(pmbs, sg, local, args.serve_seconds * 2, rate, seed=6, pool=(pool_sc, pool_pu), eng=seng)
+        sus = serving_run(pmbs, sg, local, args.serve_seconds * 2, rate, seed=9, pool=(pool_sc, pool_pu), eng=seng)
         seng.close()
         serving = {"config": "64 planners, batches log-uniform 32..2048 envs, Poisson arrivals, 5-40 boxes, "
                              "depth 3, 16 GB arena, continuous batching on 8 streams",
-                   "at_200_per_s": full, "sustainable": sus}
+                   "offered_load_sweep": sweep, "at_200_per_s": full, "sustainable": sus}
     planning = None
     if args.plan_seeds > 0 and ws == 1:
         budgets = [float(x) for x in args.serial_budgets.split(",") if x]
-        planning = {"config": "30-box clutter, target buried on 16 rays within 0.03 m, UCB c=1.4, gamma 0.8, "
-                              "d_T 7 + d_s 3, expansion candidates 16 contour points per box within 0.1 m",
+        planning = {"config": "30-box clutter, target buried on 16 rays within 0.03 m and freed by no single "
+                              "push, UCB c=1.4, gamma 0.8, d_T 7 + d_s 3, expansion candidates 16 contour points "
+                              "per box within 0.1 m, completion within 16 actions",
                     "seeds": args.plan_seeds,
                     "results": planning_run(pmbs, sg, local, args.plan_seeds, args.plan_tmax, budgets)}
     peak_fma = eng.fp32_peak()
