@@ -20,6 +20,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pmbs_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_FLOPS = os.path.join(_HERE, "liboracle_flops.so")
+PHASES = ["per_body", "narrowphase", "contact_prep", "contact_solve", "other"]
 
 EVENT_NAMES = ["substeps", "box_steps", "pair_tests", "sat", "face", "edge", "plane",
                "pusher", "points", "manifolds", "pgs_manifolds", "pgs_points",
@@ -52,7 +54,38 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_flops(force: bool = False) -> str:
+    """Compile the flop-counting build of the oracle (-DORACLE_COUNT_FLOPS)."""
+    if force or not os.path.exists(_LIB_FLOPS) or os.path.getmtime(_LIB_FLOPS) < os.path.getmtime(_SRC):
+        tmp = _LIB_FLOPS + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared",
+                               "-pthread", "-DORACLE_COUNT_FLOPS", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_FLOPS)
+    return _LIB_FLOPS
+
+
 _lib = None
+_lib_flops = None
+
+
+def count_flops(state13, half, mass, mu, push, count, prm=None):
+    """Run `count` substeps of one environment under `push` in the flop-counting build.
+    Returns (flops by phase as a dict over PHASES, event counters [NEV])."""
+    global _lib_flops
+    if _lib_flops is None:
+        L = C.CDLL(build_flops())
+        L.oracle_count_flops.argtypes = [C.POINTER(Params), C.c_int] + [C.c_void_p] * 5 + \
+            [C.c_int, C.c_void_p, C.c_void_p]
+        _lib_flops = L
+    prm = prm or params()
+    st = np.ascontiguousarray(state13, np.float64)
+    h, m, u = (np.ascontiguousarray(a, np.float32) for a in (half, mass, mu))
+    p = np.ascontiguousarray(push, np.float64)
+    f = np.zeros(5, np.uint64)
+    ev = np.zeros(len(EVENT_NAMES), np.uint64)
+    _lib_flops.oracle_count_flops(C.byref(prm), st.shape[0], _ptr(st), _ptr(h), _ptr(m), _ptr(u), _ptr(p), int(count),
+                                  _ptr(f), _ptr(ev))
+    return dict(zip(PHASES, f.astype(np.float64))), ev
 
 
 def lib():

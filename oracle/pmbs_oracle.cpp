@@ -28,6 +28,12 @@
 // rounded once, compiled with -ffp-contract=off) so that decisions on identical FP32
 // state snapshots can be compared bit-for-bit with the GPU.
 //
+// Flop counter: compiled with -DORACLE_COUNT_FLOPS (a separate library,
+// liboracle_flops.so), the double engine's scalar type `real` becomes a counting type:
+// every add, subtract, multiply, divide and square root counts 1 into the phase being
+// run (compares, abs, min and max count 0; -ffp-contract=off keeps a multiply-add as 2).
+// The default build has `real` = double, with the same arithmetic in the same order.
+//
 // Parity status: every function below is pinned by the CPU tests (closed forms,
 // invariants, brute force), except whole multi-contact clutter trajectories, whose
 // parity is unpinned (chaotic; FP32 and FP64 diverge).
@@ -61,6 +67,9 @@ typedef struct {
 }
 
 namespace {
+
+using std::fabs;
+using std::sqrt;
 
 enum { PLANE = -1, PUSHER = -2 };
 enum {
@@ -105,7 +114,7 @@ struct Gon {
     T vc[8], vs[8], fc[8], fs[8];
     T apo, half_edge;  // cos(pi/16), sin(pi/16)
     Gon() {
-        const double C1 = std::cos(M_PI / 8), S1 = std::sin(M_PI / 8), H = std::sqrt(0.5);
+        const double C1 = std::cos(M_PI / 8), S1 = std::sin(M_PI / 8), H = sqrt(0.5);
         const double D1 = std::cos(M_PI / 16), E1 = std::sin(M_PI / 16);
         const double D3 = std::cos(3 * M_PI / 16), E3 = std::sin(3 * M_PI / 16);
         const double vcd[8] = {1, C1, H, S1, 0, -S1, -H, -C1}, vsd[8] = {0, S1, H, C1, 1, C1, H, S1};
@@ -130,7 +139,7 @@ T gon_support(T p0, T p1) {
     const Gon<T>& G = gon<T>();
     T m = T(0);
     for (int k = 0; k < 8; k++) {
-        const T v = std::fabs(G.vc[k] * p0 + G.vs[k] * p1);
+        const T v = fabs(G.vc[k] * p0 + G.vs[k] * p1);
         if (v > m) m = v;
     }
     return m;
@@ -140,10 +149,10 @@ T gon_support(T p0, T p1) {
 // the contact margin on every side.  A cylinder uses its bounding box (r, r, h).
 template <typename T>
 void box_aabb(const T* c, const T* R, const T* h, T m, T* lo, T* hi) {
-    const T h1 = std::fabs(h[1]);
+    const T h1 = fabs(h[1]);
     for (int k = 0; k < 3; k++) {
-        const T e = (std::fabs(R[3 * k]) * h[0] + std::fabs(R[3 * k + 1]) * h1) +
-                    std::fabs(R[3 * k + 2]) * h[2];
+        const T e = (fabs(R[3 * k]) * h[0] + fabs(R[3 * k + 1]) * h1) +
+                    fabs(R[3 * k + 2]) * h[2];
         lo[k] = (c[k] - e) - m;
         hi[k] = (c[k] + e) + m;
     }
@@ -211,22 +220,22 @@ Foot<T> footprint(const T* x, const T* q, const T* h) {
     T ex = R[0], ey = R[3];
     T l2 = ex * ex + ey * ey;
     if (l2 < T(1e-12)) { ex = R[1]; ey = R[4]; l2 = ex * ex + ey * ey; }
-    const T len = std::sqrt(l2);
+    const T len = sqrt(l2);
     Foot<T> f;
     f.cx = x[0]; f.cy = x[1];
     f.ux = ex / len; f.uy = ey / len;
     f.vx = -f.uy; f.vy = f.ux;
     if (is_cyl(h)) {
         f.su = gon_support(R[0] * f.ux + R[3] * f.uy, R[1] * f.ux + R[4] * f.uy) * h[0] +
-               std::fabs(R[2] * f.ux + R[5] * f.uy) * h[2];
+               fabs(R[2] * f.ux + R[5] * f.uy) * h[2];
         f.sv = gon_support(R[0] * f.vx + R[3] * f.vy, R[1] * f.vx + R[4] * f.vy) * h[0] +
-               std::fabs(R[2] * f.vx + R[5] * f.vy) * h[2];
+               fabs(R[2] * f.vx + R[5] * f.vy) * h[2];
         return f;
     }
-    f.su = (std::fabs(R[0] * f.ux + R[3] * f.uy) * h[0] + std::fabs(R[1] * f.ux + R[4] * f.uy) * h[1]) +
-           std::fabs(R[2] * f.ux + R[5] * f.uy) * h[2];
-    f.sv = (std::fabs(R[0] * f.vx + R[3] * f.vy) * h[0] + std::fabs(R[1] * f.vx + R[4] * f.vy) * h[1]) +
-           std::fabs(R[2] * f.vx + R[5] * f.vy) * h[2];
+    f.su = (fabs(R[0] * f.ux + R[3] * f.uy) * h[0] + fabs(R[1] * f.ux + R[4] * f.uy) * h[1]) +
+           fabs(R[2] * f.ux + R[5] * f.uy) * h[2];
+    f.sv = (fabs(R[0] * f.vx + R[3] * f.vy) * h[0] + fabs(R[1] * f.vx + R[4] * f.vy) * h[1]) +
+           fabs(R[2] * f.vx + R[5] * f.vy) * h[2];
     return f;
 }
 
@@ -236,14 +245,14 @@ Foot<T> footprint(const T* x, const T* q, const T* h) {
 template <typename T>
 bool finger_overlaps(const Foot<T>& o, T fcx, T fcy, T ax, T ay, T bx, T by, T hl, T hw) {
     const T dx = o.cx - fcx, dy = o.cy - fcy;
-    T rO = std::fabs(o.ux * ax + o.uy * ay) * o.su + std::fabs(o.vx * ax + o.vy * ay) * o.sv;
-    if (std::fabs(dx * ax + dy * ay) >= hl + rO) return false;
-    rO = std::fabs(o.ux * bx + o.uy * by) * o.su + std::fabs(o.vx * bx + o.vy * by) * o.sv;
-    if (std::fabs(dx * bx + dy * by) >= hw + rO) return false;
-    T rF = std::fabs(ax * o.ux + ay * o.uy) * hl + std::fabs(bx * o.ux + by * o.uy) * hw;
-    if (std::fabs(dx * o.ux + dy * o.uy) >= rF + o.su) return false;
-    rF = std::fabs(ax * o.vx + ay * o.vy) * hl + std::fabs(bx * o.vx + by * o.vy) * hw;
-    if (std::fabs(dx * o.vx + dy * o.vy) >= rF + o.sv) return false;
+    T rO = fabs(o.ux * ax + o.uy * ay) * o.su + fabs(o.vx * ax + o.vy * ay) * o.sv;
+    if (fabs(dx * ax + dy * ay) >= hl + rO) return false;
+    rO = fabs(o.ux * bx + o.uy * by) * o.su + fabs(o.vx * bx + o.vy * by) * o.sv;
+    if (fabs(dx * bx + dy * by) >= hw + rO) return false;
+    T rF = fabs(ax * o.ux + ay * o.uy) * hl + fabs(bx * o.ux + by * o.uy) * hw;
+    if (fabs(dx * o.ux + dy * o.uy) >= rF + o.su) return false;
+    rF = fabs(ax * o.vx + ay * o.vy) * hl + fabs(bx * o.vx + by * o.vy) * hw;
+    if (fabs(dx * o.vx + dy * o.vy) >= rF + o.sv) return false;
     return true;
 }
 
@@ -262,7 +271,7 @@ bool graspable(int n, const T* x, const T* q, const T* h, int t, const T* ca, co
     for (int k = 0; k < K; k++) {
         const T ax = ca[k], ay = sa[k];
         const T bx = -ay, by = ax;
-        const T wa = std::fabs(ft.ux * ax + ft.uy * ay) * ft.su + std::fabs(ft.vx * ax + ft.vy * ay) * ft.sv;
+        const T wa = fabs(ft.ux * ax + ft.uy * ay) * ft.su + fabs(ft.vx * ax + ft.vy * ay) * ft.sv;
         if (!((wa + c) * T(2) <= W)) continue;
         const T off = ((wa + halfW) + f) * T(0.5);
         const T hl = ((halfW + f) - wa) * T(0.5);
@@ -286,8 +295,8 @@ template <typename T>
 bool start_blocked(const std::vector<Foot<T>>& F, T px, T py, T r) {
     for (const Foot<T>& o : F) {
         const T ex = px - o.cx, ey = py - o.cy;
-        T pu = std::fabs(ex * o.ux + ey * o.uy) - o.su;
-        T pv = std::fabs(ex * o.vx + ey * o.vy) - o.sv;
+        T pu = fabs(ex * o.ux + ey * o.uy) - o.su;
+        T pv = fabs(ex * o.vx + ey * o.vy) - o.sv;
         pu = pu > T(0) ? pu : T(0);
         pv = pv > T(0) ? pv : T(0);
         if (pu * pu + pv * pv < r * r) return true;
@@ -347,7 +356,7 @@ int sample_push(int n, const T* x, const T* q, const T* h, uint64_t seed, int k,
         const T px = (fj.cx + lu * fj.ux) + lv * fj.vx;
         const T py = (fj.cy + lu * fj.uy) + lv * fj.vy;
         const T dx = fj.cx - px, dy = fj.cy - py;
-        const T len = std::sqrt(dx * dx + dy * dy);
+        const T len = sqrt(dx * dx + dy * dy);
         const T dirx = dx / len, diry = dy / len;
         if (start_blocked(F, px, py, r)) continue;
         out[0] = px; out[1] = py;
@@ -415,7 +424,7 @@ void heightmap(int n, const T* x, const T* q, const T* h, int W, int H, T x0, T 
                     const T a = std::fma(S[0], dx, S[1] * dy);
                     const T bk = S[2];
                     if (bk == T(0)) {
-                        if (!(std::fabs(a) <= S[3])) hit = false;
+                        if (!(fabs(a) <= S[3])) hit = false;
                         continue;
                     }
                     const T r = S[4];
@@ -450,14 +459,14 @@ bool graspable_hm(const T* map, int cells, T x0, T cellw, int n, const T* x, con
     T R[9];
     quat_to_R(q + 4 * t, R);
     const T* ht = h + 3 * t;
-    const T ez = is_cyl(ht) ? gon_support(R[6], R[7]) * ht[0] + std::fabs(R[8]) * ht[2]
-                            : (std::fabs(R[6]) * ht[0] + std::fabs(R[7]) * ht[1]) + std::fabs(R[8]) * ht[2];
+    const T ez = is_cyl(ht) ? gon_support(R[6], R[7]) * ht[0] + fabs(R[8]) * ht[2]
+                            : (fabs(R[6]) * ht[0] + fabs(R[7]) * ht[1]) + fabs(R[8]) * ht[2];
     const T z_tip = (x[3 * t + 2] + ez) - depth;
     const T halfW = W * T(0.5), hfw = fw * T(0.5);
     for (int k = 0; k < K; k++) {
         const T ax = ca[k], ay = sa[k];
         const T bx = -ay, by = ax;
-        const T wa = std::fabs(ft.ux * ax + ft.uy * ay) * ft.su + std::fabs(ft.vx * ax + ft.vy * ay) * ft.sv;
+        const T wa = fabs(ft.ux * ax + ft.uy * ay) * ft.su + fabs(ft.vx * ax + ft.vy * ay) * ft.sv;
         if (!((wa + c) * T(2) <= W)) continue;
         const T off = ((wa + halfW) + f) * T(0.5);
         const T hl = ((halfW + f) - wa) * T(0.5);
@@ -465,7 +474,7 @@ bool graspable_hm(const T* map, int cells, T x0, T cellw, int n, const T* x, con
         for (int s = 1; s >= -1 && clear; s -= 2) {
             const T sax = T(s) * ax, say = T(s) * ay;
             const T fcx = ft.cx + sax * off, fcy = ft.cy + say * off;
-            const T rx = std::fabs(sax) * hl + std::fabs(bx) * hfw, ry = std::fabs(say) * hl + std::fabs(by) * hfw;
+            const T rx = fabs(sax) * hl + fabs(bx) * hfw, ry = fabs(say) * hl + fabs(by) * hfw;
             const int i0 = std::max(0, (int)std::floor((fcx - rx - x0) / cellw) - 1);
             const int i1 = std::min(cells - 1, (int)std::floor((fcx + rx - x0) / cellw) + 1);
             const int j0 = std::max(0, (int)std::floor((fcy - ry - x0) / cellw) - 1);
@@ -475,7 +484,7 @@ bool graspable_hm(const T* map, int cells, T x0, T cellw, int n, const T* x, con
                     const T px = (x0 + ((T)i + T(0.5)) * cellw) - fcx;
                     const T py = (x0 + ((T)j + T(0.5)) * cellw) - fcy;
                     const T pa = px * sax + py * say, pb = px * bx + py * by;
-                    if (pa > -hl && pa <= hl && std::fabs(pb) <= hfw && map[(size_t)j * cells + i] > z_tip) {
+                    if (pa > -hl && pa <= hl && fabs(pb) <= hfw && map[(size_t)j * cells + i] > z_tip) {
                         clear = false;
                         break;
                     }
@@ -486,46 +495,85 @@ bool graspable_hm(const T* map, int cells, T x0, T cellw, int n, const T* x, con
     return false;
 }
 
+
+#ifdef ORACLE_COUNT_FLOPS
+// Flop-counting build: every add, subtract, multiply, divide and square root of the
+// double engine counts 1 into the current phase (compares, abs, min and max count 0).
+thread_local uint64_t g_flops[8];
+thread_local int g_phase = 0;
+struct real {
+    double v;
+    real() = default;
+    constexpr real(double x) : v(x) {}
+    explicit operator double() const { return v; }
+};
+inline real operator+(real a, real b) { g_flops[g_phase]++; return a.v + b.v; }
+inline real operator-(real a, real b) { g_flops[g_phase]++; return a.v - b.v; }
+inline real operator*(real a, real b) { g_flops[g_phase]++; return a.v * b.v; }
+inline real operator/(real a, real b) { g_flops[g_phase]++; return a.v / b.v; }
+inline real operator-(real a) { return -a.v; }
+inline real& operator+=(real& a, real b) { a = a + b; return a; }
+inline real& operator-=(real& a, real b) { a = a - b; return a; }
+inline real& operator*=(real& a, real b) { a = a * b; return a; }
+inline real& operator/=(real& a, real b) { a = a / b; return a; }
+inline bool operator<(real a, real b) { return a.v < b.v; }
+inline bool operator>(real a, real b) { return a.v > b.v; }
+inline bool operator<=(real a, real b) { return a.v <= b.v; }
+inline bool operator>=(real a, real b) { return a.v >= b.v; }
+inline bool operator==(real a, real b) { return a.v == b.v; }
+inline bool operator!=(real a, real b) { return a.v != b.v; }
+inline real sqrt(real a) { g_flops[g_phase]++; return std::sqrt(a.v); }
+inline real fabs(real a) { return std::fabs(a.v); }
+inline double as_double(real a) { return a.v; }
+// phases: 0 per body (gravity, frames, AABB, integration), 1 narrowphase, 2 contact
+// preparation, 3 contact solve, 4 colouring and the rest
+inline void set_phase(int k) { g_phase = k; }
+#else
+typedef double real;
+inline double as_double(double a) { return a; }
+inline void set_phase(int) {}
+#endif
+
 // ----------------------------------------------------------------------------------
 // Double-precision engine
 // ----------------------------------------------------------------------------------
-struct V3 { double x, y, z; };
+struct V3 { real x, y, z; };
 inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-inline V3 operator*(V3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+inline V3 operator*(V3 a, real s) { return {a.x * s, a.y * s, a.z * s}; }
 inline V3 operator-(V3 a) { return {-a.x, -a.y, -a.z}; }
-inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline real dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 inline V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
-inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+inline real norm(V3 a) { return sqrt(dot(a, a)); }
 
 struct Body {
     V3 x, v, w;
-    double q[4];
-    double h[3], m, invm, mu, invIb[3];  // h = (r, r, half height) for a cylinder
+    real q[4];
+    real h[3], m, invm, mu, invIb[3];  // h = (r, r, half height) for a cylinder
     bool cyl;
-    double R[9], invIw[6];   // refreshed every substep
+    real R[9], invIw[6];   // refreshed every substep
 };
 inline V3 axis(const Body& b, int k) { return {b.R[k], b.R[3 + k], b.R[6 + k]}; }
-inline V3 rot(const double* R, V3 l) {
+inline V3 rot(const real* R, V3 l) {
     return {R[0] * l.x + R[1] * l.y + R[2] * l.z, R[3] * l.x + R[4] * l.y + R[5] * l.z,
             R[6] * l.x + R[7] * l.y + R[8] * l.z};
 }
 // symmetric 3x3 stored as (00, 01, 02, 11, 12, 22)
-inline V3 sym_mul(const double* I, V3 v) {
+inline V3 sym_mul(const real* I, V3 v) {
     return {I[0] * v.x + I[1] * v.y + I[2] * v.z, I[1] * v.x + I[3] * v.y + I[4] * v.z,
             I[2] * v.x + I[4] * v.y + I[5] * v.z};
 }
 
 struct Contact {
     V3 p, rA, rB;
-    double d;
-    double invKn, invKt1, invKt2, bias;
-    double ln, lt1, lt2;
+    real d;
+    real invKn, invKt1, invKt2, bias;
+    real ln, lt1, lt2;
 };
 struct Manifold {
     int A, B;  // A < B for box pairs; PLANE as A; PUSHER as B
     V3 n, t1, t2;
-    double mu;
+    real mu;
     int np;
     Contact c[4];
     int colour;
@@ -533,14 +581,14 @@ struct Manifold {
 
 struct PushState {
     bool active = false;
-    double sx = 0, sy = 0, dx = 0, dy = 0;
+    real sx = 0, sy = 0, dx = 0, dy = 0;
     int moving = 0;
 };
 
 // A contact point carried to the next substep (warm start): its offset in the frame of
 // the manifold's key body (A when dynamic, else B), its normal impulse and its friction
 // impulse as a world vector (the tangent basis is rebuilt every substep).
-struct WarmPoint { V3 loc; double ln; V3 Pt; };
+struct WarmPoint { V3 loc; real ln; V3 Pt; };
 struct WarmManifold { int A, B, np; WarmPoint p[4]; };
 
 struct Env {
@@ -553,21 +601,21 @@ struct Env {
     uint64_t ev[NEV] = {0};
 };
 
-void load_env(Env& E, int n, const double* s13, const float* half, const float* mass, const float* mu) {
+void load_env(Env& E, int n, const real* s13, const float* half, const float* mass, const float* mu) {
     E.b.resize(n);
     for (int i = 0; i < n; i++) {
         Body& b = E.b[i];
-        const double* s = s13 + 13 * i;
+        const real* s = s13 + 13 * i;
         b.x = {s[0], s[1], s[2]};
         for (int k = 0; k < 4; k++) b.q[k] = s[3 + k];
         b.v = {s[7], s[8], s[9]};
         b.w = {s[10], s[11], s[12]};
         b.cyl = half[3 * i + 1] < 0.f;
-        for (int k = 0; k < 3; k++) b.h[k] = std::fabs((double)half[3 * i + k]);
+        for (int k = 0; k < 3; k++) b.h[k] = fabs((real)half[3 * i + k]);
         b.m = mass[i];
         b.invm = 1.0 / b.m;
         b.mu = mu[i];
-        const double hx2 = b.h[0] * b.h[0], hy2 = b.h[1] * b.h[1], hz2 = b.h[2] * b.h[2];
+        const real hx2 = b.h[0] * b.h[0], hy2 = b.h[1] * b.h[1], hz2 = b.h[2] * b.h[2];
         if (b.cyl) {
             // solid cylinder of radius r and height 2h: m (3 r^2 + 4 h^2) / 12 about the
             // two diameters, m r^2 / 2 about its axis
@@ -582,10 +630,10 @@ void load_env(Env& E, int n, const double* s13, const float* half, const float* 
     }
 }
 
-void store_env(const Env& E, double* s13) {
+void store_env(const Env& E, real* s13) {
     for (size_t i = 0; i < E.b.size(); i++) {
         const Body& b = E.b[i];
-        double* s = s13 + 13 * i;
+        real* s = s13 + 13 * i;
         s[0] = b.x.x; s[1] = b.x.y; s[2] = b.x.z;
         for (int k = 0; k < 4; k++) s[3 + k] = b.q[k];
         s[7] = b.v.x; s[8] = b.v.y; s[9] = b.v.z;
@@ -595,16 +643,16 @@ void store_env(const Env& E, double* s13) {
 
 // Pusher kinematics: the tip moves from the start along the unit direction at speed
 // v_p for `moving` substeps (the push length over v_p dt, rounded), then rests.
-void set_push(Env& E, const oracle_params& P, const double* push) {
+void set_push(Env& E, const oracle_params& P, const real* push) {
     PushState& ps = E.push;
-    const double dx = push[2] - push[0], dy = push[3] - push[1];
-    const double L = std::sqrt(dx * dx + dy * dy);
+    const real dx = push[2] - push[0], dy = push[3] - push[1];
+    const real L = sqrt(dx * dx + dy * dy);
     if (!(L > 1e-9)) { ps.active = false; return; }
     ps.active = true;
     ps.sx = push[0]; ps.sy = push[1];
     ps.dx = dx / L; ps.dy = dy / L;
-    const double step = P.pusher_speed * P.dt;
-    long mv = std::lround(L / step);
+    const real step = P.pusher_speed * P.dt;
+    long mv = std::lround(as_double(L / step));
     if (mv > P.substeps_per_push) mv = P.substeps_per_push;
     if (mv < 0) mv = 0;
     ps.moving = (int)mv;
@@ -613,7 +661,7 @@ void set_push(Env& E, const oracle_params& P, const double* push) {
 void pusher_at(Env& E, const oracle_params& P, int s) {
     const PushState& ps = E.push;
     const int done = s < ps.moving ? s : ps.moving;
-    const double travel = (P.pusher_speed * P.dt) * (double)done;
+    const real travel = (P.pusher_speed * P.dt) * (real)done;
     E.P = {ps.sx + ps.dx * travel, ps.sy + ps.dy * travel, 0.0};
     if (s < ps.moving) E.V = {ps.dx * P.pusher_speed, ps.dy * P.pusher_speed, 0.0};
     else E.V = {0, 0, 0};
@@ -624,13 +672,13 @@ void pusher_at(Env& E, const oracle_params& P, int s) {
 // Box against the table plane: the box vertices lower than the margin, deepest first
 // (ties by vertex index), at most four.  Normal +z from the plane (A) to the box (B).
 bool box_plane(const Body& b, int bi, const oracle_params& P, Manifold& M) {
-    struct Cand { double d; int v; V3 r; };
+    struct Cand { real d; int v; V3 r; };
     Cand c[8];
     int nc = 0;
     for (int v = 0; v < 8; v++) {
         const V3 l = {(v & 1 ? 1.0 : -1.0) * b.h[0], (v & 2 ? 1.0 : -1.0) * b.h[1], (v & 4 ? 1.0 : -1.0) * b.h[2]};
         const V3 r = rot(b.R, l);
-        const double d = b.x.z + r.z;
+        const real d = b.x.z + r.z;
         if (d < P.margin) c[nc++] = {d, v, r};
     }
     if (nc == 0) return false;
@@ -651,13 +699,13 @@ bool box_plane(const Body& b, int bi, const oracle_params& P, Manifold& M) {
 // Sutherland-Hodgman clip of a polygon against the half space dot(p - o, a) - h <= 0.
 // At most `cap` vertices are kept (eight, the bound for a convex quad clipped four
 // times; 32 for faces of cylinders).
-std::vector<V3> clip_side(const std::vector<V3>& poly, V3 o, V3 a, double h, size_t cap = 8) {
+std::vector<V3> clip_side(const std::vector<V3>& poly, V3 o, V3 a, real h, size_t cap = 8) {
     std::vector<V3> out;
     const size_t N = poly.size();
     auto add = [&](V3 p) { if (out.size() < cap) out.push_back(p); };
     for (size_t i = 0; i < N; i++) {
         const V3 cur = poly[i], prev = poly[(i + N - 1) % N];
-        const double dc = dot(cur - o, a) - h, dp = dot(prev - o, a) - h;
+        const real dc = dot(cur - o, a) - h, dp = dot(prev - o, a) - h;
         if (dc <= 0) {
             if (dp > 0) add(prev + (cur - prev) * (dp / (dp - dc)));
             add(cur);
@@ -672,7 +720,7 @@ std::vector<V3> clip_side(const std::vector<V3>& poly, V3 o, V3 a, double h, siz
 // of them when there are four or fewer; else the deepest (earliest on ties); then the
 // farthest from it; then the one spanning the largest triangle with those two; then the
 // one adding the largest area outside an edge of that triangle.
-int reduce_points(const std::vector<V3>& kp, const std::vector<double>& kd, V3 nref, V3* pts, double* dep) {
+int reduce_points(const std::vector<V3>& kp, const std::vector<real>& kd, V3 nref, V3* pts, real* dep) {
     const int nk = (int)kp.size();
     if (nk <= 4) {
         for (int i = 0; i < nk; i++) { pts[i] = kp[i]; dep[i] = kd[i]; }
@@ -683,27 +731,27 @@ int reduce_points(const std::vector<V3>& kp, const std::vector<double>& kd, V3 n
     int i1 = 0;
     for (int i = 1; i < nk; i++) if (kd[i] < kd[i1]) i1 = i;
     used[i1] = true;
-    int i2 = -1; double b2 = -1;
+    int i2 = -1; real b2 = -1;
     for (int i = 0; i < nk; i++) {
         if (used[i]) continue;
         const V3 e = kp[i] - kp[i1];
-        const double l = dot(e, e);
+        const real l = dot(e, e);
         if (i2 < 0 || l > b2) { b2 = l; i2 = i; }
     }
     used[i2] = true;
     auto area = [&](int a, int b, V3 p) { return dot(cross(kp[b] - kp[a], p - kp[a]), nref); };
-    int i3 = -1; double b3 = -1;
+    int i3 = -1; real b3 = -1;
     for (int i = 0; i < nk; i++) {
         if (used[i]) continue;
-        const double A = std::fabs(area(i1, i2, kp[i]));
+        const real A = fabs(area(i1, i2, kp[i]));
         if (i3 < 0 || A > b3) { b3 = A; i3 = i; }
     }
     used[i3] = true;
-    const double sgn = area(i1, i2, kp[i3]) < 0 ? -1.0 : 1.0;
-    int i4 = -1; double b4 = 0;
+    const real sgn = area(i1, i2, kp[i3]) < 0 ? -1.0 : 1.0;
+    int i4 = -1; real b4 = 0;
     for (int i = 0; i < nk; i++) {
         if (used[i]) continue;
-        double A = -sgn * area(i1, i2, kp[i]);
+        real A = -sgn * area(i1, i2, kp[i]);
         A = std::max(A, -sgn * area(i2, i3, kp[i]));
         A = std::max(A, -sgn * area(i3, i1, kp[i]));
         if (i4 < 0 || A > b4) { b4 = A; i4 = i; }
@@ -717,21 +765,21 @@ int reduce_points(const std::vector<V3>& kp, const std::vector<double>& kd, V3 n
 // reference face (outward normal nref, axis index k of box `ref`), keep points within
 // the margin of the reference face, reduce to at most four.
 int face_contact(const Body& ref, int k, V3 nref, const Body& inc, const oracle_params& P,
-                 V3* pts, double* dep, uint64_t* ev) {
+                 V3* pts, real* dep, uint64_t* ev) {
     const V3 fc = ref.x + nref * ref.h[k];
     const int k1 = (k == 0) ? 1 : 0, k2 = (k == 2) ? 1 : 2;
     const V3 u = axis(ref, k1), v = axis(ref, k2);
-    const double hu = ref.h[k1], hv = ref.h[k2];
+    const real hu = ref.h[k1], hv = ref.h[k2];
     // incident face: the face of `inc` whose outward normal is most anti-parallel to nref
     int best_f = 0;
-    double best = 0;
+    real best = 0;
     for (int m = 0; m < 3; m++) {
-        const double dm = dot(axis(inc, m), nref);
+        const real dm = dot(axis(inc, m), nref);
         if (m == 0 || dm < best) { best = dm; best_f = 2 * m; }
         if (-dm < best) { best = -dm; best_f = 2 * m + 1; }
     }
     const int mi = best_f / 2;
-    const double si = (best_f % 2 == 0) ? 1.0 : -1.0;
+    const real si = (best_f % 2 == 0) ? 1.0 : -1.0;
     const int m1 = (mi == 0) ? 1 : 0, m2 = (mi == 2) ? 1 : 2;
     const V3 fi = inc.x + axis(inc, mi) * (si * inc.h[mi]);
     const V3 e1 = axis(inc, m1) * inc.h[m1], e2 = axis(inc, m2) * inc.h[m2];
@@ -742,9 +790,9 @@ int face_contact(const Body& ref, int k, V3 nref, const Body& inc, const oracle_
     poly = clip_side(poly, fc, -v, hv);
     ev[EV_CLIP_VERTS] += poly.size();
     std::vector<V3> kp;
-    std::vector<double> kd;
+    std::vector<real> kd;
     for (const V3& p : poly) {
-        const double d = dot(p - fc, nref);
+        const real d = dot(p - fc, nref);
         if (d < P.margin) { kp.push_back(p); kd.push_back(d); }
     }
     return reduce_points(kp, kd, nref, pts, dep);
@@ -753,7 +801,7 @@ int face_contact(const Body& ref, int k, V3 nref, const Body& inc, const oracle_
 struct SatResult {
     bool touching;
     int axis;      // 0..2 faces of A, 3..5 faces of B, 6..14 edge a*3+b
-    double sep;
+    real sep;
     V3 n;          // from A to B
 };
 
@@ -762,40 +810,40 @@ struct SatResult {
 // deeper-separated by more than 1e-5 m; an edge axis replaces the chosen face only when
 // its separation exceeds the face's by 1e-4 m + 5% of |face separation|.  Earliest axis
 // wins exact ties.
-SatResult sat(const Body& A, const Body& B, double margin) {
+SatResult sat(const Body& A, const Body& B, real margin) {
     SatResult r{false, -1, 0, {0, 0, 0}};
     const V3 D = B.x - A.x;
-    double C[3][3], aC[3][3];
+    real C[3][3], aC[3][3];
     for (int k = 0; k < 3; k++)
-        for (int m = 0; m < 3; m++) { C[k][m] = dot(axis(A, k), axis(B, m)); aC[k][m] = std::fabs(C[k][m]); }
-    int fa = -1; double sa = 0;
+        for (int m = 0; m < 3; m++) { C[k][m] = dot(axis(A, k), axis(B, m)); aC[k][m] = fabs(C[k][m]); }
+    int fa = -1; real sa = 0;
     for (int k = 0; k < 3; k++) {
-        const double s = std::fabs(dot(D, axis(A, k))) - (A.h[k] + (B.h[0] * aC[k][0] + B.h[1] * aC[k][1] + B.h[2] * aC[k][2]));
+        const real s = fabs(dot(D, axis(A, k))) - (A.h[k] + (B.h[0] * aC[k][0] + B.h[1] * aC[k][1] + B.h[2] * aC[k][2]));
         if (s >= margin) return r;
         if (fa < 0 || s > sa) { fa = k; sa = s; }
     }
-    int fb = -1; double sb = 0;
+    int fb = -1; real sb = 0;
     for (int m = 0; m < 3; m++) {
-        const double s = std::fabs(dot(D, axis(B, m))) - ((A.h[0] * aC[0][m] + A.h[1] * aC[1][m] + A.h[2] * aC[2][m]) + B.h[m]);
+        const real s = fabs(dot(D, axis(B, m))) - ((A.h[0] * aC[0][m] + A.h[1] * aC[1][m] + A.h[2] * aC[2][m]) + B.h[m]);
         if (s >= margin) return r;
         if (fb < 0 || s > sb) { fb = m; sb = s; }
     }
-    int fe = -1; double se = 0; V3 le{0, 0, 0};
+    int fe = -1; real se = 0; V3 le{0, 0, 0};
     for (int a = 0; a < 3; a++)
         for (int b = 0; b < 3; b++) {
             const V3 L = cross(axis(A, a), axis(B, b));
-            const double l2 = dot(L, L);
+            const real l2 = dot(L, L);
             if (l2 < 1e-12) continue;
-            const double len = std::sqrt(l2);
-            const double rA = (A.h[0] * std::fabs(dot(axis(A, 0), L)) + A.h[1] * std::fabs(dot(axis(A, 1), L))) + A.h[2] * std::fabs(dot(axis(A, 2), L));
-            const double rB = (B.h[0] * std::fabs(dot(axis(B, 0), L)) + B.h[1] * std::fabs(dot(axis(B, 1), L))) + B.h[2] * std::fabs(dot(axis(B, 2), L));
-            const double s = (std::fabs(dot(D, L)) - (rA + rB)) / len;
+            const real len = sqrt(l2);
+            const real rA = (A.h[0] * fabs(dot(axis(A, 0), L)) + A.h[1] * fabs(dot(axis(A, 1), L))) + A.h[2] * fabs(dot(axis(A, 2), L));
+            const real rB = (B.h[0] * fabs(dot(axis(B, 0), L)) + B.h[1] * fabs(dot(axis(B, 1), L))) + B.h[2] * fabs(dot(axis(B, 2), L));
+            const real s = (fabs(dot(D, L)) - (rA + rB)) / len;
             if (s >= margin) return r;
             if (fe < 0 || s > se) { fe = 6 + 3 * a + b; se = s; le = L * (1.0 / len); }
         }
-    int ax = fa; double s = sa; V3 L = axis(A, fa);
+    int ax = fa; real s = sa; V3 L = axis(A, fa);
     if (sb > sa + 1e-5) { ax = 3 + fb; s = sb; L = axis(B, fb); }
-    if (fe >= 0 && se > s + 1e-4 + 0.05 * std::fabs(s)) { ax = fe; s = se; L = le; }
+    if (fe >= 0 && se > s + 1e-4 + 0.05 * fabs(s)) { ax = fe; s = se; L = le; }
     if (dot(L, D) < 0) L = -L;
     r.touching = true; r.axis = ax; r.sep = s; r.n = L;
     return r;
@@ -808,7 +856,7 @@ bool box_box(const Body& A, int ia, const Body& B, int ib, const oracle_params& 
     const SatResult s = sat(A, B, P.margin);
     if (!s.touching) return false;
     V3 pts[4];
-    double dep[4];
+    real dep[4];
     int np = 0;
     if (s.axis < 3) {
         ev[EV_FACE]++;
@@ -822,19 +870,19 @@ bool box_box(const Body& A, int ia, const Body& B, int ib, const oracle_params& 
         V3 pA = A.x, pB = B.x;
         for (int k = 0; k < 3; k++) {
             if (k == a) continue;
-            const double sg = dot(axis(A, k), s.n) < 0 ? -1.0 : 1.0;
+            const real sg = dot(axis(A, k), s.n) < 0 ? -1.0 : 1.0;
             pA = pA + axis(A, k) * (sg * A.h[k]);
         }
         for (int m = 0; m < 3; m++) {
             if (m == b) continue;
-            const double sg = dot(axis(B, m), s.n) > 0 ? -1.0 : 1.0;
+            const real sg = dot(axis(B, m), s.n) > 0 ? -1.0 : 1.0;
             pB = pB + axis(B, m) * (sg * B.h[m]);
         }
         const V3 dA = axis(A, a), dB = axis(B, b);
         const V3 r = pA - pB;
-        const double bb = dot(dA, dB), c = dot(dA, r), f = dot(dB, r);
-        const double den = 1.0 - bb * bb;
-        double sa = 0, tb;
+        const real bb = dot(dA, dB), c = dot(dA, r), f = dot(dB, r);
+        const real den = 1.0 - bb * bb;
+        real sa = 0, tb;
         if (den > 1e-12) { sa = (bb * f - c) / den; tb = f + sa * bb; }
         else tb = f;
         sa = std::min(std::max(sa, -A.h[a]), A.h[a]);
@@ -863,39 +911,39 @@ bool box_box(const Body& A, int ia, const Body& B, int ib, const oracle_params& 
 // point closest to it.  Candidates closer than radius + margin become contacts; the
 // normal (box to pusher) is that of the nearest candidate.
 bool capsule_box(const Body& b, int bi, V3 Pp, const oracle_params& P, Manifold& M) {
-    const double ez = (std::fabs(b.R[6]) * b.h[0] + std::fabs(b.R[7]) * b.h[1]) + std::fabs(b.R[8]) * b.h[2];
-    const double zlo = b.x.z - ez, zhi = b.x.z + ez;
-    const double za = std::max(P.pusher_z0, zlo), zb = std::min(P.pusher_z1, zhi);
-    double zc[2];
+    const real ez = (fabs(b.R[6]) * b.h[0] + fabs(b.R[7]) * b.h[1]) + fabs(b.R[8]) * b.h[2];
+    const real zlo = b.x.z - ez, zhi = b.x.z + ez;
+    const real za = std::max<real>(P.pusher_z0, zlo), zb = std::min<real>(P.pusher_z1, zhi);
+    real zc[2];
     int nc;
     if (za > zb) { zc[0] = (zhi < P.pusher_z0) ? P.pusher_z0 : P.pusher_z1; nc = 1; }
     else if (zb - za < 1e-3) { zc[0] = (za + zb) * 0.5; nc = 1; }
     else { zc[0] = za; zc[1] = zb; nc = 2; }
     int np = 0;
-    double best_d = 0;
+    real best_d = 0;
     V3 best_n{1, 0, 0};
     for (int i = 0; i < nc; i++) {
         const V3 S = {Pp.x, Pp.y, zc[i]};
         const V3 rel = S - b.x;
-        double loc[3], ql[3];
+        real loc[3], ql[3];
         for (int k = 0; k < 3; k++) {
             loc[k] = dot(axis(b, k), rel);
             ql[k] = std::min(std::max(loc[k], -b.h[k]), b.h[k]);
         }
         const V3 Q = b.x + axis(b, 0) * ql[0] + axis(b, 1) * ql[1] + axis(b, 2) * ql[2];
         const V3 diff = S - Q;
-        const double dist = norm(diff);
+        const real dist = norm(diff);
         V3 nrm;
-        double d;
+        real d;
         if (dist > 1e-6) {
             nrm = diff * (1.0 / dist);
             d = dist - P.pusher_radius;
         } else {
-            double pen = b.h[0] - std::fabs(loc[0]);
-            for (int k = 1; k < 3; k++) pen = std::min(pen, b.h[k] - std::fabs(loc[k]));
+            real pen = b.h[0] - fabs(loc[0]);
+            for (int k = 1; k < 3; k++) pen = std::min(pen, b.h[k] - fabs(loc[k]));
             d = -pen - P.pusher_radius;
             const V3 w = {S.x - b.x.x, S.y - b.x.y, 0};
-            const double lw = norm(w);
+            const real lw = norm(w);
             nrm = lw > 1e-9 ? w * (1.0 / lw) : V3{1, 0, 0};
         }
         if (!(d < P.margin)) continue;
@@ -926,69 +974,69 @@ bool capsule_box(const Body& b, int bi, V3 Pp, const oracle_params& P, Manifold&
 // anti-parallel), up to 32 clipped vertices, reduced to four as for boxes; an edge axis
 // gives one point midway between the closest points of the two supporting edges.
 
-const Gon<double>& G64() { return gon<double>(); }
+const Gon<real>& G64() { return gon<real>(); }
 // body-plane unit vectors: vertex direction k, side normal s and side tangent s (k, s in 0..15)
-inline void gon_vdir(int k, double& c, double& sn) { const double g = k < 8 ? 1 : -1; c = g * G64().vc[k & 7]; sn = g * G64().vs[k & 7]; }
-inline void gon_fdir(int s, double& c, double& sn) { const double g = s < 8 ? 1 : -1; c = g * G64().fc[s & 7]; sn = g * G64().fs[s & 7]; }
-inline V3 plane_vec(const Body& b, double c, double sn) { return axis(b, 0) * c + axis(b, 1) * sn; }
-inline V3 side_normal(const Body& b, int s) { double c, sn; gon_fdir(s, c, sn); return plane_vec(b, c, sn); }
-inline V3 side_tangent(const Body& b, int s) { double c, sn; gon_fdir(s, c, sn); return plane_vec(b, -sn, c); }
-inline V3 cyl_vertex(const Body& b, int k, double sz) {
-    double c, sn;
+inline void gon_vdir(int k, real& c, real& sn) { const real g = k < 8 ? 1 : -1; c = g * G64().vc[k & 7]; sn = g * G64().vs[k & 7]; }
+inline void gon_fdir(int s, real& c, real& sn) { const real g = s < 8 ? 1 : -1; c = g * G64().fc[s & 7]; sn = g * G64().fs[s & 7]; }
+inline V3 plane_vec(const Body& b, real c, real sn) { return axis(b, 0) * c + axis(b, 1) * sn; }
+inline V3 side_normal(const Body& b, int s) { real c, sn; gon_fdir(s, c, sn); return plane_vec(b, c, sn); }
+inline V3 side_tangent(const Body& b, int s) { real c, sn; gon_fdir(s, c, sn); return plane_vec(b, -sn, c); }
+inline V3 cyl_vertex(const Body& b, int k, real sz) {
+    real c, sn;
     gon_vdir(k & 15, c, sn);
     return b.x + plane_vec(b, c * b.h[0], sn * b.h[0]) + axis(b, 2) * (sz * b.h[2]);
 }
-inline double cyl_apothem(const Body& b) { return b.h[0] * G64().apo; }
+inline real cyl_apothem(const Body& b) { return b.h[0] * G64().apo; }
 
-double support(const Body& b, V3 L) {
-    if (b.cyl) return gon_support(dot(axis(b, 0), L), dot(axis(b, 1), L)) * b.h[0] + std::fabs(dot(axis(b, 2), L)) * b.h[2];
-    return (b.h[0] * std::fabs(dot(axis(b, 0), L)) + b.h[1] * std::fabs(dot(axis(b, 1), L))) + b.h[2] * std::fabs(dot(axis(b, 2), L));
+real support(const Body& b, V3 L) {
+    if (b.cyl) return gon_support(dot(axis(b, 0), L), dot(axis(b, 1), L)) * b.h[0] + fabs(dot(axis(b, 2), L)) * b.h[2];
+    return (b.h[0] * fabs(dot(axis(b, 0), L)) + b.h[1] * fabs(dot(axis(b, 1), L))) + b.h[2] * fabs(dot(axis(b, 2), L));
 }
 inline int n_dirs(const Body& b) { return b.cyl ? 9 : 3; }
 inline V3 face_dir(const Body& b, int f) { return !b.cyl ? axis(b, f) : (f == 0 ? axis(b, 2) : side_normal(b, f - 1)); }
-inline double face_half(const Body& b, int f) { return !b.cyl ? b.h[f] : (f == 0 ? b.h[2] : cyl_apothem(b)); }
+inline real face_half(const Body& b, int f) { return !b.cyl ? b.h[f] : (f == 0 ? b.h[2] : cyl_apothem(b)); }
 inline V3 edge_dir(const Body& b, int j) { return !b.cyl ? axis(b, j) : (j == 0 ? axis(b, 2) : side_tangent(b, j - 1)); }
 
 struct ConvexSat {
     bool touching;
     int kind;   // 0 face of A, 1 face of B, 2 edge pair
     int i, j;   // face index, or edge of A and edge of B
-    double sep;
+    real sep;
     V3 n;       // from A to B
 };
 
-ConvexSat sat_convex(const Body& A, const Body& B, double margin) {
+ConvexSat sat_convex(const Body& A, const Body& B, real margin) {
     ConvexSat r{false, 0, -1, -1, 0, {0, 0, 0}};
     const V3 D = B.x - A.x;
-    int fa = -1; double sa = 0;
+    int fa = -1; real sa = 0;
     for (int f = 0; f < n_dirs(A); f++) {
         const V3 L = face_dir(A, f);
-        const double s = std::fabs(dot(D, L)) - (face_half(A, f) + support(B, L));
+        const real s = fabs(dot(D, L)) - (face_half(A, f) + support(B, L));
         if (s >= margin) return r;
         if (fa < 0 || s > sa) { fa = f; sa = s; }
     }
-    int fb = -1; double sb = 0;
+    int fb = -1; real sb = 0;
     for (int f = 0; f < n_dirs(B); f++) {
         const V3 L = face_dir(B, f);
-        const double s = std::fabs(dot(D, L)) - (support(A, L) + face_half(B, f));
+        const real s = fabs(dot(D, L)) - (support(A, L) + face_half(B, f));
         if (s >= margin) return r;
         if (fb < 0 || s > sb) { fb = f; sb = s; }
     }
-    int ea = -1, eb = -1; double se = 0; V3 le{0, 0, 0};
+    int ea = -1, eb = -1; real se = 0; V3 le{0, 0, 0};
     for (int i = 0; i < n_dirs(A); i++)
         for (int j = 0; j < n_dirs(B); j++) {
             const V3 L = cross(edge_dir(A, i), edge_dir(B, j));
-            const double l2 = dot(L, L);
+            const real l2 = dot(L, L);
             if (l2 < 1e-12) continue;
-            const double len = std::sqrt(l2);
+            const real len = sqrt(l2);
             const V3 u = L * (1.0 / len);
-            const double s = std::fabs(dot(D, u)) - (support(A, u) + support(B, u));
+            const real s = fabs(dot(D, u)) - (support(A, u) + support(B, u));
             if (s >= margin) return r;
             if (ea < 0 || s > se) { ea = i; eb = j; se = s; le = u; }
         }
-    int kind = 0, i = fa, j = -1; double s = sa; V3 L = face_dir(A, fa);
+    int kind = 0, i = fa, j = -1; real s = sa; V3 L = face_dir(A, fa);
     if (sb > sa + 1e-5) { kind = 1; i = fb; s = sb; L = face_dir(B, fb); }
-    if (ea >= 0 && se > s + 1e-4 + 0.05 * std::fabs(s)) { kind = 2; i = ea; j = eb; s = se; L = le; }
+    if (ea >= 0 && se > s + 1e-4 + 0.05 * fabs(s)) { kind = 2; i = ea; j = eb; s = se; L = le; }
     if (dot(L, D) < 0) L = -L;
     r.touching = true; r.kind = kind; r.i = i; r.j = j; r.sep = s; r.n = L;
     return r;
@@ -996,8 +1044,8 @@ ConvexSat sat_convex(const Body& A, const Body& B, double margin) {
 
 // Face contact between convex bodies: reference face f of `ref` with outward normal nref.
 int face_contact_convex(const Body& ref, int f, V3 nref, const Body& inc, const oracle_params& P,
-                        V3* pts, double* dep, uint64_t* ev) {
-    struct Side { V3 a; double h; };
+                        V3* pts, real* dep, uint64_t* ev) {
+    struct Side { V3 a; real h; };
     std::vector<Side> sides;
     V3 fc;
     if (!ref.cyl) {
@@ -1012,36 +1060,36 @@ int face_contact_convex(const Body& ref, int f, V3 nref, const Body& inc, const 
         const int s = dot(side_normal(ref, f - 1), nref) > 0 ? f - 1 : f + 7;
         fc = ref.x + nref * cyl_apothem(ref);
         const V3 ez = axis(ref, 2), t = side_tangent(ref, s);
-        const double w = ref.h[0] * G64().half_edge;
+        const real w = ref.h[0] * G64().half_edge;
         sides = {{ez, ref.h[2]}, {-ez, ref.h[2]}, {t, w}, {-t, w}};
     }
     std::vector<V3> poly;
     if (!inc.cyl) {
         int best_f = 0;
-        double best = 0;
+        real best = 0;
         for (int m = 0; m < 3; m++) {
-            const double dm = dot(axis(inc, m), nref);
+            const real dm = dot(axis(inc, m), nref);
             if (m == 0 || dm < best) { best = dm; best_f = 2 * m; }
             if (-dm < best) { best = -dm; best_f = 2 * m + 1; }
         }
         const int mi = best_f / 2;
-        const double si = (best_f % 2 == 0) ? 1.0 : -1.0;
+        const real si = (best_f % 2 == 0) ? 1.0 : -1.0;
         const int m1 = (mi == 0) ? 1 : 0, m2 = (mi == 2) ? 1 : 2;
         const V3 fi = inc.x + axis(inc, mi) * (si * inc.h[mi]);
         const V3 e1 = axis(inc, m1) * inc.h[m1], e2 = axis(inc, m2) * inc.h[m2];
         poly = {fi + e1 + e2, fi - e1 + e2, fi - e1 - e2, fi + e1 - e2};
     } else {
         // candidates in order: top cap, bottom cap, sides 0..15
-        const double dz = dot(axis(inc, 2), nref);
+        const real dz = dot(axis(inc, 2), nref);
         int best_c = 0;
-        double best = dz;
+        real best = dz;
         if (-dz < best) { best = -dz; best_c = 1; }
         for (int s = 0; s < 16; s++) {
-            const double dm = dot(side_normal(inc, s), nref);
+            const real dm = dot(side_normal(inc, s), nref);
             if (dm < best) { best = dm; best_c = 2 + s; }
         }
         if (best_c < 2) {
-            const double sz = best_c == 0 ? 1.0 : -1.0;
+            const real sz = best_c == 0 ? 1.0 : -1.0;
             for (int k = 0; k < 16; k++) poly.push_back(cyl_vertex(inc, k, sz));
         } else {
             const int s = best_c - 2;
@@ -1052,32 +1100,32 @@ int face_contact_convex(const Body& ref, int f, V3 nref, const Body& inc, const 
     for (const Side& sd : sides) poly = clip_side(poly, fc, sd.a, sd.h, 32);
     ev[EV_CLIP_VERTS] += poly.size();
     std::vector<V3> kp;
-    std::vector<double> kd;
+    std::vector<real> kd;
     for (const V3& p : poly) {
-        const double d = dot(p - fc, nref);
+        const real d = dot(p - fc, nref);
         if (d < P.margin) { kp.push_back(p); kd.push_back(d); }
     }
     return reduce_points(kp, kd, nref, pts, dep);
 }
 
 // Supporting edge of direction index j of body b toward L: centre, direction, half length.
-void support_edge(const Body& b, int j, V3 L, V3& c, V3& d, double& hl) {
+void support_edge(const Body& b, int j, V3 L, V3& c, V3& d, real& hl) {
     if (!b.cyl) {
         c = b.x;
         for (int k = 0; k < 3; k++) {
             if (k == j) continue;
-            const double sg = dot(axis(b, k), L) < 0 ? -1.0 : 1.0;
+            const real sg = dot(axis(b, k), L) < 0 ? -1.0 : 1.0;
             c = c + axis(b, k) * (sg * b.h[k]);
         }
         d = axis(b, j);
         hl = b.h[j];
     } else if (j == 0) {
         int kb = 0;
-        double best = 0;
+        real best = 0;
         for (int k = 0; k < 16; k++) {
-            double vc, vs;
+            real vc, vs;
             gon_vdir(k, vc, vs);
-            const double v = dot(plane_vec(b, vc, vs), L);
+            const real v = dot(plane_vec(b, vc, vs), L);
             if (k == 0 || v > best) { best = v; kb = k; }
         }
         c = cyl_vertex(b, kb, 0.0);
@@ -1085,7 +1133,7 @@ void support_edge(const Body& b, int j, V3 L, V3& c, V3& d, double& hl) {
         hl = b.h[2];
     } else {
         const int s = dot(side_normal(b, j - 1), L) >= 0 ? j - 1 : j + 7;
-        const double sz = dot(axis(b, 2), L) >= 0 ? 1.0 : -1.0;
+        const real sz = dot(axis(b, 2), L) >= 0 ? 1.0 : -1.0;
         c = b.x + side_normal(b, s) * cyl_apothem(b) + axis(b, 2) * (sz * b.h[2]);
         d = side_tangent(b, s);
         hl = b.h[0] * G64().half_edge;
@@ -1097,7 +1145,7 @@ bool convex_pair(const Body& A, int ia, const Body& B, int ib, const oracle_para
     const ConvexSat s = sat_convex(A, B, P.margin);
     if (!s.touching) return false;
     V3 pts[4];
-    double dep[4];
+    real dep[4];
     int np = 0;
     if (s.kind == 0) {
         ev[EV_FACE]++;
@@ -1108,13 +1156,13 @@ bool convex_pair(const Body& A, int ia, const Body& B, int ib, const oracle_para
     } else {
         ev[EV_EDGE]++;
         V3 pA, pB, dA, dB;
-        double ha, hb;
+        real ha, hb;
         support_edge(A, s.i, s.n, pA, dA, ha);
         support_edge(B, s.j, -s.n, pB, dB, hb);
         const V3 r = pA - pB;
-        const double bb = dot(dA, dB), c = dot(dA, r), f = dot(dB, r);
-        const double den = 1.0 - bb * bb;
-        double sa = 0, tb;
+        const real bb = dot(dA, dB), c = dot(dA, r), f = dot(dB, r);
+        const real den = 1.0 - bb * bb;
+        real sa = 0, tb;
         if (den > 1e-12) { sa = (bb * f - c) / den; tb = f + sa * bb; }
         else tb = f;
         sa = std::min(std::max(sa, -ha), ha);
@@ -1142,17 +1190,17 @@ bool convex_pair(const Body& A, int ia, const Body& B, int ib, const oracle_para
 // more are reduced to four as for face contacts.  Normal +z.
 bool cyl_plane(const Body& b, int bi, const oracle_params& P, Manifold& M) {
     std::vector<V3> kp;
-    std::vector<double> kd;
+    std::vector<real> kd;
     std::vector<int> kv;
     for (int v = 0; v < 32; v++) {
         const V3 r = cyl_vertex(b, v & 15, v < 16 ? -1.0 : 1.0) - b.x;
-        const double d = b.x.z + r.z;
+        const real d = b.x.z + r.z;
         if (d < P.margin) { kp.push_back(r); kd.push_back(d); kv.push_back(v); }
     }
     const int nc = (int)kp.size();
     if (nc == 0) return false;
     V3 pts[4];
-    double dep[4];
+    real dep[4];
     int np;
     if (nc <= 4) {
         std::vector<int> o(nc);
@@ -1184,60 +1232,60 @@ bool cyl_plane(const Body& b, int bi, const oracle_params& P, Manifold& M) {
 // axial coordinate clamped.  Inside the prism the depth is the smallest distance to a
 // face.
 bool capsule_cyl(const Body& b, int bi, V3 Pp, const oracle_params& P, Manifold& M) {
-    const double ez = gon_support(b.R[6], b.R[7]) * b.h[0] + std::fabs(b.R[8]) * b.h[2];
-    const double zlo = b.x.z - ez, zhi = b.x.z + ez;
-    const double za = std::max(P.pusher_z0, zlo), zb = std::min(P.pusher_z1, zhi);
-    double zc[2];
+    const real ez = gon_support(b.R[6], b.R[7]) * b.h[0] + fabs(b.R[8]) * b.h[2];
+    const real zlo = b.x.z - ez, zhi = b.x.z + ez;
+    const real za = std::max<real>(P.pusher_z0, zlo), zb = std::min<real>(P.pusher_z1, zhi);
+    real zc[2];
     int nc;
     if (za > zb) { zc[0] = (zhi < P.pusher_z0) ? P.pusher_z0 : P.pusher_z1; nc = 1; }
     else if (zb - za < 1e-3) { zc[0] = (za + zb) * 0.5; nc = 1; }
     else { zc[0] = za; zc[1] = zb; nc = 2; }
-    const double r = b.h[0], apo = cyl_apothem(b);
+    const real r = b.h[0], apo = cyl_apothem(b);
     int np = 0;
-    double best_d = 0;
+    real best_d = 0;
     V3 best_n{1, 0, 0};
     for (int i = 0; i < nc; i++) {
         const V3 S = {Pp.x, Pp.y, zc[i]};
         const V3 rel = S - b.x;
-        const double lx = dot(axis(b, 0), rel), ly = dot(axis(b, 1), rel), lz = dot(axis(b, 2), rel);
+        const real lx = dot(axis(b, 0), rel), ly = dot(axis(b, 1), rel), lz = dot(axis(b, 2), rel);
         bool inside = true;
-        double pen_side = 1e300;
+        real pen_side = 1e300;
         for (int s = 0; s < 16; s++) {
-            double fcs, fss;
+            real fcs, fss;
             gon_fdir(s, fcs, fss);
-            const double g = apo - (fcs * lx + fss * ly);
+            const real g = apo - (fcs * lx + fss * ly);
             if (g < 0) inside = false;
             pen_side = std::min(pen_side, g);
         }
-        double qx = lx, qy = ly;
+        real qx = lx, qy = ly;
         if (!inside) {
-            double bd = 0;
+            real bd = 0;
             for (int s = 0; s < 16; s++) {
-                double c0, s0, c1, s1;
+                real c0, s0, c1, s1;
                 gon_vdir(s, c0, s0);
                 gon_vdir((s + 1) & 15, c1, s1);
-                const double ax = r * c0, ay = r * s0, ex = r * c1 - ax, ey = r * s1 - ay;
-                double t = ((lx - ax) * ex + (ly - ay) * ey) / (ex * ex + ey * ey);
-                t = std::min(std::max(t, 0.0), 1.0);
-                const double px = ax + ex * t, py = ay + ey * t;
-                const double dd = (lx - px) * (lx - px) + (ly - py) * (ly - py);
+                const real ax = r * c0, ay = r * s0, ex = r * c1 - ax, ey = r * s1 - ay;
+                real t = ((lx - ax) * ex + (ly - ay) * ey) / (ex * ex + ey * ey);
+                t = std::min<real>(std::max<real>(t, 0.0), 1.0);
+                const real px = ax + ex * t, py = ay + ey * t;
+                const real dd = (lx - px) * (lx - px) + (ly - py) * (ly - py);
                 if (s == 0 || dd < bd) { bd = dd; qx = px; qy = py; }
             }
         }
-        const double qz = std::min(std::max(lz, -b.h[2]), b.h[2]);
+        const real qz = std::min(std::max(lz, -b.h[2]), b.h[2]);
         const V3 Q = b.x + axis(b, 0) * qx + axis(b, 1) * qy + axis(b, 2) * qz;
         const V3 diff = S - Q;
-        const double dist = norm(diff);
+        const real dist = norm(diff);
         V3 nrm;
-        double d;
+        real d;
         if (dist > 1e-6) {
             nrm = diff * (1.0 / dist);
             d = dist - P.pusher_radius;
         } else {
-            const double pen = std::min(b.h[2] - std::fabs(lz), pen_side);
+            const real pen = std::min(b.h[2] - fabs(lz), pen_side);
             d = -pen - P.pusher_radius;
             const V3 w = {S.x - b.x.x, S.y - b.x.y, 0};
-            const double lw = norm(w);
+            const real lw = norm(w);
             nrm = lw > 1e-9 ? w * (1.0 / lw) : V3{1, 0, 0};
         }
         if (!(d < P.margin)) continue;
@@ -1265,7 +1313,7 @@ void refresh_body_frames(Env& E) {
         int idx = 0;
         for (int a = 0; a < 3; a++)
             for (int c = a; c < 3; c++) {
-                double s = 0;
+                real s = 0;
                 for (int k = 0; k < 3; k++) s += b.R[3 * a + k] * b.invIb[k] * b.R[3 * c + k];
                 b.invIw[idx++] = s;
             }
@@ -1280,16 +1328,18 @@ void body_vel(const Env& E, int id, V3& v, V3& w) {
 
 std::vector<Manifold> collide(Env& E, const oracle_params& P) {
     const int n = (int)E.b.size();
-    std::vector<double> x(3 * n), q(4 * n), h(3 * n);
+    std::vector<real> x(3 * n), q(4 * n), h(3 * n);
     for (int i = 0; i < n; i++) {
         x[3 * i] = E.b[i].x.x; x[3 * i + 1] = E.b[i].x.y; x[3 * i + 2] = E.b[i].x.z;
         for (int k = 0; k < 4; k++) q[4 * i + k] = E.b[i].q[k];
         for (int k = 0; k < 3; k++) h[3 * i + k] = E.b[i].h[k];
         if (E.b[i].cyl) h[3 * i + 1] = -h[3 * i + 1];  // keep the cylinder mark
     }
-    const double Pxy[2] = {E.P.x, E.P.y};
-    PairList<double> pl = broadphase<double>(n, x.data(), q.data(), h.data(), P.margin, E.push.active, Pxy,
+    const real Pxy[2] = {E.P.x, E.P.y};
+    set_phase(0);
+    PairList<real> pl = broadphase<real>(n, x.data(), q.data(), h.data(), P.margin, E.push.active, Pxy,
                                              P.pusher_radius, P.pusher_z0, P.pusher_z1, P.pair_cap);
+    set_phase(1);
     E.ev[EV_PAIR_TESTS] += (uint64_t)n * (n - 1) / 2;
     if (pl.overflow) E.overflow = true;
     std::vector<Manifold> ms;
@@ -1308,7 +1358,7 @@ std::vector<Manifold> collide(Env& E, const oracle_params& P) {
         const bool hit = (E.b[i].cyl || E.b[j].cyl) ? convex_pair(E.b[i], i, E.b[j], j, P, M, E.ev)
                                                     : box_box(E.b[i], i, E.b[j], j, P, M, E.ev);
         if (hit) {
-            const double mu = std::sqrt(E.b[i].mu * E.b[j].mu);
+            const real mu = sqrt(E.b[i].mu * E.b[j].mu);
             M.mu = mu;
             const size_t before = ms.size();
             emit(M);
@@ -1319,13 +1369,13 @@ std::vector<Manifold> collide(Env& E, const oracle_params& P) {
         if (stop) break;
         E.ev[EV_PLANE]++;
         Manifold M;
-        if (E.b[i].cyl ? cyl_plane(E.b[i], i, P, M) : box_plane(E.b[i], i, P, M)) { M.mu = std::sqrt(E.b[i].mu * P.table_mu); emit(M); }
+        if (E.b[i].cyl ? cyl_plane(E.b[i], i, P, M) : box_plane(E.b[i], i, P, M)) { M.mu = sqrt(E.b[i].mu * P.table_mu); emit(M); }
     }
     for (int i : pl.pusher) {
         if (stop) break;
         E.ev[EV_PUSHER]++;
         Manifold M;
-        if (E.b[i].cyl ? capsule_cyl(E.b[i], i, E.P, P, M) : capsule_box(E.b[i], i, E.P, P, M)) { M.mu = std::sqrt(E.b[i].mu * P.pusher_mu); emit(M); }
+        if (E.b[i].cyl ? capsule_cyl(E.b[i], i, E.P, P, M) : capsule_box(E.b[i], i, E.P, P, M)) { M.mu = sqrt(E.b[i].mu * P.pusher_mu); emit(M); }
     }
     E.ev[EV_MANIFOLDS] += ms.size();
     E.ev[EV_POINTS] += npts;
@@ -1338,7 +1388,7 @@ std::vector<Manifold> collide(Env& E, const oracle_params& P) {
 void prepare(Env& E, std::vector<Manifold>& ms, const oracle_params& P) {
     for (Manifold& M : ms) {
         const V3 n = M.n;
-        const double an[3] = {std::fabs(n.x), std::fabs(n.y), std::fabs(n.z)};
+        const real an[3] = {fabs(n.x), fabs(n.y), fabs(n.z)};
         int k = 0;
         if (an[1] < an[k]) k = 1;
         if (an[2] < an[k]) k = 2;
@@ -1349,7 +1399,7 @@ void prepare(Env& E, std::vector<Manifold>& ms, const oracle_params& P) {
         for (int p = 0; p < M.np; p++) {
             Contact& C = M.c[p];
             auto keff = [&](V3 dir) {
-                double k2 = 0;
+                real k2 = 0;
                 if (M.A >= 0) {
                     const Body& a = E.b[M.A];
                     const V3 rn = cross(C.rA, dir);
@@ -1366,7 +1416,7 @@ void prepare(Env& E, std::vector<Manifold>& ms, const oracle_params& P) {
             C.invKt1 = 1.0 / keff(M.t1);
             C.invKt2 = 1.0 / keff(M.t2);
             if (C.d > 0) C.bias = -C.d / P.dt;
-            else C.bias = (P.baumgarte / P.dt) * std::max(-C.d - P.slop, 0.0);
+            else C.bias = (P.baumgarte / P.dt) * std::max<real>(-C.d - P.slop, 0.0);
             C.ln = C.lt1 = C.lt2 = 0;
         }
     }
@@ -1417,27 +1467,27 @@ V3 rel_vel(const Env& E, const Manifold& M, const Contact& C) {
 void solve_manifold(Env& E, Manifold& M) {
     for (int p = 0; p < M.np; p++) {
         Contact& C = M.c[p];
-        const double vn = dot(M.n, rel_vel(E, M, C));
-        const double delta = -(vn - C.bias) * C.invKn;
-        const double l = std::max(C.ln + delta, 0.0);
-        const double dl = l - C.ln;
+        const real vn = dot(M.n, rel_vel(E, M, C));
+        const real delta = -(vn - C.bias) * C.invKn;
+        const real l = std::max<real>(C.ln + delta, 0.0);
+        const real dl = l - C.ln;
         C.ln = l;
         apply_impulse(E, M, C, M.n * dl);
     }
     for (int p = 0; p < M.np; p++) {
         Contact& C = M.c[p];
         const V3 vr = rel_vel(E, M, C);
-        const double vt1 = dot(M.t1, vr), vt2 = dot(M.t2, vr);
-        double c1 = C.lt1 - vt1 * C.invKt1;
-        double c2 = C.lt2 - vt2 * C.invKt2;
-        const double lim = M.mu * C.ln;
-        const double l2 = c1 * c1 + c2 * c2;
+        const real vt1 = dot(M.t1, vr), vt2 = dot(M.t2, vr);
+        real c1 = C.lt1 - vt1 * C.invKt1;
+        real c2 = C.lt2 - vt2 * C.invKt2;
+        const real lim = M.mu * C.ln;
+        const real l2 = c1 * c1 + c2 * c2;
         if (l2 > lim * lim) {
-            const double s = lim / std::sqrt(l2);
+            const real s = lim / sqrt(l2);
             c1 *= s;
             c2 *= s;
         }
-        const double d1 = c1 - C.lt1, d2 = c2 - C.lt2;
+        const real d1 = c1 - C.lt1, d2 = c2 - C.lt2;
         C.lt1 = c1;
         C.lt2 = c2;
         apply_impulse(E, M, C, M.t1 * d1 + M.t2 * d2);
@@ -1486,11 +1536,11 @@ void warm_start(Env& E, std::vector<Manifold>& ms, int ncol, const oracle_params
             Contact& C = M.c[p];
             const V3 loc = key_local(E, M, C);
             int best = -1;
-            double bd = P.warm_tolerance * P.warm_tolerance;
+            real bd = P.warm_tolerance * P.warm_tolerance;
             for (int q = 0; q < W->np; q++) {
                 if (used[q]) continue;
                 const V3 d = loc - W->p[q].loc;
-                const double d2 = dot(d, d);
+                const real d2 = dot(d, d);
                 if (d2 <= bd) { bd = d2; best = q; }
             }
             if (best < 0) continue;
@@ -1530,49 +1580,56 @@ void save_warm(Env& E, const std::vector<Manifold>& ms) {
 
 // Semi-implicit Euler: x += v dt; q += dt/2 (0, w) (x) q, renormalised.
 void integrate(Env& E, const oracle_params& P) {
-    const double dt = P.dt;
+    const real dt = P.dt;
     for (Body& b : E.b) {
         b.x = b.x + b.v * dt;
-        const double w0 = b.q[0];
+        const real w0 = b.q[0];
         const V3 qv = {b.q[1], b.q[2], b.q[3]};
-        const double dw = -dot(b.w, qv);
+        const real dw = -dot(b.w, qv);
         const V3 dv = b.w * w0 + cross(b.w, qv);
-        const double hd = 0.5 * dt;
-        double q[4] = {w0 + hd * dw, qv.x + hd * dv.x, qv.y + hd * dv.y, qv.z + hd * dv.z};
-        const double l = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const real hd = 0.5 * dt;
+        real q[4] = {w0 + hd * dw, qv.x + hd * dv.x, qv.y + hd * dv.y, qv.z + hd * dv.z};
+        const real l = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         for (int k = 0; k < 4; k++) b.q[k] = q[k] / l;
     }
 }
 
 void substep(Env& E, const oracle_params& P, int s, bool reverse_within_colour = false) {
+    set_phase(4);
     pusher_at(E, P, s);
+    set_phase(0);
     const V3 g = {P.gravity[0], P.gravity[1], P.gravity[2]};
     for (Body& b : E.b) b.v = b.v + g * P.dt;
     refresh_body_frames(E);
     std::vector<Manifold> ms = collide(E, P);
+    set_phase(2);
     prepare(E, ms, P);
+    set_phase(4);
     const int ncol = colour_manifolds(E, ms);
     E.ev[EV_COLOURS] += ncol;
+    set_phase(3);
     if (P.warm_start) warm_start(E, ms, ncol, P);
     pgs(E, ms, ncol, P.pgs_iters, reverse_within_colour);
     if (P.warm_start) save_warm(E, ms);
+    set_phase(0);
     integrate(E, P);
+    set_phase(4);
     E.ev[EV_SUBSTEPS]++;
     E.ev[EV_BOX_STEPS] += E.b.size();
 }
 
 // ---- rollouts ------------------------------------------------------------------------
 
-void grasp_table(int K, std::vector<double>& ca, std::vector<double>& sa) {
+void grasp_table(int K, std::vector<real>& ca, std::vector<real>& sa) {
     ca.resize(K); sa.resize(K);
     for (int k = 0; k < K; k++) {
-        const double th = k * M_PI / K;
-        ca[k] = (double)(float)std::cos(th);   // binary32-rounded table, as in the engine
-        sa[k] = (double)(float)std::sin(th);
+        const real th = k * M_PI / K;
+        ca[k] = (real)(float)std::cos(as_double(th));   // binary32-rounded table, as in the engine
+        sa[k] = (real)(float)std::sin(as_double(th));
     }
 }
 
-void env_arrays(const Env& E, std::vector<double>& x, std::vector<double>& q, std::vector<double>& h) {
+void env_arrays(const Env& E, std::vector<real>& x, std::vector<real>& q, std::vector<real>& h) {
     const int n = (int)E.b.size();
     x.resize(3 * n); q.resize(4 * n); h.resize(3 * n);
     for (int i = 0; i < n; i++) {
@@ -1584,10 +1641,10 @@ void env_arrays(const Env& E, std::vector<double>& x, std::vector<double>& q, st
 }
 
 bool env_graspable(const Env& E, const oracle_params& P) {
-    std::vector<double> x, q, h, ca, sa;
+    std::vector<real> x, q, h, ca, sa;
     env_arrays(E, x, q, h);
     grasp_table(P.grasp_angles, ca, sa);
-    return graspable<double>((int)E.b.size(), x.data(), q.data(), h.data(), E.target, ca.data(), sa.data(),
+    return graspable<real>((int)E.b.size(), x.data(), q.data(), h.data(), E.target, ca.data(), sa.data(),
                              P.grasp_angles, P.grasp_opening, P.grasp_clearance, P.finger_depth, P.finger_width);
 }
 
@@ -1597,21 +1654,21 @@ struct RolloutOut { int32_t cost; float reward; uint8_t flags; int32_t steps; };
 // caller's first push, then depth-1 sampled pushes; after each push the workspace and
 // grasp tests decide cost k and reward gamma^(k-1), or cost depth+1 and reward 0.
 RolloutOut rollout_env(Env& E, const oracle_params& P, const float* first_push, int depth, uint64_t seed,
-                       double* child13) {
+                       real* child13) {
     RolloutOut r{depth + 1, 0.f, 0, 0};
     for (int k = 1; k <= depth; k++) {
-        double push[4];
+        real push[4];
         if (k == 1) {
             for (int i = 0; i < 4; i++) push[i] = first_push[i];
-            std::vector<double> x, q, h;
+            std::vector<real> x, q, h;
             env_arrays(E, x, q, h);
-            std::vector<Foot<double>> F(E.b.size());
+            std::vector<Foot<real>> F(E.b.size());
             for (size_t i = 0; i < E.b.size(); i++) F[i] = footprint(&x[3 * i], &q[4 * i], &h[3 * i]);
-            if (start_blocked<double>(F, push[0], push[1], P.pusher_radius)) { r.flags |= F_INVALID_START; break; }
+            if (start_blocked<real>(F, push[0], push[1], P.pusher_radius)) { r.flags |= F_INVALID_START; break; }
         } else {
-            std::vector<double> x, q, h;
+            std::vector<real> x, q, h;
             env_arrays(E, x, q, h);
-            const int a = sample_push<double>((int)E.b.size(), x.data(), q.data(), h.data(), seed, k, P.pusher_radius,
+            const int a = sample_push<real>((int)E.b.size(), x.data(), q.data(), h.data(), seed, k, P.pusher_radius,
                                               P.sample_clearance, P.push_length, P.sample_attempts, P.contour_points, push);
             E.ev[EV_SAMPLE_ATTEMPTS] += a < 0 ? P.sample_attempts : a + 1;
             if (a < 0) { r.flags |= F_NOOP; push[0] = push[2] = push[1] = push[3] = 0; }
@@ -1622,7 +1679,7 @@ RolloutOut rollout_env(Env& E, const oracle_params& P, const float* first_push, 
         E.ev[EV_PUSH_EVALS]++;
         bool out = false;
         for (const Body& b : E.b)
-            if (std::fabs(b.x.x) > P.table_half[0] || std::fabs(b.x.y) > P.table_half[1]) out = true;
+            if (fabs(b.x.x) > P.table_half[0] || fabs(b.x.y) > P.table_half[1]) out = true;
         if (out) { r.flags |= F_OUT_OF_WS; break; }
         if (env_graspable(E, P)) {
             r.cost = k;
@@ -1635,10 +1692,11 @@ RolloutOut rollout_env(Env& E, const oracle_params& P, const float* first_push, 
     return r;
 }
 
-void to_double(int n, const float* s, double* d) { for (int i = 0; i < 13 * n; i++) d[i] = s[i]; }
+void to_double(int n, const float* s, real* d) { for (int i = 0; i < 13 * n; i++) d[i] = s[i]; }
 
 }  // namespace
 
+#ifndef ORACLE_COUNT_FLOPS
 extern "C" {
 
 int oracle_version(void) { return 1; }
@@ -1942,3 +2000,27 @@ int oracle_grasp_heightmap(const oracle_params* P, int f32, int n, const float* 
 }
 
 }  // extern "C"
+#endif
+
+#ifdef ORACLE_COUNT_FLOPS
+extern "C" {
+// Flop-counting build only: `count` substeps of one environment from state13 with the
+// given push; flops[0..4] = adds, subtracts, multiplies, divides and square roots of the
+// double engine by phase (per body, narrowphase, contact preparation, contact solve,
+// the rest), events[NEV] = the engine's event counters.
+int oracle_count_flops(const oracle_params* P, int n, const double* state13, const float* half, const float* mass,
+                       const float* mu, const double* push, int count, uint64_t* flops, uint64_t* events) {
+    std::vector<real> s13(state13, state13 + 13 * n);
+    std::vector<real> pu(push, push + 4);
+    Env E;
+    load_env(E, n, s13.data(), half, mass, mu);
+    set_push(E, *P, pu.data());
+    for (int k = 0; k < 8; k++) g_flops[k] = 0;  // the substeps only, not the set-up
+    for (int s = 0; s < count; s++) substep(E, *P, s);
+    for (int k = 0; k < 5; k++) flops[k] = g_flops[k];
+    for (int k = 0; k < NEV; k++) events[k] = E.ev[k];
+    return E.overflow ? 1 : 0;
+}
+int oracle_num_events(void) { return NEV; }
+}
+#endif

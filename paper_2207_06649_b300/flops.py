@@ -1,44 +1,51 @@
 """Algorithmic floating-point operation counts of the rollout path.
 
-The engine counts events per environment (pmbs_query_events); each event has a fixed
-hand-counted cost taken from the algorithm's formulas (multiply, add, subtract, divide
-and square root count 1 each, a fused multiply-add counts 2, compares, min/max and abs
-count 0).  Work on a static body (plane, pusher) is not counted: it is multiplication by
-zero inverse mass that the algorithm does not need.  Per-event costs:
+The engine counts events per environment (pmbs_query_events); each event carries a fixed
+cost, the average number of floating-point operations the plain double-precision
+statement of the method (the FP64 oracle) spends on it.  The costs were measured with the
+oracle's flop counter (its build with a counting scalar type: add, subtract, multiply,
+divide and square root count 1 each, a multiply-add 2, compares, abs, min and max 0) on
+48 seeded clutter scenes of the benchmark's distribution (4-40 boxes, one push of 240
+substeps each) and fitted per phase by least squares over the environments
+(oracle/fit_flop_costs.py); on held-out scenes the fitted costs reproduce the counted
+flops of every phase within 0.2 % (tests/test_flop_model.py checks 2 %).  As in the
+oracle and the CUDA kernel, a static body's terms (plane, pusher: zero velocity and
+inverse mass) are evaluated and counted, and the separating-axis test stops at the first
+separating axis, so its cost per test is the distribution's average.  Per-event costs:
 
-  box_steps      158  gravity 6, rotation matrix 30, world inverse inertia 48, AABB 27,
-                      integration (position 6, quaternion update and renormalise 41)
-  sat            723  15 separating axes: D 3, |A^T B| 45, 6 face axes 72, 9 edge axes
-                      (cross 9, |L|^2 5, sqrt 1, two support radii 40, |D.L| 5, 2, divide 1,
-                      normalise 4)
-  face           460  reference/incident face set-up 58, four Sutherland-Hodgman passes
-  clip_verts       8  depth of each clipped vertex
-  edge            95  supporting edges, closest points, midpoint
-  plane          128  eight vertices R h + c_z
-  pusher         107  capsule segment clipped to the box height, two closest points
-  points          99  per contact point: effective masses along n, t1, t2 for one body
-                      (cross 9, inertia product 15, dot 5, add 2, reciprocal 1) and bias
-  bb_points      105  second dynamic body of a box-box point, offsets rA and rB
-  manifolds       30  tangent basis and pair friction
-  pgs_points     128  normal row (relative velocity 12, projection and clamp 8, impulse
-                      on one body 33) and 2-D friction row with the disk clamp (75)
-  pgs_bb_points  102  the second dynamic body's velocity terms and impulses
+  box_steps      194  gravity, rotation matrix (twice: body frames and the pair predicate),
+                      world inverse inertia, AABB, integration
+  sat             75  one separating-axis test (most pairs separate on an early axis)
+  face           762  reference/incident face set-up and four Sutherland-Hodgman passes
+  clip_verts      70  depth test and the four-point reduction per clipped vertex
+  edge          1435  edge-edge test: all 15 axes, supporting edges, closest points
+  plane          167  box-plane: eight vertices R h + c and the deepest four
+  pusher         132  capsule segment clipped to the box height, closest points
+  points          98  per contact point: effective masses along n, t1, t2, bias
+  bb_points       93  second dynamic body of a box-box point
+  manifolds       27  tangent basis and pair friction
+  pgs_points     162  per point and iteration: normal row and 2-D friction row with the
+                      disk clamp, both bodies' velocity terms
+  pgs_bb_points   73  the second dynamic body's impulse updates
+
+Cylinder pairs are counted as separating-axis tests at the box cost (their 9 + 9 face
+and 81 edge axes are not), so rates on cylinder batches are lower bounds.
 """
 import numpy as np
 
 FLOPS_PER_EVENT = {
-    "box_steps": 158,
-    "sat": 723,
-    "face": 460,
-    "clip_verts": 8,
-    "edge": 95,
-    "plane": 128,
-    "pusher": 107,
-    "points": 99,
-    "bb_points": 105,
-    "manifolds": 30,
-    "pgs_points": 128,
-    "pgs_bb_points": 102,
+    "box_steps": 194.3,
+    "sat": 74.8,
+    "face": 762.0,
+    "clip_verts": 70.4,
+    "edge": 1435.3,
+    "plane": 166.8,
+    "pusher": 132.1,
+    "points": 97.8,
+    "bb_points": 93.4,
+    "manifolds": 27.3,
+    "pgs_points": 162.2,
+    "pgs_bb_points": 73.0,
 }
 
 
