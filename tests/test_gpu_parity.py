@@ -411,6 +411,40 @@ def test_event_counts_match_oracle_on_simple_scene(eng, orc):
         assert abs(g - w) <= 0.02 * w + 2, k
 
 
+def test_event_counts_and_flops_match_oracle_on_clutter(eng, orc):
+    """Ten substeps of 32 clutter scenes (4-40 boxes, one push each) from identical
+    states: the GPU's event counters against the oracle's, and the flop model applied to
+    the GPU's events against the oracle's flop counter on the same scenes.  Pair, plane
+    and pusher work follows the bit-exact pair lists; contact counts may differ where
+    FP32 and FP64 take a separating-axis near-tie differently."""
+    from paper_2207_06649_b300 import flops
+    sg = _sg()
+    scn, pushes, _ = sg.config_uneven(seed=41, n_envs=32, n_lo=5, n_hi=40, workers=1)
+    ids = eng.load(scn)
+    b = eng.rollout_pushes(ids, pushes, 1)
+    eng.step(b, 10)
+    gpu_ev = eng.query_events(b).astype(np.float64)
+    eng.release_batch(b)
+    eng.free_scenes(ids)
+    st = sg.state13(scn).astype(np.float64)
+    names = _pm().EVENT_NAMES
+    ora_ev = np.zeros_like(gpu_ev)
+    counted = 0.0
+    for e in range(scn.n_scenes):
+        a, z = scn.box_offset[e], scn.box_offset[e + 1]
+        f, ev = orc.count_flops(st[a:z], scn.half[a:z], scn.mass[a:z], scn.mu[a:z], pushes[e].astype(float), 10)
+        ora_ev[e] = ev
+        counted += sum(f[p] for p in ("per_body", "narrowphase", "contact_prep", "contact_solve"))
+    G, O = gpu_ev.sum(0), ora_ev.sum(0)
+    for k in ["substeps", "box_steps", "pair_tests", "sat", "plane", "pusher"]:
+        assert G[names.index(k)] == O[names.index(k)], k
+    for k in ["face", "points", "manifolds", "pgs_points", "colours"]:
+        assert abs(G[names.index(k)] - O[names.index(k)]) <= 0.02 * O[names.index(k)] + 2, k
+    model = flops.algorithmic_flops(gpu_ev, names)
+    print(f"flops: model on GPU events {model:.4g}, oracle counter {counted:.4g}, ratio {model / counted:.4f}")
+    assert abs(model - counted) <= 0.03 * counted
+
+
 # ------------------------------------------------------------------ full-size workloads
 def test_uneven_4096_env_launch_sampled_parity(eng, orc):
     """The 4096-env uneven workload in the benchmark's launch configuration: one launch
