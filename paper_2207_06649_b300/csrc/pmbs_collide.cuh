@@ -415,6 +415,10 @@ __device__ __forceinline__ void collide_capsule_box(const CBox& b, float px, flo
 }
 
 // ------------------------------------------------------------------ cylinders
+// The loops over the 16 cap vertices or side faces stay rolled: unrolled, they make the
+// cylinder instantiation's code larger than the instruction cache holds (measured
+// slower).
+//
 // Pairs with a cylinder (a 16-gon prism, see pmbs_exact.cuh) take the general
 // separating-axis test of two convex polyhedra: face normal directions of A (box: its 3
 // axes; cylinder: its cap axis, then the 8 side normal directions), those of B, and the
@@ -608,6 +612,7 @@ __device__ __forceinline__ int face_contact_convex(const CBox& ref, int f, float
             best = -dz;
             best_c = 1;
         }
+        #pragma unroll 1
         for (int k = 0; k < 16; k++) {
             const float dm = dot3(side_normal(inc, k), nref);
             if (dm < best) {
@@ -617,6 +622,7 @@ __device__ __forceinline__ int face_contact_convex(const CBox& ref, int f, float
         }
         if (best_c < 2) {
             const float sz = best_c == 0 ? 1.f : -1.f;
+            #pragma unroll 1
             for (int k = 0; k < 16; k++) P[0][k] = cyl_vertex(inc, k, sz);
             n = 16;
         } else {
@@ -675,6 +681,7 @@ __device__ __forceinline__ void support_edge(const CBox& b, int j, float3 L, flo
     } else if (j == 0) {
         int kb = 0;
         float best = 0.f;
+        #pragma unroll 1
         for (int k = 0; k < 16; k++) {
             float vc, vs;
             gon_vdir(k, vc, vs);
@@ -932,6 +939,7 @@ __device__ __forceinline__ void collide_capsule_cyl(const CBox& b, float px, flo
         const float lx = dot3(b.ax(0), rel), ly = dot3(b.ax(1), rel), lz = dot3(b.ax(2), rel);
         bool inside = true;
         float pen_side = 3.0e38f;
+        #pragma unroll 1
         for (int s = 0; s < 16; s++) {
             float fcs, fss;
             gon_fdir(s, fcs, fss);
@@ -942,6 +950,7 @@ __device__ __forceinline__ void collide_capsule_cyl(const CBox& b, float px, flo
         float qx = lx, qy = ly;
         if (!inside) {
             float bd = 0.f;
+            #pragma unroll 1
             for (int s = 0; s < 16; s++) {
                 float c0, s0, c1, s1;
                 gon_vdir(s, c0, s0);
