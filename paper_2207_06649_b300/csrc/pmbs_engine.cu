@@ -151,8 +151,10 @@ __device__ __forceinline__ void store_state(const WarpMem& W, int n, float* dst,
 }
 
 // One substep of the group's environment (on = false: the group only takes part in the
-// warp's collectives).  Returns true on a cap overflow.
-template <bool kCyl>
+// warp's collectives).  Returns true on a cap overflow.  kWarm compiles the optional warm
+// start in (batches without it run an instantiation whose substep body is 15 KB smaller:
+// the body is larger than an SM's instruction cache).
+template <bool kCyl, bool kWarm>
 __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, int n_env, bool on, const Pusher& pu,
                                         int s, const Grp& g, float4* warm, int& warm_n, PhaseClock& pc) {
     const SimConst& C = a.C;
@@ -198,10 +200,10 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
     pc.mark(tm, W, PH_PREP, rec);
     ovf |= colour_manifolds(W, n, g, on);
     pc.mark(tm, W, PH_COLOUR, rec);
-    if (C.warm && a.warm) warm_start(W, g, on, C, warm, warm_n);
+    if (kWarm && C.warm && a.warm) warm_start(W, g, on, C, warm, warm_n);
     int bb_visits = 0;
     const int visits = pgs(W, g, on, C.iters, V, bb_visits);
-    if (C.warm && a.warm) {
+    if (kWarm && C.warm && a.warm) {
         const int m = warm_save(W, g, on, warm);
         if (on) warm_n = m;
     }
@@ -225,7 +227,7 @@ __device__ __forceinline__ bool substep(const RolloutArgs& a, const WarpMem& W, 
 // (target graspable; Sec. IV-C hands such environments other work) takes the
 // next one while the other groups continue.  Push set-up and end-of-push phases run when
 // any group needs them; groups without work take part in the collectives only.
-template <bool kCyl>
+template <bool kCyl, bool kWarm>
 __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W, const Grp& g) {
     const SimConst& C = a.C;
     int e = -1;
@@ -323,7 +325,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
         // 3. one substep
         const bool run = active && !pg.done && pg.s < C.substeps && budget > 0;
         const Pusher pu = make_pusher(C, pg.push, pg.noop != 0);
-        ovf |= substep<kCyl>(a, W, ei.n, run, pu, pg.s, g, a.warm ? a.warm + (size_t)(e < 0 ? 0 : e) * a.warm_f4_per_env : nullptr,
+        ovf |= substep<kCyl, kWarm>(a, W, ei.n, run, pu, pg.s, g, a.warm ? a.warm + (size_t)(e < 0 ? 0 : e) * a.warm_f4_per_env : nullptr,
                        pg.pad[0], pc);
         // bounded run time per environment and launch (the shuffle runs in every lane)
         const bool late = g.bcast((int)(clock64() - t_start > a.watchdog_cycles), 0) != 0;
@@ -399,7 +401,7 @@ __device__ __forceinline__ void run_slots(const RolloutArgs& a, const WarpMem& W
 // 128 threads (up to four warps) per block and a register budget for three blocks per SM
 // (two with the cylinder contact paths, whose general separating-axis test and clipping
 // stay in registers): the solver keeps its working set in registers without spilling.
-template <bool kCyl>
+template <bool kCyl, bool kWarm>
 __global__ void __launch_bounds__(128, kCyl ? 2 : 3) rollout_kernel(const __grid_constant__ RolloutArgs a) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const Grp g(a.G, lane);
@@ -407,7 +409,15 @@ __global__ void __launch_bounds__(128, kCyl ? 2 : 3) rollout_kernel(const __grid
     const int slot = wib * per_warp + (lane / a.G);
     const size_t gslot = (size_t)blockIdx.x * (blockDim.x >> 5) * per_warp + slot;
     const WarpMem W = bind_mem(a.L, (uint32_t)slot * (uint32_t)a.L.bytes, a.gscratch + gslot * a.scratch_f4_per_warp);
-    run_slots<kCyl>(a, W, g);
+    run_slots<kCyl, kWarm>(a, W, g);
+}
+
+// The instantiation for a batch: cylinder contact paths and warm start compiled in only
+// when the batch needs them.
+using RolloutFn = void (*)(RolloutArgs);
+inline RolloutFn rollout_fn(bool cyl, bool warm) {
+    return cyl ? (warm ? rollout_kernel<true, true> : rollout_kernel<true, false>)
+               : (warm ? rollout_kernel<false, true> : rollout_kernel<false, false>);
 }
 // ---- rollout device code ends
 
@@ -618,11 +628,29 @@ __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_env
         srect[b][3] = min(kHMCells - 1, cell_of(sbox[b][3]) + 1);
     }
     __syncthreads();
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int b = 0; b < n; b++) {
-        const int i0 = srect[b][0], i1 = srect[b][1], j0 = srect[b][2], j1 = srect[b][3];
-        for (int j = j0 + ty; j <= j1; j += 16)
-            for (int i = i0 + tx; i <= i1; i += 32) {
+    // work items: every (body, cell) of every body's cell rectangle, numbered body by body
+    // and row by row; the block's threads take consecutive items, so small rectangles do
+    // not leave lanes idle
+    __shared__ int sstart[kMaxBoxes + 1];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < n; b++) {
+            sstart[b] = acc;
+            acc += max(0, srect[b][1] - srect[b][0] + 1) * max(0, srect[b][3] - srect[b][2] + 1);
+        }
+        sstart[n] = acc;
+    }
+    __syncthreads();
+    const int total = sstart[n];
+    int b = 0;
+    for (int item = threadIdx.x; item < total; item += blockDim.x) {
+        while (item >= sstart[b + 1]) b++;
+        {
+            const int w = srect[b][1] - srect[b][0] + 1;
+            const int o = item - sstart[b];
+            const int jr = o / w;
+            const int i = srect[b][0] + (o - jr * w), j = srect[b][2] + jr;
+            {
                 const float xc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)i, 0.5f), kHMCell));
                 const float yc = __fadd_rn(kHMOrigin, __fmul_rn(__fadd_rn((float)j, 0.5f), kHMCell));
                 if (xc < sbox[b][0] || xc > sbox[b][1] || yc < sbox[b][2] || yc > sbox[b][3]) continue;
@@ -657,6 +685,7 @@ __global__ void __launch_bounds__(512) heightmap_kernel(const Src src, int n_env
                     if (z > 0.f) atomicMax(&map[j * kHMCells + i], __float_as_uint(z));
                 }
             }
+        }
     }
     __syncthreads();
     float4* o = reinterpret_cast<float4*>(out + (size_t)e * kHMCells * kHMCells);
@@ -1119,10 +1148,8 @@ pmbs_status create_common(const pmbs_config* cfg, void* stream, void* d_arena, s
     ctx->d_table = (SceneDesc*)(base + ctx->table_off);
     e = cudaMemsetAsync(ctx->d_table, 0, sizeof(SceneDesc) * kSceneTableCap, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    for (int k = 0; k < 4 && e == cudaSuccess; k++)
+        e = cudaFuncSetAttribute(rollout_fn(k & 1, k & 2), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(heightmap_kernel<HMCsr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHMSmem);
@@ -1288,7 +1315,8 @@ pmbs_status launch_rollout_once(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaS
     const int threads = 32 * b.wpb;
     const size_t smem = (size_t)L.bytes * b.wpb * K;
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b.cyl ? rollout_kernel<true> : rollout_kernel<false>,
+    const RolloutFn kern = rollout_fn(b.cyl, b.warm != nullptr);
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
                                                      threads, smem));
     if (per_sm < 1) return fail(ctx, PMBS_E_INVALID, "launch shape does not fit on an SM");
     per_sm = std::min(per_sm, kMaxWarpsPerSM / b.wpb);
@@ -1343,8 +1371,7 @@ pmbs_status launch_rollout_once(pmbs_ctx* ctx, Batch& b, int max_substeps, cudaS
     a.phase = b.phase;
     a.n_rows = (long long)b.state_boxes;
     CU(cudaMemsetAsync(b.counters + 2, 0, sizeof(int), stream));
-    if (b.cyl) rollout_kernel<true><<<blocks, threads, smem, stream>>>(a);
-    else rollout_kernel<false><<<blocks, threads, smem, stream>>>(a);
+    kern<<<blocks, threads, smem, stream>>>(a);
     CU(cudaGetLastError());
     return PMBS_OK;
 }
@@ -2812,9 +2839,9 @@ pmbs_status noalloc_run(const pmbs_config& c, cudaStream_t stream, int n_envs, c
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PMBS_E_CUDA;
             int sms = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess) return PMBS_E_CUDA;
-            if (cudaFuncSetAttribute(rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            if (cudaFuncSetAttribute(rollout_fn(false, false), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
                     cudaSuccess ||
-                cudaFuncSetAttribute(rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+                cudaFuncSetAttribute(rollout_fn(true, false), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
                     cudaSuccess)
                 return PMBS_E_CUDA;
             dv.scratch = (unsigned char*)p;
@@ -2865,7 +2892,7 @@ pmbs_status noalloc_run(const pmbs_config& c, cudaStream_t stream, int n_envs, c
     const size_t smem = (size_t)L.bytes * wpb * K;
     if (smem > 227 * 1024) return PMBS_E_INVALID;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.cylinders ? rollout_kernel<true> : rollout_kernel<false>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_fn(c.cylinders != 0, false),
                                                       32 * wpb, smem) != cudaSuccess)
         return PMBS_E_CUDA;
     if (per_sm < 1) return PMBS_E_INVALID;
@@ -2910,8 +2937,7 @@ pmbs_status noalloc_run(const pmbs_config& c, cudaStream_t stream, int n_envs, c
     a.C.timers = 0;    // phase timers have no output here
     a.phase = nullptr;
     a.n_rows = LLONG_MAX;  // the record count is the caller's (not passed)
-    if (c.cylinders) rollout_kernel<true><<<blocks, 32 * wpb, smem, stream>>>(a);
-    else rollout_kernel<false><<<blocks, 32 * wpb, smem, stream>>>(a);
+    rollout_fn(c.cylinders != 0, false)<<<blocks, 32 * wpb, smem, stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return PMBS_E_CUDA;
     int host_cnt[8];
     if (cudaMemcpyAsync(host_cnt, counters, sizeof(host_cnt), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
