@@ -543,8 +543,10 @@ __device__ __forceinline__ bool narrowphase(const WarpMem& W, const Grp& g, bool
             B = pr >> 8;
             const CBox a = load_cbox(W, A), b = load_cbox(W, B);
             sat++;
-            const int kd = (kCyl && (a.cyl || b.cyl)) ? collide_convex(a, b, C.margin, cm, clipv)
-                                                      : collide_box_box(a, b, C.margin, cm, clipv);
+            // with the cylinder paths compiled in, box pairs go through the general convex
+            // routine too (the same axes, thresholds and tie rules as the box-box routine):
+            // the lanes of a warp stay in one routine and the code stays smaller
+            const int kd = kCyl ? collide_convex(a, b, C.margin, cm, clipv) : collide_box_box(a, b, C.margin, cm, clipv);
             if (kd == 1) face++;
             if (kd == 2) edge++;
             mu = sqrtf(W.bw()[A].w * W.bw()[B].w);
