@@ -213,8 +213,9 @@ pmbs_status pmbs_step_graph(pmbs_ctx* ctx, int64_t batch, int substeps_per_launc
 /* Autotuner of the launch shape (batching knobs only, never the arithmetic): builds the
  * given batch once per candidate shape (lanes per environment 32/16/8, warps per block
  * 4/2/1, manifolds per environment kept in shared memory 0/8/16/40), times its first
- * `substeps` substeps (best of two freshly built batches), re-times the three fastest
- * over the whole rollout, then picks the iteration tiling of the winner (one persistent
+ * `substeps` substeps (best of two freshly built batches), re-times the five fastest and
+ * the default shape (32 lanes, 2 warps per block, 8 manifolds) over the whole rollout, then
+ * picks the iteration tiling of the winner (one persistent
  * launch, or launches of one push or a quarter push of substeps each; the same results)
  * with CUDA events, and records the fastest shape for the batch's box-count bucket; later
  * batches in that bucket use it unless a shape is fixed.  Outputs may be NULL.  Blocks

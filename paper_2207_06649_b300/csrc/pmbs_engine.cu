@@ -1876,7 +1876,7 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
         }
         if (e != cudaSuccess) result = fail(ctx, PMBS_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
     };
-    // screening on the first `substeps` substeps, then the three fastest shapes timed over
+    // screening on the first `substeps` substeps, then the fastest shapes timed over
     // the whole rollout (a batch's time follows its longest environments, which the first
     // push alone does not rank reliably)
     std::vector<std::pair<float, std::array<int, 3>>> screen;
@@ -1889,14 +1889,21 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
                 if (result == PMBS_OK) screen.push_back({ms, {Gs[gi], Ws[wi], used}});
             }
     std::sort(screen.begin(), screen.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    // whole-rollout finalists: the five fastest screened shapes and the default shape (one
+    // environment per warp, two warps per block, eight shared manifolds), which the
+    // screening has been seen to rank too low
+    std::vector<std::array<int, 3>> finalists;
+    for (size_t k = 0; k < std::min<size_t>(5, screen.size()); k++) finalists.push_back(screen[k].second);
+    const std::array<int, 3> dflt = {32, 2, 8};
+    if (std::find(finalists.begin(), finalists.end(), dflt) == finalists.end()) finalists.push_back(dflt);
     float best_ms = 1e30f;
     std::array<int, 3> best = {32, 4, -1};
     const int saved_tile = ctx->fixed_tile;
     ctx->fixed_tile = 0;
-    for (size_t k = 0; k < std::min<size_t>(3, screen.size()) && result == PMBS_OK; k++) {
+    for (size_t k = 0; k < finalists.size() && result == PMBS_OK; k++) {
         float ms = 0.f;
         int used = -1;
-        const auto& sh = screen[k].second;
+        const auto& sh = finalists[k];
         time_shape(sh[0], sh[1], sh[2], 0, ms, used);
         if (result == PMBS_OK && ms < best_ms) {
             best_ms = ms;
