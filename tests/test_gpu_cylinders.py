@@ -162,12 +162,30 @@ def test_cylinder_clutter_one_substep(orc, seed):
     st, steps = _run(eng, sc, pushes, 1)
     eng.close()
     s0 = sg.state13(sc)
+    dv, dw = [], []
     for e in range(sc.n_scenes):
         a, b = sc.box_offset[e], sc.box_offset[e + 1]
         ref, _, _ = orc.run_substeps(s0[a:b], sc.half[a:b], sc.mass[a:b], sc.mu[a:b], push=pushes[e].astype(float), count=1)
         assert steps[e] == 1
         assert np.abs(st[a:b, :3] - ref[:, :3]).max() <= 1e-4
         assert _angle_err(st[a:b, 3:7], ref[:, 3:7]).max() <= 1e-3
+        dv.extend(np.abs(st[a:b, 7:10] - ref[:, 7:10]).max(1))
+        dw.extend(np.abs(st[a:b, 10:13] - ref[:, 10:13]).max(1))
+    # Velocities: the box parity tests' FP32-rounding bounds (1e-5 m/s; for a solid
+    # cylinder of radius and half height >= 1 cm a velocity error dv at the surface turns
+    # into at most 12 sqrt(r^2 + h^2) / (3 r^2 + 4 h^2) dv = 242 dv of spin about a
+    # diameter, 2 / r = 200 dv about the axis, so 3e-3 rad/s) for at least 99 % of the
+    # bodies.  The rest sit in a contact whose separating axis or reduced points are a
+    # near-tie among a prism's 18 face and 81 edge directions, which FP32 and FP64 may
+    # break differently (several contact sets are correct there); they are held to the
+    # bound the position check already sets, 1e-4 m in one substep = 0.024 m/s (x 242 of
+    # spin).
+    dv, dw = np.array(dv), np.array(dw)
+    ok = (dv <= 1e-5) & (dw <= 3e-3)
+    print(f"cylinder clutter one substep, seed {seed}: {ok.mean() * 100:.2f} % of {len(dv)} bodies within "
+          f"1e-5 m/s and 3e-3 rad/s; max {dv.max():.2e} m/s, {dw.max():.2e} rad/s")
+    assert ok.mean() >= 0.99
+    assert dv.max() <= 0.024 and dw.max() <= 0.024 * 242
 
 
 def _env(rows, halves, mass=0.1, mu=0.5):
