@@ -7,6 +7,7 @@
 // further simulations) takes the next one.  See pmbs.h for the contract of every entry
 // point.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -982,6 +983,14 @@ struct pmbs_ctx {
 
 namespace {
 
+// NVTX range over a host call (visible in a profiler's timeline; free without one).  A
+// push runs inside the persistent kernel, so ranges mark the calls and the server's
+// launches, not individual pushes.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 pmbs_status fail(pmbs_ctx* c, pmbs_status s, const std::string& m) {
     c->err = m;
     return s;
@@ -1648,6 +1657,7 @@ const char* pmbs_last_error(const pmbs_ctx* ctx) { return ctx ? ctx->err.c_str()
 pmbs_status pmbs_load_scenes(pmbs_ctx* ctx, int n_scenes, const int32_t* box_offset, const float* pose,
                              const float* vel, const float* half_ext, const float* mass, const float* mu,
                              const int32_t* target, int32_t* out_scene_ids) {
+    NvtxRange nvtx_("pmbs_load_scenes");
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -1741,6 +1751,7 @@ pmbs_status pmbs_free_scenes(pmbs_ctx* ctx, int n, const int32_t* scene_ids) {
 
 pmbs_status pmbs_rollout_pushes(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push,
                                 int depth, const uint64_t* seeds, int64_t* out_batch) {
+    NvtxRange nvtx_("pmbs_rollout_pushes");
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -1759,6 +1770,7 @@ pmbs_status pmbs_rollout_pushes_device(pmbs_ctx* ctx, int n_envs, const int32_t*
 }
 
 pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps) {
+    NvtxRange nvtx_("pmbs_step");
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -1791,6 +1803,7 @@ pmbs_status pmbs_step(pmbs_ctx* ctx, int64_t batch, int max_substeps) {
 }
 
 pmbs_status pmbs_step_graph(pmbs_ctx* ctx, int64_t batch, int substeps_per_launch) {
+    NvtxRange nvtx_("pmbs_step_graph");
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -1829,6 +1842,7 @@ pmbs_status pmbs_step_graph(pmbs_ctx* ctx, int64_t batch, int substeps_per_launc
 pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, const float* first_push, int depth,
                           const uint64_t* seeds, int substeps, int32_t* out_lanes_per_env, int32_t* out_warps_per_block,
                           int32_t* out_smem_manifolds, float* out_ms, int32_t* out_substeps_per_launch) {
+    NvtxRange nvtx_("pmbs_autotune");
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -1944,6 +1958,7 @@ pmbs_status pmbs_autotune(pmbs_ctx* ctx, int n_envs, const int32_t* scene_ids, c
 
 pmbs_status pmbs_query_cost(pmbs_ctx* ctx, int64_t batch, int32_t* out_cost, float* out_reward, uint8_t* out_flags,
                             float* out_child_states, int32_t* out_child_scene_ids) {
+    NvtxRange nvtx_("pmbs_query_cost");
     if (!ctx) return PMBS_E_INVALID;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -2436,6 +2451,7 @@ namespace {
 // return), give it its own stream and scratch, launch it.  Returns PMBS_E_OOM when the
 // arena cannot hold it now.
 pmbs_status server_admit(pmbs_server* sv, Request& r) {
+    NvtxRange nvtx_("pmbs_server_admit");
     pmbs_ctx* ctx = sv->ctx;
     std::lock_guard<std::mutex> lk(ctx->mu);
     int64_t id = 0;
