@@ -407,9 +407,12 @@ __device__ __forceinline__ bool broadphase(const WarpMem& W, int n, const Grp& g
         if (i < n) {
             const float lx = W.lo()[i], hx = W.hi()[i], ly = W.lo()[NB + i], hy = W.hi()[NB + i];
             const float lz = W.lo()[2 * NB + i], hz = W.hi()[2 * NB + i];
+            // all six bounds loaded, then combined without short-circuits: one load latency
+            // per candidate instead of six dependent load-compare-branch steps
             for (int j = i + 1; j < n; j++) {
-                const bool ov = lx <= W.hi()[j] && W.lo()[j] <= hx && ly <= W.hi()[NB + j] && W.lo()[NB + j] <= hy &&
-                                lz <= W.hi()[2 * NB + j] && W.lo()[2 * NB + j] <= hz;
+                const float hxj = W.hi()[j], lxj = W.lo()[j], hyj = W.hi()[NB + j], lyj = W.lo()[NB + j];
+                const float hzj = W.hi()[2 * NB + j], lzj = W.lo()[2 * NB + j];
+                const bool ov = (lx <= hxj) & (lxj <= hx) & (ly <= hyj) & (lyj <= hy) & (lz <= hzj) & (lzj <= hz);
                 mask |= (unsigned long long)ov << j;
             }
         }
