@@ -95,16 +95,21 @@ __device__ __forceinline__ void collide_box_plane(const CBox& b, float margin, C
 // produce more, and vertices beyond the eighth are dropped.
 __device__ __forceinline__ int clip_side(const float3* in, int n, float3* out, float3 o, float3 a, float h) {
     int m = 0;
+    if (n <= 0) return 0;
+    // the previous vertex and its signed distance carried from the last iteration
+    float3 prev = in[n - 1];
+    float dp = dot3(prev - o, a) - h;
     for (int i = 0; i < n; i++) {
         const float3 cur = in[i];
-        const float3 prev = in[(i + n - 1) % n];
-        const float dc = dot3(cur - o, a) - h, dp = dot3(prev - o, a) - h;
+        const float dc = dot3(cur - o, a) - h;
         if (dc <= 0.f) {
             if (dp > 0.f && m < 8) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
             if (m < 8) out[m++] = cur;
         } else if (dp <= 0.f) {
             if (m < 8) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
         }
+        prev = cur;
+        dp = dc;
     }
     return m;
 }
@@ -546,16 +551,21 @@ __device__ __forceinline__ int reduce_points(const float3* B, const float* kd, i
 // Sutherland-Hodgman clip against dot(p - o, a) - h <= 0, at most 32 vertices kept.
 __device__ __forceinline__ int clip_side32(const float3* in, int n, float3* out, float3 o, float3 a, float h) {
     int m = 0;
+    if (n <= 0) return 0;
+    // the previous vertex and its signed distance carried from the last iteration
+    float3 prev = in[n - 1];
+    float dp = dot3(prev - o, a) - h;
     for (int i = 0; i < n; i++) {
         const float3 cur = in[i];
-        const float3 prev = in[(i + n - 1) % n];
-        const float dc = dot3(cur - o, a) - h, dp = dot3(prev - o, a) - h;
+        const float dc = dot3(cur - o, a) - h;
         if (dc <= 0.f) {
             if (dp > 0.f && m < 32) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
             if (m < 32) out[m++] = cur;
         } else if (dp <= 0.f) {
             if (m < 32) out[m++] = prev + (cur - prev) * __fdividef(dp, dp - dc);
         }
+        prev = cur;
+        dp = dc;
     }
     return m;
 }
