@@ -36,8 +36,8 @@ sys.path.insert(0, ROOT)
 
 # DRAM traffic of one rollout-kernel launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was measured on.
-TRAFFIC = {"source_sha": "b43a6a204e3857f5", "bytes_per_launch": 123297792,
-           "note": "ncu dram bytes (read 21.37 MB + write 101.93 MB) of one launch of the benchmark "
+TRAFFIC = {"source_sha": "f79caa85e37b8739", "bytes_per_launch": 118213120,
+           "note": "ncu dram bytes (read 21.36 MB + write 96.85 MB) of one launch of the benchmark "
                    "workload itself (4096 scenes, depth 3) in the 32,2,0 launch shape, single-pass capture"}
 
 
