@@ -36,6 +36,27 @@ def test_counter_counts_free_flight_by_hand(orc):
     assert abs(_model_by_phase(ev1)["per_body"] - f1["per_body"]) <= 0.01 * f1["per_body"]
 
 
+@pytest.mark.parametrize("vx, clamped", [(0.0, False), (0.1, True)])
+def test_counter_counts_the_solve_by_hand(orc, vx, clamped):
+    """A box resting on the table (4 plane points, 10 iterations, one substep), counted by
+    hand from the solve's formulas (Sec. III-A transition; the projected Gauss-Seidel
+    reading), with the plane as the static body: normal row = relative velocity of the
+    two bodies 27 (two cross products 9 + 9, two sums 3 + 3, difference 3), dot 5, target
+    and projection 4 (difference, product, sum, difference), impulse n dl 3, one dynamic
+    body's update 33 (v + P im: 6, r x P: 9, I^-1 (.): 15, sum 3) -- 72; friction pair =
+    relative velocity 27, two dots 10, two candidates 4, limit 1, |c|^2 3, the clamp test
+    1, two differences 2, impulse t1 d1 + t2 d2 9, body update 33 -- 90, plus 4 when the
+    candidate is scaled onto the disk (a quotient, a square root, two products).  At rest
+    the candidate is inside the disk; sliding (0.1 m/s) it is scaled every time."""
+    st = np.array([[0.0, 0.0, 0.01, 1, 0, 0, 0, vx, 0, 0, 0, 0, 0]], np.float64)
+    half = np.array([[0.01, 0.01, 0.01]], np.float32)
+    f, ev = orc.count_flops(st, half, np.array([0.1], np.float32), np.array([0.5], np.float32),
+                            np.array([0.19, 0.19, 0.19, 0.19]), 1)
+    visits = 10 * 4
+    assert int(ev[orc.EVENT_NAMES.index("pgs_points")]) == visits
+    assert f["contact_solve"] == visits * (72 + 90 + (4 if clamped else 0))
+
+
 @pytest.mark.parametrize("seed", [31, 32])
 def test_model_reproduces_the_counter_on_held_out_clutter(orc, seed):
     from paper_2207_06649_b300 import scenegen as sg
